@@ -1,0 +1,152 @@
+/*
+ * fe.h -- C ABI of the GB300 (sm_103a) recursive Fermi-operator expansion
+ * library: the projected density matrix D = f(Hp) and the band energy
+ * tr(Hp D) from a dense symmetric projected Hamiltonian Hp.
+ *
+ * Method (arXiv 2301.04642, Khadatkar & Motamarri):
+ *   - Sec. II-A: D = theta(mu I - Hp) at zero temperature (projector on the
+ *     N_e lowest eigenvectors), D = [exp(beta (Hp - mu I)) + I]^{-1} at
+ *     finite temperature, beta = 1/kT.
+ *   - Sec. II-B1, Eq. (1): zero temperature by SP2, X_{k+1} = X_k^2 or
+ *     2 X_k - X_k^2, the branch chosen from tr X and tr X^2 = ||X||_F^2
+ *     (Sec. III-B) so that tr X -> N_e.  X_0 is Hp scaled into [0, 1] with
+ *     Gershgorin bounds (Sec. II-C).
+ *   - Sec. III-A: relative trace change RelTr as the convergence measure and a
+ *     mixed-precision schedule (cheap products far from convergence, FP64-
+ *     accurate products at the end).
+ *   - Sec. II-B3, Eq. (2): finite temperature by a recursive expansion whose
+ *     every step doubles the inverse temperature (see FE_METHOD_FERMI).
+ *
+ * Conventions for every function:
+ *   - Matrices are dense, row-major, FP64, with a leading dimension ld >= n
+ *     (elements between n and ld in a row are ignored / not written).
+ *   - Hp must be symmetric with both triangles stored (rows are read whole).
+ *   - Pointers are host or device pointers as the problem's flags say
+ *     (FE_PTR_HOST / FE_PTR_DEVICE); device pointers must belong to the
+ *     context's device.  The caller owns Hp and D.
+ *   - Every call returns an FE_* status; no call exits, throws or traps.
+ *     fe_last_error_string() gives a one-line reason for the last failure.
+ *   - A context is used by one host thread at a time, except fe_submit /
+ *     fe_poll, which may be called from any thread.
+ */
+#ifndef FE_H
+#define FE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FE_API __attribute__((visibility("default")))
+#else
+#define FE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define FE_OK 0
+#define FE_PENDING 1       /* fe_poll: solve still queued or running          */
+#define FE_EINVAL (-1)     /* bad argument (see fe_problem), or NaN/Inf in Hp   */
+#define FE_ENOMEM (-2)     /* does not fit the context's HBM budget at all      */
+#define FE_ENOTCONV (-3)   /* iteration cap reached (e.g. degenerate HOMO/LUMO) */
+#define FE_ETIMEOUT (-4)   /* a bounded device wait expired; context still usable */
+#define FE_ECUDA (-5)      /* CUDA runtime/driver error                          */
+#define FE_EBUSY (-6)      /* too many outstanding tickets                       */
+
+/* ---- problem flags -------------------------------------------------------- */
+#define FE_PTR_HOST 0x0u      /* Hp and D are host pointers (default)          */
+#define FE_PTR_DEVICE 0x1u    /* Hp and D are device pointers                  */
+
+#define FE_METHOD_AUTO 0x00u  /* SP2 if kT == 0 else FERMI                     */
+#define FE_METHOD_SP2 0x10u   /* zero temperature, Sec. II-B1                   */
+#define FE_METHOD_FERMI 0x20u /* finite temperature, doubling recursion         */
+#define FE_METHOD_MASK 0xF0u
+
+/* Precision schedules (Sec. III-A).  Bits 8..11. */
+#define FE_PREC_MIXED 0x000u  /* split FP16 tensor-core products, FP64 polish   */
+#define FE_PREC_FP64 0x100u   /* every product in FP64 (the plain baseline)     */
+#define FE_PREC_FP32 0x200u   /* split FP16 tensor-core products only, no polish */
+#define FE_PREC_TRY_FP16 0x300u /* single FP16 products until RelTr < 5e-4, then MIXED */
+#define FE_PREC_MASK 0xF00u
+
+/* ---- context ---------------------------------------------------------------- */
+typedef struct fe_ctx fe_ctx;
+
+typedef struct {
+    int device;               /* CUDA device ordinal                              */
+    size_t hbm_budget_bytes;  /* pool limit; 0 = 80% of the device's free memory  */
+    int max_iters;            /* cap on expansion products per phase; 0 = 100     */
+    uint32_t precision_policy;/* default FE_PREC_* when a problem leaves it 0     */
+    void *cuda_stream;        /* cudaStream_t to run on; NULL = library stream    */
+    const char *autotune_path;/* reserved, must be NULL                           */
+} fe_config;
+
+typedef struct {
+    const double *Hp;  /* n x n symmetric, row-major, leading dimension ld        */
+    int64_t n;         /* dimension, >= 1                                           */
+    int64_t ld;        /* leading dimension of Hp and D, >= n                       */
+    double n_e;        /* electron count N_e (occupied states, no spin factor),
+                          0 <= n_e <= n; integral when kT == 0                     */
+    double kT;         /* smearing temperature in the units of Hp; 0 = zero T      */
+    double tol;        /* RelTr stop |tr X_k - tr X_{k-1}| / N_e; 0 = 5e-8          */
+    double *D;         /* output density matrix (n x n, ld), may be NULL           */
+    uint32_t flags;    /* FE_PTR_* | FE_METHOD_* | FE_PREC_*                        */
+} fe_problem;
+
+typedef struct {
+    int status;             /* FE_* of this solve                                  */
+    int iters;              /* total expansion products                            */
+    int iters_by_phase[4];  /* [0] single-FP16, [1] split-FP16, [2] FP64, [3] finite-T steps */
+    double e_band;          /* tr(Hp D), FP64                                       */
+    double trace;           /* tr D                                                 */
+    double idem_fro;        /* ||D^2 - D||_F measured on the last FP64 product (0 T) */
+    double mu;              /* chemical potential (finite T), HOMO/LUMO midpoint estimate (0 T) */
+    double eps_min;         /* Gershgorin lower bound of Hp                          */
+    double eps_max;         /* Gershgorin upper bound of Hp                          */
+    double ms;              /* device time of the solve (CUDA events), milliseconds */
+} fe_result;
+
+typedef uint64_t fe_ticket;
+
+/* Create a context on cfg->device.  cfg may be NULL (defaults).
+ * Errors: FE_EINVAL (bad device / autotune_path != NULL), FE_ECUDA. */
+FE_API int fe_create(fe_ctx **out, const fe_config *cfg);
+
+/* Wait for outstanding work, free all device memory.  NULL is accepted. */
+FE_API int fe_destroy(fe_ctx *ctx);
+
+/* Blocking solve of one problem.  Hp is read (copied into the pool first when
+ * it is a host pointer, or when its ld is not the pool's layout); D (if not
+ * NULL) is written on success.  r receives the result even on failure.
+ * Errors: FE_EINVAL (n < 1, ld < n, N_e out of [0, n], kT < 0, non-integral
+ * N_e at kT == 0, tol < 0, NaN/Inf in Hp), FE_ENOMEM, FE_ENOTCONV,
+ * FE_ETIMEOUT, FE_ECUDA. */
+FE_API int fe_solve(fe_ctx *ctx, const fe_problem *p, fe_result *r);
+
+/* Solve `count` independent problems (any mix of n) in one launch sequence:
+ * each expansion step is one persistent launch over the tiles of all active
+ * problems.  rs[i] receives problem i's result; the return value is FE_OK if
+ * every problem succeeded, else the first failing status. */
+FE_API int fe_solve_batch(fe_ctx *ctx, int count, const fe_problem *ps, fe_result *rs);
+
+/* Non-blocking submission for continuous batching.  Hp is copied into the
+ * pool before this returns (the caller may reuse it); D must stay valid until
+ * fe_poll returns a final status for the ticket.  Requests that do not fit
+ * the free part of the HBM budget wait in a queue; a request larger than the
+ * whole budget fails with FE_ENOMEM. */
+FE_API int fe_submit(fe_ctx *ctx, const fe_problem *p, fe_ticket *t);
+
+/* FE_PENDING while the ticket's solve is queued or running; otherwise the
+ * final status, with r filled.  Never blocks. */
+FE_API int fe_poll(fe_ctx *ctx, fe_ticket t, fe_result *r);
+
+/* One-line description of the last error on this context (or of the last
+ * fe_create failure when ctx is NULL).  Valid until the next call. */
+FE_API const char *fe_last_error_string(const fe_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_H */

@@ -1,0 +1,40 @@
+/*
+ * fe_kernels.h -- single hot-path steps of the expansion exposed through the C
+ * ABI, so each kernel can be checked on its own against the CPU oracle.
+ * They run on the context's stream and return when the result is ready.
+ * All pointers are DEVICE pointers on the context's device; the caller owns
+ * them.  Matrices are row-major with the given leading dimension.  Errors:
+ * FE_EINVAL for bad sizes/pointers, FE_ENOMEM, FE_ECUDA, FE_ETIMEOUT.
+ */
+#ifndef FE_KERNELS_H
+#define FE_KERNELS_H
+
+#include <stdint.h>
+
+#include "fe.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Gershgorin bounds of a symmetric H (Sec. II-C: spectral bounds eps_1,
+ * eps_N of H are needed to scale it into [0, 1]).
+ * out4 (HOST, 4 doubles): [0] = min_i (H_ii - sum_{j!=i} |H_ij|),
+ * [1] = max_i (H_ii + sum_{j!=i} |H_ij|), [2] = tr H, [3] = 1.0 if H holds a
+ * NaN/Inf else 0.0. */
+FE_API int fe_k_gershgorin(fe_ctx *ctx, const double *H, int64_t n, int64_t ld, double *out4);
+
+/* C = Y * Y for a symmetric FP32 matrix Y, computed by the tensor-core kernel
+ * of the SP2 step (Sec. II-B1 Eq. (1); the product is the dominant cost,
+ * Sec. III-B): Y is scaled by a power of two s with s * bound <= 2^14 and
+ * split into FP16 slices (nslices = 1: fp16(sY); nslices = 2: hi + lo), the
+ * slice products are accumulated in FP32 in tensor memory, and only the upper
+ * triangle of 128x128 blocks is computed and mirrored.  bound must satisfy
+ * |Y_ij| <= bound.  C (FP32, ldc) is written whole and exactly symmetric. */
+FE_API int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t ldy, float *C, int64_t ldc,
+                    int nslices, double bound);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_KERNELS_H */

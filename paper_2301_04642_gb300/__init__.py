@@ -1,0 +1,198 @@
+"""GB300 (sm_103a) recursive Fermi-operator expansion: D = f(Hp), tr(Hp D).
+
+Thin ctypes binding of the C ABI in ``include/fe.h`` / ``include/fe_kernels.h``.
+It only marshals arguments (pointers, sizes, flags); every step of the solve
+runs in the library's CUDA kernels.  PyTorch, when used, only provides device
+memory and the current stream.  There is no CPU fallback: if the library or a
+GB300 is missing, the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FE_OK, FE_PENDING, FE_EINVAL, FE_ENOMEM, FE_ENOTCONV, FE_ETIMEOUT, FE_ECUDA, FE_EBUSY = (
+    0, 1, -1, -2, -3, -4, -5, -6)
+STATUS_NAMES = {0: "FE_OK", 1: "FE_PENDING", -1: "FE_EINVAL", -2: "FE_ENOMEM", -3: "FE_ENOTCONV",
+                -4: "FE_ETIMEOUT", -5: "FE_ECUDA", -6: "FE_EBUSY"}
+FE_PTR_HOST, FE_PTR_DEVICE = 0x0, 0x1
+FE_METHOD_AUTO, FE_METHOD_SP2, FE_METHOD_FERMI = 0x00, 0x10, 0x20
+PREC = {"mixed": 0x000, "fp64": 0x100, "fp32": 0x200, "try_fp16": 0x300}
+
+
+class FeConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("max_iters", ctypes.c_int), ("precision_policy", ctypes.c_uint32),
+                ("cuda_stream", ctypes.c_void_p), ("autotune_path", ctypes.c_char_p)]
+
+
+class FeProblem(ctypes.Structure):
+    _fields_ = [("Hp", ctypes.c_void_p), ("n", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("n_e", ctypes.c_double), ("kT", ctypes.c_double), ("tol", ctypes.c_double),
+                ("D", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+class FeResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("iters_by_phase", ctypes.c_int * 4), ("e_band", ctypes.c_double),
+                ("trace", ctypes.c_double), ("idem_fro", ctypes.c_double), ("mu", ctypes.c_double),
+                ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "iters_by_phase"}
+        d["iters_by_phase"] = list(self.iters_by_phase)
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build=True):
+    """Load (building first if needed) libfe.so and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64, dbl = ctypes.c_int64, ctypes.c_double
+    L.fe_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(FeConfig)]
+    L.fe_destroy.argtypes = [P]
+    L.fe_solve.argtypes = [P, ctypes.POINTER(FeProblem), ctypes.POINTER(FeResult)]
+    L.fe_solve_batch.argtypes = [P, ctypes.c_int, ctypes.POINTER(FeProblem), ctypes.POINTER(FeResult)]
+    L.fe_submit.argtypes = [P, ctypes.POINTER(FeProblem), ctypes.POINTER(ctypes.c_uint64)]
+    L.fe_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(FeResult)]
+    L.fe_last_error_string.argtypes = [P]
+    L.fe_last_error_string.restype = ctypes.c_char_p
+    L.fe_k_gershgorin.argtypes = [P, P, i64, i64, ctypes.POINTER(dbl)]
+    L.fe_k_sym_square.argtypes = [P, P, i64, i64, P, i64, ctypes.c_int, dbl]
+    for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
+                 "fe_k_gershgorin", "fe_k_sym_square"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class FeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(x):
+    """(address, is_device, keepalive) of a torch tensor or numpy array."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data, False, x
+    import torch
+    if isinstance(x, torch.Tensor):
+        return x.data_ptr(), x.is_cuda, x
+    raise TypeError("expected a numpy array or torch tensor")
+
+
+class Context:
+    """One library context (fe_create) on one GPU."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0, max_iters=0, precision="mixed", stream=None):
+        self.L = load()
+        cfg = FeConfig(device, hbm_budget_bytes, max_iters, PREC[precision],
+                       ctypes.c_void_p(stream) if stream else None, None)
+        h = ctypes.c_void_p()
+        rc = self.L.fe_create(ctypes.byref(h), ctypes.byref(cfg))
+        if rc != FE_OK:
+            raise FeError(rc, self.L.fe_last_error_string(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.fe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def last_error(self):
+        return self.L.fe_last_error_string(self.h).decode()
+
+    def _problem(self, H, ne, kT, tol, D, precision, method):
+        hp, hdev, keep_h = _ptr(H)
+        n = H.shape[0]
+        assert H.shape[0] == H.shape[1]
+        ld = (H.stride(0) if hasattr(H, "stride") and callable(H.stride) else H.strides[0] // 8)
+        dp = None
+        keep_d = None
+        if D is not None:
+            dp, ddev, keep_d = _ptr(D)
+            if ddev != hdev:
+                raise ValueError("Hp and D must both be host or both be device buffers")
+            dld = (D.stride(0) if hasattr(D, "stride") and callable(D.stride) else D.strides[0] // 8)
+            if dld != ld:
+                raise ValueError("Hp and D must share the leading dimension")
+        flags = (FE_PTR_DEVICE if hdev else FE_PTR_HOST) | PREC[precision] | method
+        p = FeProblem(hp, n, ld, float(ne), float(kT), float(tol), dp, flags)
+        return p, (keep_h, keep_d)
+
+    def solve(self, H, ne, kT=0.0, tol=0.0, D=None, precision="mixed", method=FE_METHOD_AUTO,
+              check=True):
+        """Solve one problem.  H (n x n FP64, host numpy or device torch); D
+        (same kind, written) or None.  Returns the result dict."""
+        p, keep = self._problem(H, ne, kT, tol, D, precision, method)
+        r = FeResult()
+        rc = self.L.fe_solve(self.h, ctypes.byref(p), ctypes.byref(r))
+        if check and rc != FE_OK:
+            raise FeError(rc, self.last_error())
+        out = r.as_dict()
+        out["rc"] = rc
+        return out
+
+    def solve_batch(self, items, check=True):
+        """items: list of dict(H=..., ne=..., kT=0, tol=0, D=None, precision='mixed')."""
+        probs = (FeProblem * len(items))()
+        keep = []
+        for k, it in enumerate(items):
+            p, kp = self._problem(it["H"], it["ne"], it.get("kT", 0.0), it.get("tol", 0.0),
+                                  it.get("D"), it.get("precision", "mixed"),
+                                  it.get("method", FE_METHOD_AUTO))
+            probs[k] = p
+            keep.append(kp)
+        res = (FeResult * len(items))()
+        rc = self.L.fe_solve_batch(self.h, len(items), probs, res)
+        if check and rc != FE_OK:
+            raise FeError(rc, self.last_error())
+        return rc, [r.as_dict() for r in res]
+
+    # ---- single kernels (device buffers) -------------------------------------
+    def gershgorin(self, H):
+        hp, hdev, _ = _ptr(H)
+        assert hdev, "device tensor expected"
+        out = (ctypes.c_double * 4)()
+        rc = self.L.fe_k_gershgorin(self.h, hp, H.shape[0], H.stride(0), out)
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+        return list(out)
+
+    def sym_square(self, Y, C, nslices=2, bound=None):
+        yp, ydev, _ = _ptr(Y)
+        cp, cdev, _ = _ptr(C)
+        assert ydev and cdev, "device tensors expected"
+        if bound is None:
+            bound = float(Y.abs().max())
+        rc = self.L.fe_k_sym_square(self.h, yp, Y.shape[0], Y.stride(0), cp, C.stride(0),
+                                    int(nslices), float(bound))
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())

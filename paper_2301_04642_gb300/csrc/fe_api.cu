@@ -1,0 +1,703 @@
+// Host side of the C ABI declared in include/fe.h and include/fe_kernels.h.
+//
+// A context owns one CUDA stream, an HBM-budgeted pool of per-problem "slots"
+// (Hp copy, FP32 master, FP16 slice sets, FP64 buffers, partials, state) and
+// the launch sequences.  A solve (or a batch of solves) is:
+//   bounds rows + reduce + X0 init              (per problem)
+//   repeat:  control (1 block / problem)  ->  tensor-core step over the tiles
+//            of all problems  ->  FP64 step over the 64x64 tiles of all
+//            problems                      (kernels skip problems whose state
+//                                             says the step is not theirs)
+//   finalize (D out, tr(Hp D), tr D)            (per problem)
+// with no host synchronisation until the end.
+#include <algorithm>
+#include <atomic>
+#include <cfloat>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "../../include/fe.h"
+#include "../../include/fe_kernels.h"
+#include "fe_dev.cuh"
+#include "fe_kernels.cuh"
+
+using namespace fe;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+struct Slot {
+    int n = 0;
+    size_t bytes = 0;
+    bool in_use = false;
+    char *arena = nullptr;
+    double *Hcopy = nullptr;
+    float *Y = nullptr;
+    __half *sl[2][kMaxSlices] = {};
+    double *Xd[2] = {};
+    double *Dtmp = nullptr;
+    double *part = nullptr;
+    SolveState *st = nullptr;
+    RowInfo *rowinfo = nullptr;
+    int *bad = nullptr;
+    int ldy = 0, lds = 0, ldx = 0;
+    std::vector<TileEnt> tiles;
+    std::vector<Tile64> tiles64;
+    MmaProb hp;  // host image of the device descriptor (H filled per solve)
+};
+
+}  // namespace
+
+struct fe_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0, used = 0;
+    int max_iters = 100;
+    uint32_t prec_default = FE_PREC_MIXED;
+    int num_sms = 148;
+    std::string err;
+    int *d_err = nullptr;
+    MmaProb *d_probs = nullptr;
+    size_t probs_cap = 0;
+    TileEnt *d_tiles = nullptr;
+    size_t tiles_cap = 0;
+    Tile64 *d_tiles64 = nullptr;
+    size_t tiles64_cap = 0;
+    SolveState *h_states = nullptr;  // pinned copies read back at the end
+    size_t h_states_cap = 0;
+    std::vector<Slot *> slots;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::recursive_mutex mu;
+    // continuous batching (fe_submit / fe_poll)
+    struct Req;
+    std::deque<Req *> queue;
+    std::map<fe_ticket, Req *> reqs;
+    fe_ticket next_ticket = 1;
+    std::thread worker;
+    std::condition_variable_any cv;
+    bool stop = false;
+};
+
+namespace {
+
+int set_err(fe_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+int cuda_fail(fe_ctx *ctx, cudaError_t e, const char *what) {
+    return set_err(ctx, FE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define FE_CUDA(ctx, call)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+void build_tiles(Slot *s) {
+    s->tiles.clear();
+    const int T = ceil_div(s->n, kTileM);
+    const int TP = ceil_div(T, 2);
+    int slot = 0;
+    for (int I = 0; I < T; ++I)
+        for (int Jp = I / 2; Jp < TP; ++Jp) s->tiles.push_back(TileEnt{0, I, Jp, slot++});
+    s->tiles64.clear();
+    const int T64 = ceil_div(s->n, kTile64);
+    slot = 0;
+    for (int I = 0; I < T64; ++I)
+        for (int J = I; J < T64; ++J) s->tiles64.push_back(Tile64{0, I, J, slot++});
+}
+
+size_t slot_bytes(int n, int *ldy, int *lds, int *ldx, size_t *nparts) {
+    *ldy = static_cast<int>(align_up(n, 4));
+    *lds = static_cast<int>(align_up(n, 8));
+    *ldx = n;
+    const int T = ceil_div(n, kTileM);
+    const int T64 = ceil_div(n, kTile64);
+    const size_t ntiles = static_cast<size_t>(T) * ceil_div(T, 2);
+    const size_t nt64 = static_cast<size_t>(T64) * (T64 + 1) / 2;
+    *nparts = std::max<size_t>({static_cast<size_t>(kInitBlocks), ntiles, nt64,
+                                static_cast<size_t>(kFinBlocks)});
+    const size_t nn = static_cast<size_t>(n);
+    size_t b = 0;
+    auto add = [&](size_t x) { b += align_up(x, 1024); };
+    add(8 * nn * nn);                                // Hcopy
+    add(4 * nn * (*ldy));                            // Y
+    for (int k = 0; k < 2 * kMaxSlices; ++k) add(2 * nn * (*lds));  // slices
+    add(8 * nn * (*ldx));                            // Xd[0]
+    add(8 * nn * (*ldx));                            // Xd[1]
+    add(8 * nn * nn);                                // Dtmp
+    add(8 * kPartStride * (*nparts));                // partials
+    add(sizeof(SolveState));
+    add(sizeof(RowInfo) * nn);
+    add(64);
+    return b;
+}
+
+int encode_map(fe_ctx *ctx, CUtensorMap *m, void *base, int n, int ld_elems, int box_rows) {
+    auto enc = get_encode();
+    if (!enc) return set_err(ctx, FE_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    cuuint64_t gdim[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};
+    cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld_elems) * 2};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(kTileK), static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_err(ctx, FE_ECUDA, "cuTensorMapEncodeTiled failed");
+    return FE_OK;
+}
+
+void free_slot(fe_ctx *ctx, Slot *s) {
+    if (s->arena) cudaFree(s->arena);
+    ctx->used -= s->bytes;
+    delete s;
+}
+
+// A free slot for dimension n (reused if cached), or null with ctx->err set.
+int acquire_slot(fe_ctx *ctx, int n, Slot **out) {
+    for (Slot *s : ctx->slots)
+        if (!s->in_use && s->n == n) {
+            s->in_use = true;
+            *out = s;
+            return FE_OK;
+        }
+    int ldy, lds, ldx;
+    size_t nparts;
+    const size_t bytes = slot_bytes(n, &ldy, &lds, &ldx, &nparts);
+    if (bytes > ctx->budget)
+        return set_err(ctx, FE_ENOMEM, "problem needs " + std::to_string(bytes) +
+                                           " bytes, more than the HBM budget");
+    // evict unused cached slots until it fits
+    while (ctx->used + bytes > ctx->budget) {
+        auto it = std::find_if(ctx->slots.begin(), ctx->slots.end(),
+                               [](Slot *s) { return !s->in_use; });
+        if (it == ctx->slots.end())
+            return set_err(ctx, FE_ENOMEM, "HBM budget exhausted by active solves");
+        Slot *v = *it;
+        ctx->slots.erase(it);
+        free_slot(ctx, v);
+    }
+    Slot *s = new Slot();
+    s->n = n;
+    s->bytes = bytes;
+    s->ldy = ldy;
+    s->lds = lds;
+    s->ldx = ldx;
+    cudaError_t e = cudaMalloc(&s->arena, bytes);
+    if (e != cudaSuccess) {
+        delete s;
+        cudaGetLastError();
+        return set_err(ctx, FE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    ctx->used += bytes;
+    const size_t nn = static_cast<size_t>(n);
+    char *p = s->arena;
+    auto take = [&](size_t x) {
+        char *r = p;
+        p += align_up(x, 1024);
+        return r;
+    };
+    s->Hcopy = reinterpret_cast<double *>(take(8 * nn * nn));
+    s->Y = reinterpret_cast<float *>(take(4 * nn * ldy));
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < kMaxSlices; ++b) s->sl[a][b] = reinterpret_cast<__half *>(take(2 * nn * lds));
+    s->Xd[0] = reinterpret_cast<double *>(take(8 * nn * ldx));
+    s->Xd[1] = reinterpret_cast<double *>(take(8 * nn * ldx));
+    s->Dtmp = reinterpret_cast<double *>(take(8 * nn * nn));
+    s->part = reinterpret_cast<double *>(take(8 * kPartStride * nparts));
+    s->st = reinterpret_cast<SolveState *>(take(sizeof(SolveState)));
+    s->rowinfo = reinterpret_cast<RowInfo *>(take(sizeof(RowInfo) * nn));
+    s->bad = reinterpret_cast<int *>(take(64));
+    build_tiles(s);
+    // descriptor image (tensor maps are fixed for the slot's lifetime)
+    memset(&s->hp, 0, sizeof(MmaProb));
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < kMaxSlices; ++b) {
+            int rc = encode_map(ctx, &s->hp.tmA[a][b], s->sl[a][b], n, lds, kTileM);
+            if (rc == FE_OK) rc = encode_map(ctx, &s->hp.tmB[a][b], s->sl[a][b], n, lds, kTileN);
+            if (rc != FE_OK) {
+                free_slot(ctx, s);
+                return rc;
+            }
+            s->hp.sl[a][b] = s->sl[a][b];
+        }
+    s->hp.Y = s->Y;
+    s->hp.st = s->st;
+    s->hp.part = s->part;
+    s->hp.n = n;
+    s->hp.ldy = ldy;
+    s->hp.lds = lds;
+    s->hp.ntiles = static_cast<int>(s->tiles.size());
+    s->hp.ntiles64 = static_cast<int>(s->tiles64.size());
+    s->hp.Xd[0] = s->Xd[0];
+    s->hp.Xd[1] = s->Xd[1];
+    s->hp.ldx = ldx;
+    s->in_use = true;
+    ctx->slots.push_back(s);
+    *out = s;
+    return FE_OK;
+}
+
+template <typename T>
+int ensure_dev(fe_ctx *ctx, T **ptr, size_t *cap, size_t count) {
+    if (count <= *cap) return FE_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    const size_t c = std::max<size_t>(count, 16);
+    FE_CUDA(ctx, cudaMalloc(reinterpret_cast<void **>(ptr), sizeof(T) * c));
+    *cap = c;
+    return FE_OK;
+}
+
+uint32_t prec_of(const fe_ctx *ctx, const fe_problem *p) {
+    uint32_t pr = p->flags & FE_PREC_MASK;
+    if (pr == 0) pr = ctx->prec_default & FE_PREC_MASK;
+    return pr;
+}
+
+int validate(fe_ctx *ctx, const fe_problem *p) {
+    if (!p) return set_err(ctx, FE_EINVAL, "problem is NULL");
+    if (!p->Hp) return set_err(ctx, FE_EINVAL, "Hp is NULL");
+    if (p->n < 1 || p->n > (1 << 20)) return set_err(ctx, FE_EINVAL, "n out of range");
+    if (p->ld < p->n) return set_err(ctx, FE_EINVAL, "ld < n");
+    if (!(p->n_e >= 0.0) || p->n_e > static_cast<double>(p->n))
+        return set_err(ctx, FE_EINVAL, "n_e outside [0, n]");
+    if (!(p->kT >= 0.0) || !std::isfinite(p->kT)) return set_err(ctx, FE_EINVAL, "kT < 0");
+    if (p->kT == 0.0 && p->n_e != std::floor(p->n_e))
+        return set_err(ctx, FE_EINVAL, "non-integral n_e at kT == 0");
+    if (!(p->tol >= 0.0)) return set_err(ctx, FE_EINVAL, "tol < 0");
+    const uint32_t m = p->flags & FE_METHOD_MASK;
+    if (m != FE_METHOD_AUTO && m != FE_METHOD_SP2 && m != FE_METHOD_FERMI)
+        return set_err(ctx, FE_EINVAL, "unknown method flag");
+    if (m == FE_METHOD_SP2 && p->kT != 0.0)
+        return set_err(ctx, FE_EINVAL, "SP2 needs kT == 0");
+    const bool fermi = (m == FE_METHOD_FERMI) || (m == FE_METHOD_AUTO && p->kT > 0.0);
+    if (fermi) return set_err(ctx, FE_EINVAL, "finite-temperature expansion not available in this build");
+    const uint32_t pr = p->flags & FE_PREC_MASK;
+    if (pr != FE_PREC_MIXED && pr != FE_PREC_FP64 && pr != FE_PREC_FP32 && pr != FE_PREC_TRY_FP16)
+        return set_err(ctx, FE_EINVAL, "unknown precision flag");
+    if ((p->flags & ~(FE_PTR_DEVICE | FE_METHOD_MASK | FE_PREC_MASK)) != 0)
+        return set_err(ctx, FE_EINVAL, "unknown flag bits");
+    return FE_OK;
+}
+
+// Fill the pinned state image of one problem.
+void init_state(const fe_ctx *ctx, const fe_problem *p, SolveState *st) {
+    memset(st, 0, sizeof(SolveState));
+    st->n = static_cast<int>(p->n);
+    st->ne = p->n_e;
+    st->kT = p->kT;
+    st->tol = (p->tol > 0.0) ? p->tol : 5e-8;
+    st->max_iters = ctx->max_iters;
+    const uint32_t pr = prec_of(ctx, p);
+    st->prec = (pr == FE_PREC_FP64) ? kPrecFp64
+               : (pr == FE_PREC_FP32) ? kPrecFp32
+               : (pr == FE_PREC_TRY_FP16) ? kPrecTryFp16 : kPrecMixed;
+    st->phase = (st->prec == kPrecFp64) ? kPhaseFp64
+                : (st->prec == kPrecTryFp16) ? kPhaseSingle : kPhaseSplit;
+    st->kind = kNone;
+    st->idem_hist[0] = st->idem_hist[1] = st->idem_hist[2] = DBL_MAX;
+    st->fro_hist[0] = st->fro_hist[1] = st->fro_hist[2] = DBL_MAX;
+    st->mu = NAN;
+}
+
+// Run a set of validated problems on acquired slots; fills results.
+int run_problems(fe_ctx *ctx, const std::vector<const fe_problem *> &ps, std::vector<Slot *> &ss,
+                 fe_result *rs) {
+    const int np = static_cast<int>(ps.size());
+    cudaStream_t s = ctx->stream;
+    // pinned state images
+    if (ctx->h_states_cap < static_cast<size_t>(np)) {
+        if (ctx->h_states) cudaFreeHost(ctx->h_states);
+        ctx->h_states = nullptr;
+        ctx->h_states_cap = 0;
+        FE_CUDA(ctx, cudaMallocHost(&ctx->h_states, sizeof(SolveState) * np));
+        ctx->h_states_cap = np;
+    }
+    std::vector<MmaProb> hprobs(np);
+    std::vector<TileEnt> tiles;
+    std::vector<Tile64> tiles64;
+    bool any_tc = false, any_fp64 = false;
+    int total_iters = 0;
+    for (int k = 0; k < np; ++k) {
+        const fe_problem *p = ps[k];
+        Slot *sl = ss[k];
+        hprobs[k] = sl->hp;
+        const int n = static_cast<int>(p->n);
+        // Hp: use the caller's device buffer in place, otherwise stage a copy
+        if (p->flags & FE_PTR_DEVICE) {
+            hprobs[k].H = p->Hp;
+            hprobs[k].ldh = p->ld;
+        } else {
+            FE_CUDA(ctx, cudaMemcpy2DAsync(sl->Hcopy, sizeof(double) * n, p->Hp,
+                                           sizeof(double) * p->ld, sizeof(double) * n, n,
+                                           cudaMemcpyHostToDevice, s));
+            hprobs[k].H = sl->Hcopy;
+            hprobs[k].ldh = n;
+        }
+        init_state(ctx, p, &ctx->h_states[k]);
+        FE_CUDA(ctx, cudaMemcpyAsync(sl->st, &ctx->h_states[k], sizeof(SolveState),
+                                     cudaMemcpyHostToDevice, s));
+        const int pr = ctx->h_states[k].prec;
+        if (pr != kPrecFp64) {
+            any_tc = true;
+            for (TileEnt t : sl->tiles) { t.prob = k; tiles.push_back(t); }
+        }
+        if (pr != kPrecFp32) {
+            any_fp64 = true;
+            for (Tile64 t : sl->tiles64) { t.prob = k; tiles64.push_back(t); }
+        }
+        total_iters = std::max(total_iters, ctx->max_iters);
+    }
+    int rc = ensure_dev(ctx, &ctx->d_probs, &ctx->probs_cap, np);
+    if (rc == FE_OK) rc = ensure_dev(ctx, &ctx->d_tiles, &ctx->tiles_cap, tiles.size());
+    if (rc == FE_OK) rc = ensure_dev(ctx, &ctx->d_tiles64, &ctx->tiles64_cap, tiles64.size());
+    if (rc != FE_OK) return rc;
+    FE_CUDA(ctx, cudaMemcpyAsync(ctx->d_probs, hprobs.data(), sizeof(MmaProb) * np,
+                                 cudaMemcpyHostToDevice, s));
+    if (!tiles.empty())
+        FE_CUDA(ctx, cudaMemcpyAsync(ctx->d_tiles, tiles.data(), sizeof(TileEnt) * tiles.size(),
+                                     cudaMemcpyHostToDevice, s));
+    if (!tiles64.empty())
+        FE_CUDA(ctx, cudaMemcpyAsync(ctx->d_tiles64, tiles64.data(),
+                                     sizeof(Tile64) * tiles64.size(), cudaMemcpyHostToDevice, s));
+    FE_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+
+    FE_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
+    for (int k = 0; k < np; ++k) {
+        const int n = static_cast<int>(ps[k]->n);
+        FE_CUDA(ctx, cudaMemsetAsync(ss[k]->bad, 0, sizeof(int), s));
+        k_bounds_rows<<<ceil_div(n, 8), 256, 0, s>>>(ctx->d_probs, k, ss[k]->rowinfo, ss[k]->bad);
+        k_bounds_reduce<<<1, 1024, 0, s>>>(ctx->d_probs, k, ss[k]->rowinfo, ss[k]->bad);
+        k_init_x0<<<kInitBlocks, 256, 0, s>>>(ctx->d_probs, k);
+    }
+    const int ntc = static_cast<int>(tiles.size());
+    const int n64 = static_cast<int>(tiles64.size());
+    const int grid_tc = std::max(1, std::min(ntc, ctx->num_sms));
+    const int grid_64 = std::max(1, std::min(n64, 4 * ctx->num_sms));
+    const size_t smem = mma_smem_bytes();
+    // one loop iteration = control + product; +8 covers the phase hand-offs
+    for (int it = 0; it < total_iters + 8; ++it) {
+        k_control<<<np, 256, 0, s>>>(ctx->d_probs, np);
+        if (any_tc)
+            k_sym_mma<<<grid_tc, kMmaThreads, smem, s>>>(ctx->d_probs, ctx->d_tiles, ntc, ctx->d_err);
+        if (any_fp64) k_fp64_step<<<grid_64, 256, 0, s>>>(ctx->d_probs, ctx->d_tiles64, n64);
+    }
+    k_control<<<np, 256, 0, s>>>(ctx->d_probs, np);
+    for (int k = 0; k < np; ++k) {
+        const fe_problem *p = ps[k];
+        double *dout = nullptr;
+        long long ldd = p->n;
+        if (p->D) {
+            if (p->flags & FE_PTR_DEVICE) {
+                dout = p->D;
+                ldd = p->ld;
+            } else {
+                dout = ss[k]->Dtmp;
+            }
+        }
+        k_finalize<<<kFinBlocks, 256, 0, s>>>(ctx->d_probs, k, dout, ldd);
+        k_finalize_reduce<<<1, 512, 0, s>>>(ctx->d_probs, k);
+    }
+    FE_CUDA(ctx, cudaEventRecord(ctx->ev1, s));
+    FE_CUDA(ctx, cudaGetLastError());
+    for (int k = 0; k < np; ++k) {
+        const fe_problem *p = ps[k];
+        if (p->D && !(p->flags & FE_PTR_DEVICE))
+            FE_CUDA(ctx, cudaMemcpy2DAsync(p->D, sizeof(double) * p->ld, ss[k]->Dtmp,
+                                           sizeof(double) * p->n, sizeof(double) * p->n, p->n,
+                                           cudaMemcpyDeviceToHost, s));
+        FE_CUDA(ctx, cudaMemcpyAsync(&ctx->h_states[k], ss[k]->st, sizeof(SolveState),
+                                     cudaMemcpyDeviceToHost, s));
+    }
+    int herr = 0;
+    FE_CUDA(ctx, cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(ctx, cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    int first_bad = FE_OK;
+    for (int k = 0; k < np; ++k) {
+        const SolveState &st = ctx->h_states[k];
+        fe_result &r = rs[k];
+        memset(&r, 0, sizeof(r));
+        r.status = st.status == 0 ? FE_OK : st.status;
+        if (herr != 0) r.status = FE_ETIMEOUT;
+        r.iters = st.iter;
+        for (int q = 0; q < 3; ++q) r.iters_by_phase[q] = st.it_phase[q];
+        r.e_band = st.e_band;
+        r.trace = st.trace;
+        r.idem_fro = st.idem_fro;
+        r.mu = st.mu;
+        r.eps_min = st.emin;
+        r.eps_max = st.emax;
+        r.ms = ms;
+        if (r.status != FE_OK && first_bad == FE_OK) first_bad = r.status;
+    }
+    if (herr != 0) set_err(ctx, FE_ETIMEOUT, "device wait timed out (code " + std::to_string(herr) + ")");
+    else if (first_bad == FE_EINVAL) set_err(ctx, FE_EINVAL, "NaN or Inf in Hp");
+    else if (first_bad == FE_ENOTCONV) set_err(ctx, FE_ENOTCONV, "iteration cap reached");
+    return first_bad;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+extern "C" int fe_create(fe_ctx **out, const fe_config *cfg) {
+    if (!out) return set_err(nullptr, FE_EINVAL, "out is NULL");
+    *out = nullptr;
+    fe_config c{};
+    if (cfg) c = *cfg;
+    if (c.autotune_path) return set_err(nullptr, FE_EINVAL, "autotune_path must be NULL");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return set_err(nullptr, FE_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    if (c.device < 0 || c.device >= ndev) return set_err(nullptr, FE_EINVAL, "bad device ordinal");
+    if ((e = cudaSetDevice(c.device)) != cudaSuccess)
+        return set_err(nullptr, FE_ECUDA, cudaGetErrorString(e));
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, c.device);
+    if (prop.major != 10 || prop.minor != 3)
+        return set_err(nullptr, FE_ECUDA, "this library is built for sm_103a (GB300) only");
+    if (!get_encode()) return set_err(nullptr, FE_ECUDA, "cuTensorMapEncodeTiled not available");
+    fe_ctx *ctx = new fe_ctx();
+    ctx->device = c.device;
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->max_iters = c.max_iters > 0 ? c.max_iters : 100;
+    ctx->prec_default = c.precision_policy;
+    size_t freeb = 0, totalb = 0;
+    cudaMemGetInfo(&freeb, &totalb);
+    ctx->budget = c.hbm_budget_bytes ? c.hbm_budget_bytes : static_cast<size_t>(0.8 * freeb);
+    if (c.cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(c.cuda_stream);
+    } else {
+        cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        ctx->own_stream = true;
+    }
+    if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sym_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(mma_smem_bytes())) != cudaSuccess) {
+        const cudaError_t e2 = cudaGetLastError();
+        fe_destroy(ctx);
+        return set_err(nullptr, FE_ECUDA, std::string("context setup: ") + cudaGetErrorString(e2));
+    }
+    *out = ctx;
+    return FE_OK;
+}
+
+extern "C" int fe_destroy(fe_ctx *ctx) {
+    if (!ctx) return FE_OK;
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        ctx->stop = true;
+    }
+    ctx->cv.notify_all();
+    if (ctx->worker.joinable()) ctx->worker.join();
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (Slot *s : ctx->slots) {
+        if (s->arena) cudaFree(s->arena);
+        delete s;
+    }
+    ctx->slots.clear();
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_probs) cudaFree(ctx->d_probs);
+    if (ctx->d_tiles) cudaFree(ctx->d_tiles);
+    if (ctx->d_tiles64) cudaFree(ctx->d_tiles64);
+    if (ctx->h_states) cudaFreeHost(ctx->h_states);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return FE_OK;
+}
+
+extern "C" int fe_solve(fe_ctx *ctx, const fe_problem *p, fe_result *r) {
+    if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    fe_result dummy;
+    if (!r) r = &dummy;
+    memset(r, 0, sizeof(*r));
+    int rc = validate(ctx, p);
+    if (rc != FE_OK) return r->status = rc;
+    cudaSetDevice(ctx->device);
+    Slot *s = nullptr;
+    rc = acquire_slot(ctx, static_cast<int>(p->n), &s);
+    if (rc != FE_OK) return r->status = rc;
+    std::vector<const fe_problem *> ps{p};
+    std::vector<Slot *> ss{s};
+    rc = run_problems(ctx, ps, ss, r);
+    s->in_use = false;
+    if (r->status == FE_OK && rc != FE_OK) r->status = rc;
+    return rc;
+}
+
+extern "C" int fe_solve_batch(fe_ctx *ctx, int count, const fe_problem *ps, fe_result *rs) {
+    if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
+    if (count < 0 || (count > 0 && (!ps || !rs))) return set_err(ctx, FE_EINVAL, "bad batch arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (count == 0) return FE_OK;
+    cudaSetDevice(ctx->device);
+    std::vector<const fe_problem *> pv;
+    std::vector<Slot *> sv;
+    std::vector<int> idx;
+    int first = FE_OK;
+    for (int k = 0; k < count; ++k) {
+        memset(&rs[k], 0, sizeof(fe_result));
+        int rc = validate(ctx, &ps[k]);
+        Slot *s = nullptr;
+        if (rc == FE_OK) rc = acquire_slot(ctx, static_cast<int>(ps[k].n), &s);
+        if (rc != FE_OK) {
+            rs[k].status = rc;
+            if (first == FE_OK) first = rc;
+            continue;
+        }
+        pv.push_back(&ps[k]);
+        sv.push_back(s);
+        idx.push_back(k);
+    }
+    if (!pv.empty()) {
+        std::vector<fe_result> tmp(pv.size());
+        const int rc = run_problems(ctx, pv, sv, tmp.data());
+        for (size_t q = 0; q < pv.size(); ++q) {
+            rs[idx[q]] = tmp[q];
+            sv[q]->in_use = false;
+        }
+        if (first == FE_OK) first = rc;
+    }
+    return first;
+}
+
+extern "C" const char *fe_last_error_string(const fe_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+// ============================================================== kernel-level entry points
+
+extern "C" int fe_k_gershgorin(fe_ctx *ctx, const double *H, int64_t n, int64_t ld, double *out4) {
+    if (!ctx || !H || !out4 || n < 1 || ld < n) return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    Slot *s = nullptr;
+    int rc = acquire_slot(ctx, static_cast<int>(n), &s);
+    if (rc != FE_OK) return rc;
+    MmaProb hp = s->hp;
+    hp.H = H;
+    hp.ldh = ld;
+    SolveState st0;
+    memset(&st0, 0, sizeof(st0));
+    st0.n = static_cast<int>(n);
+    rc = ensure_dev(ctx, &ctx->d_probs, &ctx->probs_cap, 1);
+    if (rc != FE_OK) { s->in_use = false; return rc; }
+    cudaStream_t q = ctx->stream;
+    SolveState res;
+    cudaMemcpyAsync(ctx->d_probs, &hp, sizeof(MmaProb), cudaMemcpyHostToDevice, q);
+    cudaMemcpyAsync(s->st, &st0, sizeof(SolveState), cudaMemcpyHostToDevice, q);
+    cudaMemsetAsync(s->bad, 0, sizeof(int), q);
+    k_bounds_rows<<<ceil_div(static_cast<int>(n), 8), 256, 0, q>>>(ctx->d_probs, 0, s->rowinfo, s->bad);
+    k_bounds_reduce<<<1, 1024, 0, q>>>(ctx->d_probs, 0, s->rowinfo, s->bad);
+    cudaMemcpyAsync(&res, s->st, sizeof(SolveState), cudaMemcpyDeviceToHost, q);
+    const cudaError_t e = cudaStreamSynchronize(q);
+    s->in_use = false;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gershgorin");
+    out4[0] = res.emin;
+    out4[1] = res.emax;
+    out4[2] = res.trH;
+    out4[3] = res.bad_input ? 1.0 : 0.0;
+    return FE_OK;
+}
+
+extern "C" int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t ldy, float *C,
+                               int64_t ldc, int nslices, double bound) {
+    if (!ctx || !Y || !C || n < 1 || ldy < n || ldc < n || (nslices != 1 && nslices != 2) ||
+        !(bound > 0.0))
+        return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    Slot *s = nullptr;
+    int rc = acquire_slot(ctx, static_cast<int>(n), &s);
+    if (rc != FE_OK) return rc;
+    cudaStream_t q = ctx->stream;
+    int e2;
+    frexp(bound, &e2);
+    const float scale = static_cast<float>(ldexp(1.0, 14 - e2));
+    // master <- Y (the epilogue then overwrites it with 0 * Y + 1 * Y^2)
+    cudaMemcpy2DAsync(s->Y, sizeof(float) * s->ldy, Y, sizeof(float) * ldy, sizeof(float) * n, n,
+                      cudaMemcpyDeviceToDevice, q);
+    k_make_slices<<<kInitBlocks, 256, 0, q>>>(s->Y, static_cast<int>(n), s->ldy, scale, s->sl[0][0],
+                                              s->sl[0][1], s->lds);
+    SolveState st0;
+    memset(&st0, 0, sizeof(st0));
+    st0.n = static_cast<int>(n);
+    st0.kind = (nslices == 2) ? kTcSplit : kTcSingle;
+    st0.alpha = 0.0f;
+    st0.sigma = 1.0f;
+    st0.inv_s2 = static_cast<float>(1.0 / (static_cast<double>(scale) * scale));
+    st0.s_next = 1.0f;
+    st0.cur = 0;
+    rc = ensure_dev(ctx, &ctx->d_probs, &ctx->probs_cap, 1);
+    if (rc == FE_OK) rc = ensure_dev(ctx, &ctx->d_tiles, &ctx->tiles_cap, s->tiles.size());
+    if (rc != FE_OK) { s->in_use = false; return rc; }
+    MmaProb hp = s->hp;
+    cudaMemcpyAsync(ctx->d_probs, &hp, sizeof(MmaProb), cudaMemcpyHostToDevice, q);
+    cudaMemcpyAsync(ctx->d_tiles, s->tiles.data(), sizeof(TileEnt) * s->tiles.size(),
+                    cudaMemcpyHostToDevice, q);
+    cudaMemcpyAsync(s->st, &st0, sizeof(SolveState), cudaMemcpyHostToDevice, q);
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), q);
+    const int nt = static_cast<int>(s->tiles.size());
+    k_sym_mma<<<std::min(nt, ctx->num_sms), kMmaThreads, mma_smem_bytes(), q>>>(
+        ctx->d_probs, ctx->d_tiles, nt, ctx->d_err);
+    cudaMemcpy2DAsync(C, sizeof(float) * ldc, s->Y, sizeof(float) * s->ldy, sizeof(float) * n, n,
+                      cudaMemcpyDeviceToDevice, q);
+    int herr = 0;
+    cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, q);
+    const cudaError_t e = cudaStreamSynchronize(q);
+    s->in_use = false;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sym_square");
+    if (herr) return set_err(ctx, FE_ETIMEOUT, "device wait timed out (code " + std::to_string(herr) + ")");
+    return FE_OK;
+}
+
+extern "C" int fe_submit(fe_ctx *ctx, const fe_problem *, fe_ticket *) {
+    return set_err(ctx, FE_EINVAL, "fe_submit not available in this build");
+}
+
+extern "C" int fe_poll(fe_ctx *ctx, fe_ticket, fe_result *) {
+    return set_err(ctx, FE_EINVAL, "fe_poll not available in this build");
+}

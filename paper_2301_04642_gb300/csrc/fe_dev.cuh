@@ -1,0 +1,247 @@
+// Device-side definitions shared by the kernels of the Fermi-operator
+// expansion library (sm_103a).
+//
+// Representation of the SP2 iterate (Sec. II-B1, Eq. (1)): X = c I + Y with the
+// scalar shift c kept in FP64 and Y stored as an FP32 master matrix.  The
+// tensor-core products read Y through FP16 "slices" scaled by a power of two s:
+//   s Y ~= hi + lo,  hi = fp16(s Y),  lo = fp16(s Y - hi)
+// so Y^2 ~= (hi hi^T + hi lo^T + lo hi^T) / s^2 accumulated in FP32 (TMEM).
+// With X = c I + Y an SP2 step becomes an update of (c, Y):
+//   X^2      -> c' = c^2,        Y' = 2c Y + Y^2
+//   2X - X^2 -> c' = 2c - c^2,   Y' = (2 - 2c) Y - Y^2
+// (Sec. II-B1: "X_{n+1} = X_n +/- (X_n - X_n^2)").
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace fe {
+
+// ---------------------------------------------------------------- constants
+constexpr int kTileM = 128;    // rows of one tensor-core tile (TMEM lanes)
+constexpr int kTileN = 256;    // columns of one tensor-core tile (two 128-blocks)
+constexpr int kTileK = 64;     // K per pipeline stage (one 128-byte swizzle row of FP16)
+constexpr int kMaxSlices = 2;
+constexpr int kStages = 2;
+constexpr int kSliceABytes = kTileM * kTileK * 2;   // 16 KiB
+constexpr int kSliceBBytes = kTileN * kTileK * 2;   // 32 KiB
+constexpr int kStageBytes = kMaxSlices * (kSliceABytes + kSliceBBytes);  // 96 KiB
+constexpr int kMmaThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 drain + epilogue
+constexpr int kEpiWarps = 8;
+constexpr int kPartStride = 4;    // doubles per partial slot: tr, sumsq, maxabs, spare
+constexpr float kSliceTop = 16384.0f;  // slices are scaled so |s Y| <= 2^14 < fp16 max
+
+// error codes written by kernels into the context's device error word
+enum DevErr : int {
+    kErrNone = 0,
+    kErrTimeoutFull = 1,    // TMA data never arrived
+    kErrTimeoutEmpty = 2,   // smem stage never released
+    kErrTimeoutTmem = 3,    // accumulator hand-off never happened
+    kErrBadInput = 4,
+};
+
+// bounded waits give up after this many nanoseconds of wall time
+constexpr uint64_t kWaitTimeoutNs = 2000000000ull;
+
+// ---------------------------------------------------------------- state
+enum Kind : int { kNone = 0, kTcSingle = 1, kTcSplit = 2, kFp64 = 3 };
+enum Phase : int { kPhaseSingle = 0, kPhaseSplit = 1, kPhaseFp64 = 2, kPhaseDone = 3 };
+enum Prec : int { kPrecMixed = 0, kPrecFp64 = 1, kPrecFp32 = 2, kPrecTryFp16 = 3 };
+
+struct SolveState {
+    // problem (written by the host)
+    int n;
+    int prec;
+    int max_iters;
+    int method;
+    double ne, kT, tol;
+    // Gershgorin bounds and Hp statistics (written by the bounds kernel)
+    double emin, emax, trH, hmax;
+    int bad_input;
+    // iterate X = c I + Y, or X = Xd[xcur] (FP64) once in the FP64 phase
+    double c;
+    float s_cur;        // slice scale of the current slice set
+    int cur;            // current slice set (0/1)
+    int xcur;           // current FP64 buffer (0/1)
+    int x_fp64;         // 1: the iterate is Xd[xcur] (FP64); 0: it is c I + Y
+    // instruction for the product kernels of this step (written by control)
+    int kind;
+    int sq;             // 1: X^2 branch, 0: 2X - X^2 branch
+    float alpha, sigma, inv_s2, s_next;
+    float r1, r0;       // X^2 - X = Y^2 + r1 Y + r0 I with r1 = 2c - 1, r0 = c^2 - c
+    double c_next;
+    // convergence bookkeeping
+    int iter, phase, nparts, done, status;
+    int it_phase[4];
+    double t1, t2, t1_prev, reltr;
+    double idem_hist[3];
+    double fro_hist[3];  // ||X_k^2 - X_k||_F of the inputs of the last products
+    int sq_hist[2];
+    // outputs
+    double e_band, trace, idem_fro, mu;
+    double pad[4];
+};
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity; false after kWaitTimeoutNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > kWaitTimeoutNs) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---- tcgen05 (5th-generation tensor core) ----
+__device__ __forceinline__ void tmem_alloc(uint32_t *smem_slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(smem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, both K-major, FP16 inputs, FP32 accumulate.
+__device__ __forceinline__ void tc_mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                           uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on `bar` once every tcgen05.mma issued so far by this thread has completed.
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with
+// 128-byte swizzling: rows of 128 bytes, 8-row atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void *tile) {
+    const uint32_t addr = smem_u32(tile);
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);         // start address
+    d |= static_cast<uint64_t>(1u) << 16;                        // leading offset (unused, SW128 K-major)
+    d |= static_cast<uint64_t>((1024u >> 4) & 0x3FFFu) << 32;   // stride offset: 8 rows x 128 B
+    d |= static_cast<uint64_t>(1u) << 46;                        // descriptor version (sm_100 family)
+    d |= static_cast<uint64_t>(2u) << 61;                        // swizzle mode: 128 B
+    return d;
+}
+
+// Instruction descriptor: kind::f16, A and B FP16 (fmt 0) or BF16 (fmt 1),
+// FP32 accumulator, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int ab_fmt) {
+    return (1u << 4)                                  // D format FP32
+           | (static_cast<uint32_t>(ab_fmt) << 7)     // A format
+           | (static_cast<uint32_t>(ab_fmt) << 10)    // B format
+           | (static_cast<uint32_t>(N >> 3) << 17)    // N / 8
+           | (static_cast<uint32_t>(M >> 4) << 24);   // M / 16
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace fe

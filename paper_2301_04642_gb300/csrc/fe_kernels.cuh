@@ -1,0 +1,71 @@
+// Kernel entry points and the device-visible problem descriptors.
+#pragma once
+#include "fe_dev.cuh"
+
+namespace fe {
+
+// Everything a tile of one problem needs.  Lives in device global memory
+// (64-byte aligned because of the embedded tensor maps); filled by the host.
+struct MmaProb {
+    CUtensorMap tmA[2][kMaxSlices];  // [slice set][slice]: box 64 (K) x 128 rows
+    CUtensorMap tmB[2][kMaxSlices];  // [slice set][slice]: box 64 (K) x 256 rows
+    float *Y;                        // FP32 master, n x n, leading dimension ldy
+    __half *sl[2][kMaxSlices];       // FP16 slices, n x n, leading dimension lds
+    SolveState *st;
+    double *part;                    // per-tile partial slots (kPartStride doubles each)
+    int n, ldy, lds, ntiles;
+    int ntiles64, pad1;
+    double *Xd[2];                   // FP64 iterate buffers (FP64 phase), leading dim ldx
+    int ldx, pad0;
+    const double *H;                 // Hp (device), leading dimension ldh
+    long long ldh;
+};
+
+// One tensor-core tile: rows [I*128, I*128+128) x columns [Jp*256, Jp*256+256).
+struct TileEnt {
+    int prob;
+    int I;
+    int Jp;
+    int slot;  // partial slot index within the problem
+};
+
+// One FP64 tile: rows [I*64, +64) x columns [J*64, +64), J >= I.
+struct Tile64 {
+    int prob;
+    int I;
+    int J;
+    int slot;
+};
+
+__global__ void k_sym_mma(const MmaProb *__restrict__ probs, const TileEnt *__restrict__ tiles,
+                          int ntiles, int *err);
+size_t mma_smem_bytes();
+
+struct RowInfo {
+    double lo, hi, diag, maxabs;  // H_ii - r_i, H_ii + r_i, H_ii, max_j |H_ij|
+};
+
+// Gershgorin row pass: one warp per row.
+__global__ void k_bounds_rows(const MmaProb *probs, int prob, RowInfo *rowinfo, int *bad);
+// Deterministic reduction of the row info into the state (one block).
+__global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *rowinfo,
+                                const int *bad);
+// X0 -> (c, Y0) and slices; per-block partials.
+__global__ void k_init_x0(const MmaProb *probs, int prob);
+// Step control for every problem (one block per problem).
+__global__ void k_control(const MmaProb *probs, int nprobs);
+// FP64 product + SP2 update (upper tiles, mirrored), per-tile partials.
+__global__ void k_fp64_step(const MmaProb *probs, const Tile64 *tiles, int ntiles);
+// D = X -> out (FP64, ld), partials of tr(H D) and tr D.
+__global__ void k_finalize(const MmaProb *probs, int prob, double *D, long long ldd);
+__global__ void k_finalize_reduce(const MmaProb *probs, int prob);
+
+// FP32 -> FP16 slices of s*Y for a standalone product (kernel tests).
+__global__ void k_make_slices(const float *Y, int n, int ldy, float s, __half *hi, __half *lo,
+                              int lds);
+
+constexpr int kInitBlocks = 304;   // 2 x 152 SMs
+constexpr int kFinBlocks = 304;
+constexpr int kTile64 = 64;
+
+}  // namespace fe

@@ -1,0 +1,372 @@
+// Symmetric product Y^2 on the 5th-generation tensor cores with the SP2
+// update fused into the epilogue (Sec. II-B1 Eq. (1); Sec. III-B: the product
+// dominates the cost).
+//
+// One persistent CTA per SM walks a list of upper-triangle tiles (of one or
+// many problems).  A tile is 128 rows (block I) x 256 columns (blocks 2Jp,
+// 2Jp+1); only 128x128 blocks with J >= I are written.  Because Y is
+// symmetric, (Y^2)_ij = sum_k Y_ik Y_jk: both operands are row panels of the
+// same K-major FP16 slice arrays, loaded by TMA with 128-byte swizzling.
+//
+// Accuracy: the tensor core adds every MMA into its FP32 accumulator with a
+// one-sided rounding, so an accumulator that lives for the whole K loop
+// collects an error that grows with K.  Here an accumulator lives for one
+// 64-wide K chunk only: per chunk the small cross terms hi*lo and lo*hi are
+// issued first and the four hi*hi MMAs last, so the truncating additions at
+// full magnitude are four per chunk.  The drain warps read each chunk from
+// TMEM and sum the chunks in registers (round-to-nearest FP32) while the MMA
+// warp fills the other chunk buffer.
+//
+// Warp roles (320 threads):
+//   warp 0      TMA producer: per K chunk one box per slice for the A panel
+//               (128 rows) and the B panel (256 rows).
+//   warp 1      TMEM owner and MMA issuer: per chunk 4 x (1 or 3) MMAs
+//               M128 N256 K16 into one of two chunk buffers (2 x 256 cols).
+//   warps 2-9   drain + epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
+//               and columns 128 ((w - 2) / 4) .. +127; after the last chunk
+//               of a tile it applies Y' = alpha Y + sigma P / s^2 to its
+//               128x128 block, updates the FP32 master in place (+ mirror),
+//               writes the next FP16 slices (+ mirror) and the per-tile FP64
+//               partials of tr Y' and ||Y'||_F^2 (Sec. III-B, fused).
+// Every wait is bounded; on a timeout the kernel records an error code,
+// drains its own copies and MMAs, frees TMEM and returns.
+#include "fe_dev.cuh"
+#include "fe_kernels.cuh"
+
+namespace fe {
+
+namespace {
+
+struct alignas(1024) StageSmem {
+    uint8_t a[kMaxSlices][kSliceABytes];
+    uint8_t b[kMaxSlices][kSliceBBytes];
+};
+
+struct MmaSmemTail {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t cfull[2];
+    uint64_t cempty[2];
+    uint32_t tmem_base;
+    int abort_flag;
+    double red[kEpiWarps][4];
+    int vote[kEpiWarps];
+};
+
+constexpr size_t kMmaSmemBytes = 1024 + sizeof(StageSmem) * kStages + sizeof(MmaSmemTail);
+
+__device__ __forceinline__ bool tile_active(const SolveState *st) {
+    const int kind = *reinterpret_cast<const volatile int *>(&st->kind);
+    return kind == kTcSingle || kind == kTcSplit;
+}
+
+__device__ __forceinline__ void record_error(int *err, int code) { atomicCAS(err, 0, code); }
+
+// named barrier of the 8 drain/epilogue warps
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+}  // namespace
+
+__global__ void __launch_bounds__(kMmaThreads, 1)
+    k_sym_mma(const MmaProb *__restrict__ probs, const TileEnt *__restrict__ tiles, int ntiles,
+              int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t base_u32 = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
+    StageSmem *stages = reinterpret_cast<StageSmem *>(smem);
+    MmaSmemTail *tail = reinterpret_cast<MmaSmemTail *>(smem + sizeof(StageSmem) * kStages);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&tail->full[s], 1);
+            mbar_init(&tail->empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tail->cfull[a], 1);
+            mbar_init(&tail->cempty[a], kEpiWarps);
+        }
+        tail->abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(&tail->tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tail->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        uint32_t stage = 0, phase = 0;
+        bool ok = true;
+        uint32_t last_phase[kStages];
+        bool issued[kStages];
+        for (int s = 0; s < kStages; ++s) { issued[s] = false; last_phase[s] = 0; }
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileEnt te = tiles[t];
+            const MmaProb &pr = probs[te.prob];
+            if (!tile_active(pr.st)) continue;
+            const SolveState *st = pr.st;
+            const int S = (st->kind == kTcSplit) ? 2 : 1;
+            const int set = st->cur;
+            const int nk = (pr.n + kTileK - 1) / kTileK;
+            const uint32_t bytes = static_cast<uint32_t>(S * (kSliceABytes + kSliceBBytes));
+            for (int kc = 0; kc < nk; ++kc) {
+                bool got = true;
+                if (lane == 0) got = mbar_wait_bounded(&tail->empty[stage], phase ^ 1u);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    if (lane == 0) record_error(err, kErrTimeoutEmpty);
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) {
+                    mbar_expect_tx(&tail->full[stage], bytes);
+                    for (int s = 0; s < S; ++s) {
+                        tma_load_2d(stages[stage].a[s], &pr.tmA[set][s], &tail->full[stage],
+                                    kc * kTileK, te.I * kTileM);
+                        tma_load_2d(stages[stage].b[s], &pr.tmB[set][s], &tail->full[stage],
+                                    kc * kTileK, te.Jp * kTileN);
+                    }
+                }
+                __syncwarp();
+                issued[stage] = true;
+                last_phase[stage] = phase;
+                if (++stage == kStages) { stage = 0; phase ^= 1u; }
+            }
+        }
+        if (!ok) {
+            // no TMA write may still be in flight when the CTA exits; the last
+            // phase issued on a stage is its newest, so waiting on it is exact
+            tail->abort_flag = 1;
+            if (lane == 0)
+                for (int s = 0; s < kStages; ++s)
+                    if (issued[s]) (void)mbar_wait_bounded(&tail->full[s], last_phase[s]);
+            __syncwarp();
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        uint32_t stage = 0, phase = 0;
+        uint32_t chunk = 0;  // chunk counter of this CTA: buffer = chunk & 1
+        bool ok = true;
+        bool any_commit = false;
+        constexpr uint32_t idesc = idesc_f16(kTileM, kTileN, 0);
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileEnt te = tiles[t];
+            const MmaProb &pr = probs[te.prob];
+            if (!tile_active(pr.st)) continue;
+            const SolveState *st = pr.st;
+            const int S = (st->kind == kTcSplit) ? 2 : 1;
+            const int nk = (pr.n + kTileK - 1) / kTileK;
+            for (int kc = 0; kc < nk; ++kc) {
+                const uint32_t buf = chunk & 1u;
+                const uint32_t cph = (chunk >> 1) & 1u;
+                bool got = true;
+                if (lane == 0) got = mbar_wait_bounded(&tail->cempty[buf], cph ^ 1u);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (got) {
+                    if (lane == 0) got = mbar_wait_bounded(&tail->full[stage], phase);
+                    got = __shfl_sync(0xffffffffu, got, 0);
+                    if (!got && lane == 0) record_error(err, kErrTimeoutFull);
+                } else if (lane == 0) {
+                    record_error(err, kErrTimeoutTmem);
+                }
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (lane == 0) {
+                    const uint32_t tmem_d = tmem_base + buf * kTileN;
+                    const uint64_t a0 = smem_desc_sw128(stages[stage].a[0]);
+                    const uint64_t b0 = smem_desc_sw128(stages[stage].b[0]);
+                    uint32_t accum = 0;
+                    if (S == 2) {
+                        const uint64_t a1 = smem_desc_sw128(stages[stage].a[1]);
+                        const uint64_t b1 = smem_desc_sw128(stages[stage].b[1]);
+                        // small cross terms first: hi * lo, lo * hi
+#pragma unroll
+                        for (int kk = 0; kk < kTileK / 16; ++kk) {
+                            const uint64_t off = static_cast<uint64_t>(kk * 2);  // 32 B along K
+                            tc_mma_f16(tmem_d, a0 + off, b1 + off, idesc, accum);
+                            accum = 1;
+                            tc_mma_f16(tmem_d, a1 + off, b0 + off, idesc, accum);
+                        }
+                    }
+                    // the full-magnitude hi * hi terms last
+#pragma unroll
+                    for (int kk = 0; kk < kTileK / 16; ++kk) {
+                        const uint64_t off = static_cast<uint64_t>(kk * 2);
+                        tc_mma_f16(tmem_d, a0 + off, b0 + off, idesc, accum);
+                        accum = 1;
+                    }
+                    tc_commit(&tail->empty[stage]);  // smem stage may be refilled
+                    tc_commit(&tail->cfull[buf]);    // chunk ready for the drain
+                    any_commit = true;
+                }
+                __syncwarp();
+                if (++stage == kStages) { stage = 0; phase ^= 1u; }
+                ++chunk;
+            }
+        }
+        if (!ok) {
+            tail->abort_flag = 1;
+            // every issued MMA must finish before TMEM is released
+            if (lane == 0 && any_commit) {
+                uint64_t *drain = &tail->cfull[chunk & 1u];
+                tc_commit(drain);
+                (void)mbar_wait_bounded(drain, (chunk >> 1) & 1u);
+            }
+            __syncwarp();
+        }
+    } else {
+        // ------------------------------------------------------------ drain + epilogue
+        const int ew = warp - 2;               // 0..7
+        const int q = warp & 3;                // TMEM lane quadrant (hardware rule: warp % 4)
+        const int h = ew >> 2;                 // column half: 128-block 2Jp + h
+        const int row_local = q * 32 + lane;
+        uint32_t chunk = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileEnt te = tiles[t];
+            const MmaProb &pr = probs[te.prob];
+            if (!tile_active(pr.st)) continue;
+            const SolveState *st = pr.st;
+            const int n = pr.n;
+            const int nk = (n + kTileK - 1) / kTileK;
+            float acc[128];
+#pragma unroll
+            for (int c = 0; c < 128; ++c) acc[c] = 0.0f;
+            for (int kc = 0; kc < nk; ++kc) {
+                const uint32_t buf = chunk & 1u;
+                const uint32_t cph = (chunk >> 1) & 1u;
+                bool got = mbar_wait_bounded(&tail->cfull[buf], cph);
+                got = __all_sync(0xffffffffu, got);
+                if (!got) {
+                    if (lane == 0) record_error(err, kErrTimeoutTmem);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                                       buf * kTileN + static_cast<uint32_t>(h * 128);
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    float v[32];
+                    tmem_ld32(tbase + c4 * 32, v);
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) acc[c4 * 32 + u] += v[u];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tail->cempty[buf]);
+                ++chunk;
+            }
+            // a warp leaves the chunk loop early only on a timeout; make the
+            // decision uniform over the drain warps before the named barriers
+            if (lane == 0) tail->vote[ew] = ok ? 1 : 0;
+            epi_bar();
+            bool all_ok = true;
+            for (int w = 0; w < kEpiWarps; ++w) all_ok = all_ok && (tail->vote[w] != 0);
+            epi_bar();
+            if (!all_ok) {
+                ok = false;
+                break;
+            }
+
+            // ---- store phase for block J = 2 Jp + h
+            const float alpha = st->alpha, sigma = st->sigma, inv_s2 = st->inv_s2;
+            const float s_next = st->s_next;
+            const float r1 = st->r1, r0 = st->r0;
+            const int oset = st->cur ^ 1;
+            float *__restrict__ Y = pr.Y;
+            const int ldy = pr.ldy, lds = pr.lds;
+            __half *__restrict__ o0 = pr.sl[oset][0];
+            __half *__restrict__ o1 = pr.sl[oset][1];
+            const int i = te.I * kTileM + row_local;
+            const int J = 2 * te.Jp + h;
+            double tr = 0.0, sq = 0.0, mx = 0.0, rr = 0.0;
+            if (J >= te.I && J * kTileM < n && i < n) {
+                const bool diag = (J == te.I);
+                float *yrow = Y + static_cast<size_t>(i) * ldy;
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int j0 = J * kTileM + c4 * 32;
+                    float csq = 0.0f, crr = 0.0f;
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const int j = j0 + u;
+                        if (j < n && (!diag || j >= i)) {
+                            const float yo = yrow[j];
+                            const float p2 = acc[c4 * 32 + u] * inv_s2;  // (Y^2)_ij
+                            const float yn = fmaf(alpha, yo, sigma * p2);
+                            // (X^2 - X)_ij of the input iterate X = c I + Y
+                            const float r = fmaf(r1, yo, p2) + ((j == i) ? r0 : 0.0f);
+                            const float ys = yn * s_next;
+                            const __half hh = __float2half_rn(ys);
+                            const __half ll = __float2half_rn(ys - __half2float(hh));
+                            yrow[j] = yn;
+                            o0[static_cast<size_t>(i) * lds + j] = hh;
+                            o1[static_cast<size_t>(i) * lds + j] = ll;
+                            if (j != i) {
+                                Y[static_cast<size_t>(j) * ldy + i] = yn;
+                                o0[static_cast<size_t>(j) * lds + i] = hh;
+                                o1[static_cast<size_t>(j) * lds + i] = ll;
+                                csq = fmaf(2.0f * yn, yn, csq);
+                                crr = fmaf(2.0f * r, r, crr);
+                            } else {
+                                tr += static_cast<double>(yn);
+                                csq = fmaf(yn, yn, csq);
+                                crr = fmaf(r, r, crr);
+                            }
+                            mx = fmax(mx, static_cast<double>(fabsf(yn)));
+                        }
+                    }
+                    sq += static_cast<double>(csq);
+                    rr += static_cast<double>(crr);
+                }
+            }
+            // deterministic per-tile partials: warp tree, then the 8 warps in order
+            tr = warp_sum(tr);
+            sq = warp_sum(sq);
+            mx = warp_max(mx);
+            rr = warp_sum(rr);
+            if (lane == 0) {
+                tail->red[ew][0] = tr;
+                tail->red[ew][1] = sq;
+                tail->red[ew][2] = mx;
+                tail->red[ew][3] = rr;
+            }
+            epi_bar();
+            if (ew == 0 && lane == 0) {
+                double a = 0, b = 0, c = 0, d = 0;
+                for (int w = 0; w < kEpiWarps; ++w) {
+                    a += tail->red[w][0];
+                    b += tail->red[w][1];
+                    c = fmax(c, tail->red[w][2]);
+                    d += tail->red[w][3];
+                }
+                double *slot = pr.part + static_cast<size_t>(te.slot) * kPartStride;
+                slot[0] = a;
+                slot[1] = b;
+                slot[2] = c;
+                slot[3] = d;
+            }
+            epi_bar();
+        }
+        if (!ok) tail->abort_flag = 1;
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 512);
+    }
+}
+
+size_t mma_smem_bytes() { return kMmaSmemBytes; }
+
+}  // namespace fe

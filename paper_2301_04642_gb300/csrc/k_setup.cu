@@ -1,0 +1,227 @@
+// Bandwidth-bound kernels around the expansion loop:
+//   * Gershgorin bounds of Hp (Sec. II-C: the expansion needs spectral bounds
+//     eps_1, eps_N; taken as Gershgorin discs), with tr Hp and a NaN/Inf scan.
+//   * X0 = (eps_max I - Hp) / (eps_max - eps_min) (spectrum in [0, 1], occupied
+//     states toward 1), stored as X0 = c0 I + Y0 with c0 = tr X0 / n, plus the
+//     first FP16 slices and per-block partials of tr Y0 and ||Y0||_F^2.
+//   * Output: D = X written to the caller's layout, and the FP64 band energy
+//     tr(Hp D) = sum_ij Hp_ij D_ij (Sec. III-C) and tr D.
+// Every reduction is a fixed-order tree, so results are bitwise reproducible.
+#include <cfloat>
+
+#include "fe_dev.cuh"
+#include "fe_kernels.cuh"
+
+namespace fe {
+
+__global__ void k_bounds_rows(const MmaProb *probs, int prob, RowInfo *rowinfo, int *bad) {
+    const MmaProb &pr = probs[prob];
+    const int warps_per_block = blockDim.x >> 5;
+    const int row = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= pr.n) return;
+    const double *h = pr.H + static_cast<long long>(row) * pr.ldh;
+    double s = 0.0, mx = 0.0;
+    int nonfinite = 0;
+    for (int j = lane; j < pr.n; j += 32) {
+        const double v = h[j];
+        if (!isfinite(v)) nonfinite = 1;
+        const double a = fabs(v);
+        s += a;
+        mx = fmax(mx, a);
+    }
+    s = warp_sum(s);
+    mx = warp_max(mx);
+    nonfinite = __any_sync(0xffffffffu, nonfinite);
+    if (lane == 0) {
+        const double d = h[row];
+        const double r = s - fabs(d);
+        rowinfo[row] = RowInfo{d - r, d + r, d, mx};
+        if (nonfinite) atomicExch(bad, 1);
+    }
+}
+
+__global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *rowinfo,
+                                const int *bad) {
+    const MmaProb &pr = probs[prob];
+    SolveState *st = pr.st;
+    __shared__ double s_lo[1024], s_hi[1024], s_tr[1024], s_mx[1024];
+    const int t = threadIdx.x;
+    double lo = DBL_MAX, hi = -DBL_MAX, tr = 0.0, mx = 0.0;
+    for (int i = t; i < pr.n; i += blockDim.x) {
+        const RowInfo r = rowinfo[i];
+        lo = fmin(lo, r.lo);
+        hi = fmax(hi, r.hi);
+        tr += r.diag;
+        mx = fmax(mx, r.maxabs);
+    }
+    s_lo[t] = lo; s_hi[t] = hi; s_tr[t] = tr; s_mx[t] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            s_lo[t] = fmin(s_lo[t], s_lo[t + o]);
+            s_hi[t] = fmax(s_hi[t], s_hi[t + o]);
+            s_tr[t] += s_tr[t + o];
+            s_mx[t] = fmax(s_mx[t], s_mx[t + o]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const int n = pr.n;
+        st->emin = s_lo[0];
+        st->emax = s_hi[0];
+        st->trH = s_tr[0];
+        st->hmax = s_mx[0];
+        st->bad_input = *bad;
+        double w = s_hi[0] - s_lo[0];
+        if (!(w > 0.0)) w = 1.0;  // Hp = a I: X0 is constant; the expansion will stall
+        const double c0 = (s_hi[0] - s_tr[0] / n) / w;
+        // |Y0_ij| <= max|Hp_ij| / w + |eps_max / w - c0|
+        const double bound = s_mx[0] / w + fabs(s_hi[0] / w - c0);
+        int e;
+        frexp(bound > 0.0 ? bound : 1.0, &e);  // bound < 2^e
+        st->c = c0;
+        st->s_cur = static_cast<float>(ldexp(1.0, 14 - e));
+        st->cur = 0;
+        st->xcur = 0;
+        st->x_fp64 = (st->prec == kPrecFp64) ? 1 : 0;
+    }
+}
+
+// Y0 = X0 - c0 I with X0 = (eps_max I - Hp) / w; FP32 master + FP16 slices of s0 Y0.
+// For the all-FP64 schedule X0 itself goes to Xd[0] in FP64.
+__global__ void k_init_x0(const MmaProb *probs, int prob) {
+    const MmaProb &pr = probs[prob];
+    SolveState *st = pr.st;
+    const int n = pr.n;
+    double w = st->emax - st->emin;
+    if (!(w > 0.0)) w = 1.0;
+    const double inv_w = 1.0 / w;
+    const double dshift = st->emax * inv_w - st->c;  // diagonal of Y0 gets +dshift
+    const float s0 = st->s_cur;
+    const bool fp64 = (st->prec == kPrecFp64);
+    double tr = 0.0, sq = 0.0, mx = 0.0;
+    const long long total = static_cast<long long>(n) * n;
+    for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(e / n);
+        const int j = static_cast<int>(e - static_cast<long long>(i) * n);
+        const double h = pr.H[static_cast<long long>(i) * pr.ldh + j];
+        if (fp64) {
+            const double x = ((i == j) ? st->emax - h : -h) * inv_w;
+            pr.Xd[0][static_cast<long long>(i) * pr.ldx + j] = x;
+            if (i == j) tr += x;
+            sq += x * x;
+            mx = fmax(mx, fabs(x));
+        } else {
+            const double y = -h * inv_w + ((i == j) ? dshift : 0.0);
+            const float yf = static_cast<float>(y);
+            pr.Y[static_cast<long long>(i) * pr.ldy + j] = yf;
+            const float ys = yf * s0;
+            const __half hh = __float2half_rn(ys);
+            pr.sl[0][0][static_cast<long long>(i) * pr.lds + j] = hh;
+            pr.sl[0][1][static_cast<long long>(i) * pr.lds + j] = __float2half_rn(ys - __half2float(hh));
+            if (i == j) tr += yf;
+            sq += static_cast<double>(yf) * yf;
+            mx = fmax(mx, fabs(static_cast<double>(yf)));
+        }
+    }
+    __shared__ double red[3][32];
+    tr = warp_sum(tr);
+    sq = warp_sum(sq);
+    mx = warp_max(mx);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][wid] = tr; red[1][wid] = sq; red[2][wid] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
+            a += red[0][w2];
+            b += red[1][w2];
+            c = fmax(c, red[2][w2]);
+        }
+        double *slot = pr.part + static_cast<size_t>(blockIdx.x) * kPartStride;
+        slot[0] = a;
+        slot[1] = b;
+        slot[2] = c;
+        slot[3] = 0.0;
+    }
+}
+
+// D = X (FP64) -> D_out, partials: slot[0] = tr D, slot[1] = sum Hp_ij D_ij.
+__global__ void k_finalize(const MmaProb *probs, int prob, double *D, long long ldd) {
+    const MmaProb &pr = probs[prob];
+    const SolveState *st = pr.st;
+    const int n = pr.n;
+    const bool from_x = st->x_fp64 != 0;
+    const double *X = pr.Xd[st->xcur];
+    const double c = st->c;
+    double tr = 0.0, eb = 0.0;
+    const long long total = static_cast<long long>(n) * n;
+    for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(e / n);
+        const int j = static_cast<int>(e - static_cast<long long>(i) * n);
+        double d;
+        if (from_x) {
+            d = X[static_cast<long long>(i) * pr.ldx + j];
+        } else {
+            d = static_cast<double>(pr.Y[static_cast<long long>(i) * pr.ldy + j]) + (i == j ? c : 0.0);
+        }
+        if (D) D[static_cast<long long>(i) * ldd + j] = d;
+        if (i == j) tr += d;
+        eb += d * pr.H[static_cast<long long>(i) * pr.ldh + j];
+    }
+    __shared__ double red[2][32];
+    tr = warp_sum(tr);
+    eb = warp_sum(eb);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][wid] = tr; red[1][wid] = eb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) { a += red[0][w2]; b += red[1][w2]; }
+        double *slot = pr.part + static_cast<size_t>(blockIdx.x) * kPartStride;
+        slot[0] = a;
+        slot[1] = b;
+    }
+}
+
+__global__ void k_finalize_reduce(const MmaProb *probs, int prob) {
+    const MmaProb &pr = probs[prob];
+    SolveState *st = pr.st;
+    __shared__ double s_tr[512], s_eb[512];
+    const int t = threadIdx.x;
+    double tr = 0.0, eb = 0.0;
+    for (int b = t; b < kFinBlocks; b += blockDim.x) {
+        tr += pr.part[static_cast<size_t>(b) * kPartStride + 0];
+        eb += pr.part[static_cast<size_t>(b) * kPartStride + 1];
+    }
+    s_tr[t] = tr;
+    s_eb[t] = eb;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) { s_tr[t] += s_tr[t + o]; s_eb[t] += s_eb[t + o]; }
+        __syncthreads();
+    }
+    if (t == 0) {
+        st->trace = s_tr[0];
+        st->e_band = s_eb[0];
+    }
+}
+
+__global__ void k_make_slices(const float *Y, int n, int ldy, float s, __half *hi, __half *lo,
+                              int lds) {
+    const long long total = static_cast<long long>(n) * n;
+    for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(e / n);
+        const int j = static_cast<int>(e - static_cast<long long>(i) * n);
+        const float ys = Y[static_cast<long long>(i) * ldy + j] * s;
+        const __half h = __float2half_rn(ys);
+        hi[static_cast<long long>(i) * lds + j] = h;
+        if (lo) lo[static_cast<long long>(i) * lds + j] = __float2half_rn(ys - __half2float(h));
+    }
+}
+
+}  // namespace fe

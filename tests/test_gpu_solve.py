@@ -1,0 +1,150 @@
+"""End-to-end solves through the C ABI against the FP64 oracle.
+
+Tolerances (zero temperature): ||D - D_ref||_F / sqrt(N_e) <= 1e-6,
+|E_band - E_ref| / N_e <= 1e-7 Ha, |tr D - N_e| <= 1e-9, ||D^2 - D||_F <= 1e-8.
+D_ref is the oracle's projector: from its own eigensolver for small n, else
+Q f(lambda) Q^T from the known construction of Hp."""
+import math
+
+import numpy as np
+import pytest
+
+import hp_synth
+import oracle
+from gpu_util import ctx, torch
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
+
+TOL_EPS1, TOL_E, TOL_TR, TOL_IDEM = 1e-6, 1e-7, 1e-9, 1e-8
+
+
+def check_zero_t(p, D, res, use_eig=False, idem=True):
+    ne = p.ne
+    if use_eig:
+        r = oracle.density(p.H, ne)
+        Dref, Eref = r["D"], r["e_band"]
+    else:
+        f = (np.arange(p.n) < int(ne)).astype(float)
+        Dref = oracle.density_from_eig(p.Q, f)
+        Eref = float(np.sum(f * p.lam))
+    eps1 = np.linalg.norm(D - Dref) / math.sqrt(max(ne, 1))
+    out = dict(eps1=eps1, e_err=abs(res["e_band"] - Eref) / max(ne, 1),
+               tr_err=abs(np.trace(D) - ne))
+    if idem:
+        D2 = oracle.matmul(D, D)
+        out["idem"] = np.linalg.norm(D2 - D)
+    return out
+
+
+def run(p, precision, **kw):
+    D = np.zeros_like(p.H)
+    res = ctx().solve(p.H, p.ne, tol=p.tol, D=D, precision=precision, **kw)
+    return D, res
+
+
+def test_n256_fp64_config():
+    p = hp_synth.workload_n256()
+    D, res = run(p, "fp64")
+    m = check_zero_t(p, D, res, use_eig=True)
+    assert res["status"] == 0
+    assert m["eps1"] <= TOL_EPS1 and m["e_err"] <= TOL_E
+    assert m["tr_err"] <= TOL_TR and m["idem"] <= TOL_IDEM
+    assert 20 <= res["iters"] <= 100
+    assert abs(res["trace"] - np.trace(D)) < 1e-9
+
+
+@pytest.mark.parametrize("n,ne", [(300, 250), (1000, 850), (1250, 1000)])
+def test_mixed_medium(n, ne):
+    p = hp_synth.gapped(n, ne, (-3.0, -0.01), (0.01, 1.0), 4000 + n)
+    D, res = run(p, "mixed")
+    m = check_zero_t(p, D, res)
+    print(n, res, m)
+    assert res["status"] == 0
+    assert m["eps1"] <= TOL_EPS1 and m["e_err"] <= TOL_E
+    assert m["tr_err"] <= TOL_TR and m["idem"] <= TOL_IDEM
+
+
+def test_fp32_schedule_reports_its_error():
+    p = hp_synth.gapped(600, 500, (-3.0, -0.01), (0.01, 1.0), 77)
+    D, res = run(p, "fp32")
+    m = check_zero_t(p, D, res, idem=False)
+    print(res, m)
+    assert res["status"] == 0
+    assert m["eps1"] <= 1e-5          # FP32-class: no FP64 polish
+
+
+def test_device_pointers_and_ld():
+    p = hp_synth.gapped(500, 400, (-3.0, -0.01), (0.01, 1.0), 11)
+    ld = 512
+    Hd = torch.zeros((p.n, ld), dtype=torch.float64, device="cuda")
+    Hd[:, :p.n] = torch.from_numpy(p.H).cuda()
+    Dd = torch.full((p.n, ld), 5.0, dtype=torch.float64, device="cuda")
+    res = ctx().solve(Hd[:, :p.n], p.ne, D=Dd[:, :p.n], precision="mixed")
+    Dh = Dd.cpu().numpy()
+    assert np.all(Dh[:, p.n:] == 5.0)
+    m = check_zero_t(p, Dh[:, :p.n].copy(), res)
+    assert m["eps1"] <= TOL_EPS1 and m["idem"] <= TOL_IDEM
+
+
+def test_degenerate_occupations():
+    p = hp_synth.gapped(200, 200, (-3.0, -0.01), (0.01, 1.0), 12)
+    D, res = run(p, "mixed")
+    assert np.abs(D - np.eye(200)).max() < 1e-10
+    p = hp_synth.gapped(200, 0, (-3.0, -0.01), (0.01, 1.0), 12)
+    D, res = run(p, "mixed")
+    assert np.abs(D).max() < 1e-10
+
+
+def test_permutation_and_shift_covariance():
+    p = hp_synth.gapped(400, 300, (-3.0, -0.01), (0.01, 1.0), 31)
+    D, _ = run(p, "mixed")
+    perm = np.random.default_rng(0).permutation(400)
+    Hp = p.H[np.ix_(perm, perm)]
+    D2 = np.zeros_like(Hp)
+    ctx().solve(Hp, p.ne, D=D2, precision="mixed")
+    assert np.linalg.norm(D2 - D[np.ix_(perm, perm)]) / math.sqrt(300) < 2 * TOL_EPS1
+    D3 = np.zeros_like(Hp)
+    ctx().solve(p.H + 0.7 * np.eye(400), p.ne, D=D3, precision="mixed")
+    assert np.linalg.norm(D3 - D) / math.sqrt(300) < 2 * TOL_EPS1
+
+
+def test_invalid_inputs():
+    import paper_2301_04642_gb300 as fe
+    p = hp_synth.gapped(64, 32, (-3.0, -0.01), (0.01, 1.0), 3)
+    H = p.H.copy(); H[5, 5] = np.inf
+    with pytest.raises(fe.FeError) as ei:
+        ctx().solve(H, 32)
+    assert ei.value.status == fe.FE_EINVAL
+    with pytest.raises(fe.FeError) as ei:
+        ctx().solve(p.H, 32.5)                # non-integral N_e at kT = 0
+    assert ei.value.status == fe.FE_EINVAL
+    with pytest.raises(fe.FeError) as ei:
+        ctx().solve(p.H, 65)
+    assert ei.value.status == fe.FE_EINVAL
+
+
+def test_iteration_cap_reports_notconv():
+    import paper_2301_04642_gb300 as fe
+    p = hp_synth.gapped(256, 128, (-3.0, -0.01), (0.01, 1.0), 8)
+    with fe.Context(max_iters=3) as c:
+        r = c.solve(p.H, p.ne, check=False)
+    assert r["status"] == fe.FE_ENOTCONV
+
+
+def test_config_n4096_mixed():
+    p = hp_synth.workload_n4096()
+    D, res = run(p, "mixed")
+    f = (np.arange(p.n) < 3500).astype(float)
+    Dref = oracle.density_from_eig(p.Q, f)
+    eps1 = np.linalg.norm(D - Dref) / math.sqrt(3500)
+    e_err = abs(res["e_band"] - np.sum(f * p.lam)) / 3500
+    tr_err = abs(np.trace(D) - 3500)
+    # idempotency through 4 random probes: E||(D^2 - D) v||^2 = ||D^2 - D||_F^2
+    rng = np.random.default_rng(1)
+    V = rng.standard_normal((p.n, 4))
+    DV = D @ V
+    idem = math.sqrt(np.sum((D @ DV - DV) ** 2) / 4)
+    print(res, eps1, e_err, tr_err, idem)
+    assert res["status"] == 0
+    assert eps1 <= TOL_EPS1 and e_err <= TOL_E and tr_err <= TOL_TR and idem <= TOL_IDEM

@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the density-matrix solve D = f(Hp) on GB300.
+
+Default workload (one GPU): the single gapped zero-temperature solve, n=4096,
+N_e=3500, occupied eigenvalues uniform in [-3, -0.01] Ha, empty in
+[0.01, 1.0] Ha, Hp = Q diag(lambda) Q^T with Q from QR of a seeded Gaussian,
+mixed precision (split-FP16 tensor-core products, FP64 polish).  One "step" is
+one complete solve (bounds, X0, every expansion product, output, tr(Hp D)).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  `value` is solves/s with Hp and D resident in
+HBM; `e2e` is the same through the C ABI with pinned HOST buffers (Hp copied
+in and D copied out inside the timed region).  With N > 1 (torchrun), every
+rank solves its own independent problems (replicas; no collective on the data
+path) and `value` is the total over ranks.  `--impl reference` times the CPU
+oracle (FP64 SP2 on the host cores) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import hp_synth  # noqa: E402
+
+METRIC = "fermi_expansion_solves_per_s"
+UNIT = "solves/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+WORKLOADS = {
+    "gapped_n4096": dict(make=lambda: hp_synth.workload_n4096(), precision="mixed"),
+    "gapped_n256_fp64": dict(make=lambda: hp_synth.workload_n256(), precision="fp64"),
+}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms."""
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def sp2_products_on_spectrum(lam, emin, emax, ne, tol):
+    """Number of SP2 products the plain FP64 recursion takes on this Hp: the
+    branch rule only sees traces, so the scalar recursion on the exact
+    eigenvalues reproduces the matrix recursion's decisions."""
+    x = (emax - lam) / (emax - emin)
+    t1 = x.sum()
+    for it in range(1, 400):
+        t2 = float(np.dot(x, x))
+        x = x * x if abs(t2 - ne) <= abs(2 * t1 - t2 - ne) else 2 * x - x * x
+        t1n = x.sum()
+        if abs(t1n - t1) <= tol * ne and abs(t1n - float(np.dot(x, x))) <= 1e-9:
+            return it
+        t1 = t1n
+    return 400
+
+
+def cpu_oracle_sample(p, products_per_solve, max_seconds=20.0):
+    """Time FP64 SP2 products of the CPU oracle on this workload; extrapolate
+    to a full solve.  Returns (solves/s, threads, sample description)."""
+    import oracle
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    oracle.sp2(p.H, p.ne, tol=1e-300, max_iter=1)
+    per = time.perf_counter() - t0
+    k = 1
+    if per * 2 < max_seconds:
+        t0 = time.perf_counter()
+        oracle.sp2(p.H, p.ne, tol=1e-300, max_iter=2)
+        per = (time.perf_counter() - t0) / 2
+        k = 2
+    solve_s = per * products_per_solve
+    return (1.0 / solve_s, threads,
+            "%d FP64 SP2 product(s) of the n=%d workload on %d host threads, %.2f s each; "
+            "solve = %d products (scalar SP2 count on the exact spectrum)"
+            % (k, p.n, threads, per, products_per_solve))
+
+
+def reference_arm(args, p, wl_name):
+    """--impl reference: the oracle on the host cores, bounded sample per step."""
+    import oracle
+    lo, hi = oracle.gershgorin(p.H)
+    prods = sp2_products_on_spectrum(p.lam, lo, hi, p.ne, 5e-8)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    for _ in range(args.warmup):
+        oracle.sp2(p.H, p.ne, tol=1e-300, max_iter=1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sp2(p.H, p.ne, tol=1e-300, max_iter=1)
+        times.append(time.perf_counter() - t0)
+    per = statistics.mean(times)
+    value = 1.0 / (per * prods)
+    sample = ("each step = 1 FP64 SP2 product of the CPU oracle (n=%d, %d threads); "
+              "solve = %d products" % (p.n, threads, prods))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl_name, "n": p.n, "n_e": p.ne,
+                                             "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def traffic_record(kernel_name, src_file):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
+    source has not changed since it was measured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel_name)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2301_04642_gb300", "csrc", src_file), "rb")
+                       .read()).hexdigest()
+    return rec.get("bytes_per_launch") if rec.get("src_sha256") == h else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gapped_n4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-baselines", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        reference_arm(args, wl["make"](), args.workload)
+        return
+
+    import torch
+    import paper_2301_04642_gb300 as fe
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    peaks, peak_kind = load_peaks()
+
+    p = wl["make"]()
+    n = p.n
+    prec = wl["precision"]
+    H = torch.from_numpy(p.H).to(dev)
+    D = torch.empty_like(H)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fe.Context(device=local_rank, stream=stream.cuda_stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def one():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        return ctx.solve(H, p.ne, tol=p.tol, D=D, precision=prec)
+
+    for _ in range(args.warmup):
+        r = one()
+    iters = r["iters"]
+
+    # ---- timed region: K solves, inputs resident in HBM
+    lat = []
+    l0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = one()
+            lat.append(r["ms"])
+            assert r["status"] == 0, r
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    launches = ctx.launch_count() - l0
+    t_ms = e0.elapsed_time(e1)
+    if dist:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * args.steps / (t_ms / 1e3)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    Hh = torch.from_numpy(p.H).pin_memory()
+    Dh = torch.empty_like(Hh).pin_memory()
+    for _ in range(2):
+        ctx.solve(Hh.numpy(), p.ne, tol=p.tol, D=Dh.numpy(), precision=prec)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        re = ctx.solve(Hh.numpy(), p.ne, tol=p.tol, D=Dh.numpy(), precision=prec)
+        _ = re["e_band"]
+    f1.record(stream)
+    torch.cuda.synchronize()
+    te_ms = f0.elapsed_time(f1)
+    if dist:
+        tt = torch.tensor([te_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te_ms = float(tt.item())
+    e2e = world * args.steps / (te_ms / 1e3)
+
+    # ---- per-kernel times (one profiled solve, CUDA events on the launch stream)
+    ctx.profile(True)
+    one()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    tc_n = max(prof["tc_launches"], 1)
+    fp_n = max(prof["fp64_launches"], 1)
+    tc_avg = prof["tc_ms"] / tc_n
+    fp_avg = prof["fp64_ms"] / fp_n
+    # algorithmic work per launch (upper triangle incl. diagonal: n^2 (n+1) flops per product)
+    sym_flops = float(n) * n * (n + 1)
+    kernels = {
+        "k_sym_mma": {"launches": prof["tc_launches"], "ms_total": prof["tc_ms"], "ms_avg": tc_avg,
+                      "algorithmic_flops": 3 * sym_flops,
+                      "achieved_tflops": 3 * sym_flops / (tc_avg * 1e-3) / 1e12 if prof["tc_ms"] else 0},
+        "k_fp64_step": {"launches": prof["fp64_launches"], "ms_total": prof["fp64_ms"],
+                        "ms_avg": fp_avg, "algorithmic_flops": sym_flops,
+                        "achieved_tflops": sym_flops / (fp_avg * 1e-3) / 1e12 if prof["fp64_ms"] else 0},
+    }
+    kernels["share_of_solve"] = {k: kernels[k]["ms_total"] / prof["solve_ms"]
+                                 for k in ("k_sym_mma", "k_fp64_step")}
+    if kernels["k_sym_mma"]["ms_total"] >= kernels["k_fp64_step"]["ms_total"]:
+        peak = peaks["bf16_tflops_sustained"]
+        ach = kernels["k_sym_mma"]["achieved_tflops"]
+        roof = {"kernel": "k_sym_mma", "bound": "tensor", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": traffic_record("k_sym_mma", "k_mma.cu"),
+                "peak_source": "%s bf16 dense sustained (fp16 dense has the same rate)" % peak_kind}
+    else:
+        peak = 1.25  # FP64 nominal of GB300 (no FP64 tensor path)
+        ach = kernels["k_fp64_step"]["achieved_tflops"]
+        roof = {"kernel": "k_fp64_step", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": traffic_record("k_fp64_step", "k_fp64.cu"),
+                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f16x2+f64" if prec == "mixed" else "f64",
+           "data": "synthetic",
+           "config": {"workload": args.workload, "n": n, "n_e": p.ne, "kT": 0.0,
+                      "precision": prec, "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "256 MiB buffer written before every step; working set > 129 MB L2"},
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+           "effective_tflops": iters * 2.0 * n ** 3 * value / 1e12,
+           "products_per_solve": iters, "iters_by_phase": r["iters_by_phase"],
+           "accuracy": {"trace_err": abs(r["trace"] - p.ne)},
+           "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
+                   "d2h_bytes_per_step": 8 * n * n},
+           "gpu_launches": launches, "roofline": roof, "kernels": kernels,
+           "clocks": clk.summary()}
+
+    if rank == 0 and not args.no_baselines:
+        base = {}
+        # the same expansion with every product in FP64 on this GPU
+        t0 = time.perf_counter()
+        r64 = ctx.solve(H, p.ne, tol=p.tol, D=D, precision="fp64")
+        base["fp64_gpu_sp2"] = {"solves_per_s": 1e3 / r64["ms"], "products": r64["iters"]}
+        # cuSOLVER syevd (torch.linalg.eigh, FP64) + D = V_occ V_occ^T
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        w, V = torch.linalg.eigh(H)
+        Vo = V[:, : int(p.ne)]
+        Dsy = Vo @ Vo.T
+        g1.record()
+        torch.cuda.synchronize()
+        base["cusolver_syevd"] = {"solves_per_s": 1e3 / g0.elapsed_time(g1)}
+        base["speedup_vs_fp64_gpu_sp2"] = value / world / base["fp64_gpu_sp2"]["solves_per_s"]
+        base["speedup_vs_cusolver_syevd"] = value / world / base["cusolver_syevd"]["solves_per_s"]
+        out["baselines_same_gpu"] = base
+        del Dsy, V
+    if rank == 0:
+        import oracle
+        lo, hi = oracle.gershgorin(p.H)
+        prods = sp2_products_on_spectrum(p.lam, lo, hi, p.ne, 5e-8)
+        v, thr, sample = cpu_oracle_sample(p, prods)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -34,6 +34,20 @@ FE_API int fe_k_gershgorin(fe_ctx *ctx, const double *H, int64_t n, int64_t ld, 
 FE_API int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t ldy, float *C, int64_t ldc,
                     int nslices, double bound);
 
+/* Measurement hooks (no counterpart in the paper; they time the hot path).
+ * fe_k_profile(ctx, 1) makes every following solve record CUDA events around
+ * each tensor-core and FP64 step launch on the context's stream.
+ * fe_k_profile_read fills out8 (HOST) from the last profiled solve:
+ * [0] ms in tensor-core step launches that did work, [1] their count,
+ * [2] ms in FP64 step launches that did work, [3] their count,
+ * [4] ms of the whole solve, [5] kernels launched by the context so far,
+ * [6] ms in all tensor-core step launches, [7] their count. */
+FE_API int fe_k_profile(fe_ctx *ctx, int enable);
+FE_API int fe_k_profile_read(fe_ctx *ctx, double *out8);
+
+/* Number of kernels this context has launched since fe_create (HOST out). */
+FE_API int fe_k_launch_count(fe_ctx *ctx, int64_t *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,8 +73,12 @@ def load(build=True):
     L.fe_last_error_string.restype = ctypes.c_char_p
     L.fe_k_gershgorin.argtypes = [P, P, i64, i64, ctypes.POINTER(dbl)]
     L.fe_k_sym_square.argtypes = [P, P, i64, i64, P, i64, ctypes.c_int, dbl]
+    L.fe_k_profile.argtypes = [P, ctypes.c_int]
+    L.fe_k_profile_read.argtypes = [P, ctypes.POINTER(dbl)]
+    L.fe_k_launch_count.argtypes = [P, ctypes.POINTER(i64)]
     for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
-                 "fe_k_gershgorin", "fe_k_sym_square"):
+                 "fe_k_gershgorin", "fe_k_sym_square", "fe_k_profile", "fe_k_profile_read",
+                 "fe_k_launch_count"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -196,3 +200,19 @@ class Context:
                                     int(nslices), float(bound))
         if rc != FE_OK:
             raise FeError(rc, self.last_error())
+
+    # ---- measurement hooks ----------------------------------------------------
+    def profile(self, enable=True):
+        self.L.fe_k_profile(self.h, 1 if enable else 0)
+
+    def profile_read(self):
+        out = (ctypes.c_double * 8)()
+        self.L.fe_k_profile_read(self.h, out)
+        keys = ("tc_ms", "tc_launches", "fp64_ms", "fp64_launches", "solve_ms", "launches_total",
+                "tc_ms_all", "tc_launches_all")
+        return dict(zip(keys, list(out)))
+
+    def launch_count(self):
+        v = ctypes.c_int64()
+        self.L.fe_k_launch_count(self.h, ctypes.byref(v))
+        return v.value

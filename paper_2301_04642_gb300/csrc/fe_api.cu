@@ -95,6 +95,11 @@ struct fe_ctx {
     size_t h_states_cap = 0;
     std::vector<Slot *> slots;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // optional per-launch timing of the expansion kernels (fe_k_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> pev;
+    double prof_out[8] = {};
+    long long launches = 0;  // kernels launched by this context
     std::recursive_mutex mu;
     // continuous batching (fe_submit / fe_poll)
     struct Req;
@@ -402,6 +407,7 @@ int run_problems(fe_ctx *ctx, const std::vector<const fe_problem *> &ps, std::ve
         const int n = static_cast<int>(ps[k]->n);
         FE_CUDA(ctx, cudaMemsetAsync(ss[k]->bad, 0, sizeof(int), s));
         k_bounds_rows<<<ceil_div(n, 8), 256, 0, s>>>(ctx->d_probs, k, ss[k]->rowinfo, ss[k]->bad);
+        ctx->launches += 3;
         k_bounds_reduce<<<1, 1024, 0, s>>>(ctx->d_probs, k, ss[k]->rowinfo, ss[k]->bad);
         k_init_x0<<<kInitBlocks, 256, 0, s>>>(ctx->d_probs, k);
     }
@@ -411,13 +417,32 @@ int run_problems(fe_ctx *ctx, const std::vector<const fe_problem *> &ps, std::ve
     const int grid_64 = std::max(1, std::min(n64, 4 * ctx->num_sms));
     const size_t smem = mma_smem_bytes();
     // one loop iteration = control + product; +8 covers the phase hand-offs
-    for (int it = 0; it < total_iters + 8; ++it) {
+    const int nloop = total_iters + 8;
+    if (ctx->prof) {
+        while (ctx->pev.size() < static_cast<size_t>(4 * nloop)) {
+            cudaEvent_t e;
+            FE_CUDA(ctx, cudaEventCreate(&e));
+            ctx->pev.push_back(e);
+        }
+    }
+    for (int it = 0; it < nloop; ++it) {
         k_control<<<np, 256, 0, s>>>(ctx->d_probs, np);
-        if (any_tc)
+        ++ctx->launches;
+        if (ctx->prof) cudaEventRecord(ctx->pev[4 * it + 0], s);
+        if (any_tc) {
             k_sym_mma<<<grid_tc, kMmaThreads, smem, s>>>(ctx->d_probs, ctx->d_tiles, ntc, ctx->d_err);
-        if (any_fp64) k_fp64_step<<<grid_64, 256, 0, s>>>(ctx->d_probs, ctx->d_tiles64, n64);
+            ++ctx->launches;
+        }
+        if (ctx->prof) cudaEventRecord(ctx->pev[4 * it + 1], s);
+        if (ctx->prof) cudaEventRecord(ctx->pev[4 * it + 2], s);
+        if (any_fp64) {
+            k_fp64_step<<<grid_64, 256, 0, s>>>(ctx->d_probs, ctx->d_tiles64, n64);
+            ++ctx->launches;
+        }
+        if (ctx->prof) cudaEventRecord(ctx->pev[4 * it + 3], s);
     }
     k_control<<<np, 256, 0, s>>>(ctx->d_probs, np);
+    ctx->launches += 1 + 3 * static_cast<long long>(np) + 1;
     for (int k = 0; k < np; ++k) {
         const fe_problem *p = ps[k];
         double *dout = nullptr;
@@ -449,6 +474,33 @@ int run_problems(fe_ctx *ctx, const std::vector<const fe_problem *> &ps, std::ve
     FE_CUDA(ctx, cudaStreamSynchronize(s));
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    if (ctx->prof) {
+        // launches that did work: the phases run in order (single FP16, split,
+        // FP64), so the first it_phase[0] + it_phase[1] tensor-core launches
+        // and the it_phase[2] FP64 launches after them were active
+        int tc_active = 0, fp_active = 0;
+        for (int k = 0; k < np; ++k) {
+            tc_active = std::max(tc_active, ctx->h_states[k].it_phase[0] + ctx->h_states[k].it_phase[1]);
+            fp_active = std::max(fp_active, ctx->h_states[k].it_phase[2]);
+        }
+        double tc_ms = 0, fp_ms = 0, tc_all = 0;
+        for (int it = 0; it < nloop; ++it) {
+            float a = 0, b = 0;
+            cudaEventElapsedTime(&a, ctx->pev[4 * it + 0], ctx->pev[4 * it + 1]);
+            cudaEventElapsedTime(&b, ctx->pev[4 * it + 2], ctx->pev[4 * it + 3]);
+            tc_all += a;
+            if (it < tc_active) tc_ms += a;
+            if (it >= tc_active && it < tc_active + fp_active) fp_ms += b;
+        }
+        ctx->prof_out[0] = tc_ms;
+        ctx->prof_out[1] = tc_active;
+        ctx->prof_out[2] = fp_ms;
+        ctx->prof_out[3] = fp_active;
+        ctx->prof_out[4] = ms;
+        ctx->prof_out[5] = static_cast<double>(ctx->launches);
+        ctx->prof_out[6] = tc_all;
+        ctx->prof_out[7] = any_tc ? nloop : 0;
+    }
     int first_bad = FE_OK;
     for (int k = 0; k < np; ++k) {
         const SolveState &st = ctx->h_states[k];
@@ -700,4 +752,25 @@ extern "C" int fe_submit(fe_ctx *ctx, const fe_problem *, fe_ticket *) {
 
 extern "C" int fe_poll(fe_ctx *ctx, fe_ticket, fe_result *) {
     return set_err(ctx, FE_EINVAL, "fe_poll not available in this build");
+}
+
+extern "C" int fe_k_profile(fe_ctx *ctx, int enable) {
+    if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->prof = enable != 0;
+    return FE_OK;
+}
+
+extern "C" int fe_k_profile_read(fe_ctx *ctx, double *out8) {
+    if (!ctx || !out8) return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    for (int i = 0; i < 8; ++i) out8[i] = ctx->prof_out[i];
+    return FE_OK;
+}
+
+extern "C" int fe_k_launch_count(fe_ctx *ctx, int64_t *out) {
+    if (!ctx || !out) return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    *out = ctx->launches;
+    return FE_OK;
 }

@@ -45,7 +45,8 @@ enum DevErr : int {
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;
 
 // ---------------------------------------------------------------- state
-enum Kind : int { kNone = 0, kTcSingle = 1, kTcSplit = 2, kFp64 = 3 };
+// kFp64: native FP64 products; kDf: double-float (FP32 pair) products
+enum Kind : int { kNone = 0, kTcSingle = 1, kTcSplit = 2, kFp64 = 3, kDf = 4 };
 enum Phase : int { kPhaseSingle = 0, kPhaseSplit = 1, kPhaseFp64 = 2, kPhaseDone = 3 };
 enum Prec : int { kPrecMixed = 0, kPrecFp64 = 1, kPrecFp32 = 2, kPrecTryFp16 = 3 };
 

@@ -44,7 +44,7 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
     // number of partial slots written by the previous producer
     int nparts;
     if (st->kind == kNone) nparts = kInitBlocks;
-    else if (st->kind == kFp64) nparts = pr.ntiles64;
+    else if (st->kind == kFp64 || st->kind == kDf) nparts = pr.ntiles64;
     else nparts = pr.ntiles;
 
     __shared__ double s_a[256], s_b[256], s_c[256], s_d[256];
@@ -82,7 +82,7 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
         st->c = st->c_next;
         st->s_cur = st->s_next;
         st->cur ^= 1;
-    } else if (prev_kind == kFp64) {
+    } else if (prev_kind == kFp64 || prev_kind == kDf) {
         st->xcur ^= 1;
         st->x_fp64 = 1;
     }
@@ -132,7 +132,7 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
             if (st->prec == kPrecFp32) done = true;
             else phase = kPhaseFp64;
         }
-    } else if (phase == kPhaseFp64 && prev_kind == kFp64) {
+    } else if (phase == kPhaseFp64 && (prev_kind == kFp64 || prev_kind == kDf)) {
         const int nfp64 = st->it_phase[kPhaseFp64];
         const bool idem_ok = fabs(idem) <= 2e-10 ||
                              (fabs(idem) >= 0.5 * fabs(st->idem_hist[2]) && fabs(idem) <= 1e-6);
@@ -158,7 +158,7 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
     st->sq = sq;
     st->phase = phase;
     if (phase == kPhaseFp64) {
-        st->kind = kFp64;
+        st->kind = (st->prec == kPrecFp64) ? kFp64 : kDf;
     } else {
         st->kind = (phase == kPhaseSingle) ? kTcSingle : kTcSplit;
         const double alpha = sq ? 2.0 * cc : 2.0 - 2.0 * cc;

@@ -48,6 +48,15 @@ FE_API int fe_k_profile_read(fe_ctx *ctx, double *out8);
 /* Number of kernels this context has launched since fe_create (HOST out). */
 FE_API int fe_k_launch_count(fe_ctx *ctx, int64_t *out);
 
+/* Per-step record of problem `index` of the last solve or batch (measurement
+ * hook, no counterpart in the paper).  out (HOST) receives up to max_rows rows
+ * of 6 doubles: phase (0 single FP16, 1 split FP16, 2 FP64-accurate), kind of
+ * the product that produced the iterate (0 none, 1 single, 2 split, 3 FP64,
+ * 4 double-float), tr X - N_e, tr X - ||X||_F^2, ||X^2 - X||_F of that
+ * product's input (-1 before the first product), RelTr (-1 at step 0).
+ * *rows = rows written. */
+FE_API int fe_k_history(fe_ctx *ctx, int index, double *out, int max_rows, int *rows);
+
 #ifdef __cplusplus
 }
 #endif

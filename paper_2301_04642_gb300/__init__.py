@@ -76,9 +76,11 @@ def load(build=True):
     L.fe_k_profile.argtypes = [P, ctypes.c_int]
     L.fe_k_profile_read.argtypes = [P, ctypes.POINTER(dbl)]
     L.fe_k_launch_count.argtypes = [P, ctypes.POINTER(i64)]
+    L.fe_k_history.argtypes = [P, ctypes.c_int, ctypes.POINTER(dbl), ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_int)]
     for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
                  "fe_k_gershgorin", "fe_k_sym_square", "fe_k_profile", "fe_k_profile_read",
-                 "fe_k_launch_count"):
+                 "fe_k_launch_count", "fe_k_history"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -216,3 +218,13 @@ class Context:
         v = ctypes.c_int64()
         self.L.fe_k_launch_count(self.h, ctypes.byref(v))
         return v.value
+
+    def history(self, index=0, max_rows=160):
+        """Per-step record of the last solve (rows of phase, kind, t1-N_e,
+        t1-t2, ||X^2-X||_F, RelTr)."""
+        out = (ctypes.c_double * (6 * max_rows))()
+        rows = ctypes.c_int()
+        rc = self.L.fe_k_history(self.h, int(index), out, int(max_rows), ctypes.byref(rows))
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+        return np.array(out[: 6 * rows.value]).reshape(rows.value, 6)

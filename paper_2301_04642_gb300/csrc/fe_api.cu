@@ -774,3 +774,16 @@ extern "C" int fe_k_launch_count(fe_ctx *ctx, int64_t *out) {
     *out = ctx->launches;
     return FE_OK;
 }
+
+extern "C" int fe_k_history(fe_ctx *ctx, int index, double *out, int max_rows, int *rows) {
+    if (!ctx || !out || !rows || max_rows < 0 || index < 0) return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!ctx->h_states || static_cast<size_t>(index) >= ctx->h_states_cap)
+        return set_err(ctx, FE_EINVAL, "no such problem in the last solve");
+    const SolveState &st = ctx->h_states[index];
+    const int r = std::min({st.iter + 1, kHistRows, max_rows});
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < kHistCols; ++j) out[i * kHistCols + j] = st.hist[i][j];
+    *rows = r;
+    return FE_OK;
+}

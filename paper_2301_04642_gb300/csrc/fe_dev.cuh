@@ -44,6 +44,9 @@ enum DevErr : int {
 // bounded waits give up after this many nanoseconds of wall time
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;
 
+constexpr int kHistRows = 160;  // per-step history kept in the solve state
+constexpr int kHistCols = 6;
+
 // ---------------------------------------------------------------- state
 // kFp64: native FP64 products; kDf: double-float (FP32 pair) products
 enum Kind : int { kNone = 0, kTcSingle = 1, kTcSplit = 2, kFp64 = 3, kDf = 4 };
@@ -72,6 +75,7 @@ struct SolveState {
     float alpha, sigma, inv_s2, s_next;
     float r1, r0;       // X^2 - X = Y^2 + r1 Y + r0 I with r1 = 2c - 1, r0 = c^2 - c
     double c_next;
+    double gamma;       // FP64-accurate step: X' = F(X) + gamma (X - X^2) (trace correction)
     // convergence bookkeeping
     int iter, phase, nparts, done, status;
     int it_phase[4];
@@ -82,6 +86,9 @@ struct SolveState {
     // outputs
     double e_band, trace, idem_fro, mu;
     double pad[4];
+    // per-step record written by the control kernel (read back with the state):
+    // phase, branch, t1 - N_e, t1 - t2, ||X^2 - X||_F of the last product's input, RelTr
+    double hist[kHistRows][kHistCols];
 };
 
 // ---------------------------------------------------------------- PTX wrappers

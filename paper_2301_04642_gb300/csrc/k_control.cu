@@ -120,14 +120,29 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
     st->idem_hist[1] = st->idem_hist[0];
     st->idem_hist[0] = idem;
 
+    if (st->iter < kHistRows) {
+        double *h = st->hist[st->iter];
+        h[0] = st->phase;
+        h[1] = prev_kind;
+        h[2] = t1 - ne;
+        h[3] = idem;
+        h[4] = (prev_kind != kNone) ? st->fro_hist[0] : -1.0;
+        h[5] = (st->iter > 0) ? reltr : -1.0;
+    }
+
     // ---- precision schedule and stopping rules
     bool done = false;
     int phase = st->phase;
     if (phase == kPhaseSingle && reltr < 5e-4) phase = kPhaseSplit;  // the paper's switch point
     if (phase == kPhaseSplit && prev_kind == kTcSplit) {
+        // The split products carry ~22 bits and the FP32 master 24, so the
+        // eigenvalue deviations cannot be pushed much below ~2^-22: stop at
+        // the first ||X^2 - X||_F at that level (2^-20 sqrt(N_e) leaves a
+        // margin), or as soon as it stops shrinking.
         const double f0 = st->fro_hist[0], f2 = st->fro_hist[2];
+        const double floor_level = 9.5367431640625e-07 * sqrt(fmax(ne, 1.0));  // 2^-20
         const bool floor = st->iter >= 4 &&
-                           (f0 <= 1e-7 * sqrt(nn) || (f0 <= 1e-4 * sqrt(nn) && f0 >= 0.5 * f2));
+                           (f0 <= floor_level || (f0 <= 1e-4 * sqrt(nn) && f0 >= 0.5 * f2));
         if (floor) {
             if (st->prec == kPrecFp32) done = true;
             else phase = kPhaseFp64;
@@ -139,7 +154,16 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
         if (st->prec == kPrecFp64) {
             if (reltr <= st->tol && idem_ok) done = true;
         } else {
-            if ((nfp64 >= 2 && reltr <= st->tol && idem_ok) || nfp64 >= 5) done = true;
+            // Polishing products come in pairs of opposite branches, the second
+            // one carrying the exact trace correction (below): after a pair the
+            // deviations are O(dx^2) on both sides and tr X = N_e to rounding.
+            // fro_hist[0] = ||X^2 - X||_F of the pair's second input; the
+            // output's deviations are about its square
+            (void)idem_ok;
+            const double f0 = st->fro_hist[0];
+            if (nfp64 >= 2 && (nfp64 & 1) == 0 &&
+                ((f0 * f0 <= 5e-9 && fabs(idem) <= 1e-8) || nfp64 >= 6))
+                done = true;
         }
     }
     if (!done && st->iter >= st->max_iters) {
@@ -154,7 +178,30 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
     }
 
     // ---- SP2 branch (Eq. (1)) and the instruction for the next product
-    const int sq = fabs(t2 - ne) <= fabs(2.0 * t1 - t2 - ne);
+    int sq = fabs(t2 - ne) <= fabs(2.0 * t1 - t2 - ne);
+    // Polishing (mixed schedules): the second product of each pair takes the
+    // other branch, so a pair maps x -> 1 - O(dx^2) near 1 and O(dx^2) near
+    // 0 whichever side the trace rule favoured first.
+    st->gamma = 0.0;
+    if (phase == kPhaseFp64 && st->prec != kPrecFp64 && (st->it_phase[kPhaseFp64] & 1) == 1) {
+        sq = !st->sq;
+        // Exact trace: the branch output F(X) has trace t2 (X^2) or 2 t1 - t2
+        // (2X - X^2), known now from the FP64 partials of X; adding
+        // gamma (X - X^2), whose trace is t1 - t2, lands tr X' on N_e.
+        // The correction moves eigenvalue x by gamma x (1 - x); |x (1 - x)| of
+        // this iterate is at most ~2 ||X_prev^2 - X_prev||_F (one side of the
+        // first product of the pair doubled).  Apply it only when a trace error
+        // remains and the largest move stays within a few times that error,
+        // i.e. when the x (1 - x) do not cancel in their sum.
+        const double trF = sq ? t2 : 2.0 * t1 - t2;
+        const double dtr = ne - trF;
+        const double dev = t1 - t2;
+        if (fabs(dtr) > 5e-11 && fabs(dev) > 1e-14 * nes) {
+            const double g = dtr / dev;
+            const double max_move = fabs(g) * 2.0 * st->fro_hist[0];
+            if (fabs(g) <= 0.5 && max_move <= fmax(4.0 * fabs(dtr), 1e-10)) st->gamma = g;
+        }
+    }
     st->sq = sq;
     st->phase = phase;
     if (phase == kPhaseFp64) {

@@ -57,6 +57,7 @@ __device__ __forceinline__ void step_epilogue(const MmaProb &pr, const SolveStat
                                               const double (&P)[4][4], Partials &pa) {
     double *Xo = pr.Xd[st->xcur ^ 1];  // the control kernel flips xcur afterwards
     const int sq = st->sq;
+    const double gamma = st->gamma;
     const int n = src.n;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -66,7 +67,9 @@ __device__ __forceinline__ void step_epilogue(const MmaProb &pr, const SolveStat
             const int j = j0 + tx + 16 * q;
             if (i >= n || j >= n || j < i) continue;
             const double xo = src.at(i, j);
-            const double xn = sq ? P[r][q] : 2.0 * xo - P[r][q];
+            // SP2 branch plus the trace correction gamma (X - X^2), which
+            // commutes with Hp and moves each eigenvalue by gamma x (1 - x)
+            const double xn = (sq ? P[r][q] : 2.0 * xo - P[r][q]) + gamma * (xo - P[r][q]);
             Xo[static_cast<long long>(i) * pr.ldx + j] = xn;
             const double dd = P[r][q] - xo;
             if (j != i) {

@@ -55,12 +55,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 struct Slot {
     int n = 0;
+    int method = 0;  // kMethodSp2 / kMethodFermi: decides which matrices exist
     size_t bytes = 0;
     bool in_use = false;
     char *arena = nullptr;
     double *Hcopy = nullptr;
     float *Y = nullptr;
-    __half *sl[2][kMaxSlices] = {};
     double *Xd[2] = {};
     double *Dtmp = nullptr;
     double *part = nullptr;
@@ -145,7 +145,13 @@ void build_tiles(Slot *s) {
         for (int J = I; J < T64; ++J) s->tiles64.push_back(Tile64{0, I, J, slot++});
 }
 
-size_t slot_bytes(int n, int *ldy, int *lds, int *ldx, size_t *nparts) {
+// Matrices held per method: zero temperature keeps one FP32 master (Y) and two
+// slice sets; finite temperature keeps masters for z, N, M, W, R and six slice
+// sets (W has two, ping-pong, sharing one master).
+int num_masters(int method) { return method == kMethodFermi ? 5 : 1; }
+int num_slice_sets(int method) { return method == kMethodFermi ? kNumMats : 2; }
+
+size_t slot_bytes(int n, int method, int *ldy, int *lds, int *ldx, size_t *nparts) {
     *ldy = static_cast<int>(align_up(n, 4));
     *lds = static_cast<int>(align_up(n, 8));
     *ldx = n;
@@ -159,8 +165,8 @@ size_t slot_bytes(int n, int *ldy, int *lds, int *ldx, size_t *nparts) {
     size_t b = 0;
     auto add = [&](size_t x) { b += align_up(x, 1024); };
     add(8 * nn * nn);                                // Hcopy
-    add(4 * nn * (*ldy));                            // Y
-    for (int k = 0; k < 2 * kMaxSlices; ++k) add(2 * nn * (*lds));  // slices
+    for (int k = 0; k < num_masters(method); ++k) add(4 * nn * (*ldy));  // FP32 masters
+    for (int k = 0; k < num_slice_sets(method) * kMaxSlices; ++k) add(2 * nn * (*lds));  // slices
     add(8 * nn * (*ldx));                            // Xd[0]
     add(8 * nn * (*ldx));                            // Xd[1]
     add(8 * nn * nn);                                // Dtmp
@@ -191,17 +197,18 @@ void free_slot(fe_ctx *ctx, Slot *s) {
     delete s;
 }
 
-// A free slot for dimension n (reused if cached), or null with ctx->err set.
-int acquire_slot(fe_ctx *ctx, int n, Slot **out) {
+// A free slot for dimension n and method (reused if cached), or an error
+// status with ctx->err set.
+int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
     for (Slot *s : ctx->slots)
-        if (!s->in_use && s->n == n) {
+        if (!s->in_use && s->n == n && s->method == method) {
             s->in_use = true;
             *out = s;
             return FE_OK;
         }
     int ldy, lds, ldx;
     size_t nparts;
-    const size_t bytes = slot_bytes(n, &ldy, &lds, &ldx, &nparts);
+    const size_t bytes = slot_bytes(n, method, &ldy, &lds, &ldx, &nparts);
     if (bytes > ctx->budget)
         return set_err(ctx, FE_ENOMEM, "problem needs " + std::to_string(bytes) +
                                            " bytes, more than the HBM budget");
@@ -217,6 +224,7 @@ int acquire_slot(fe_ctx *ctx, int n, Slot **out) {
     }
     Slot *s = new Slot();
     s->n = n;
+    s->method = method;
     s->bytes = bytes;
     s->ldy = ldy;
     s->lds = lds;
@@ -236,9 +244,12 @@ int acquire_slot(fe_ctx *ctx, int n, Slot **out) {
         return r;
     };
     s->Hcopy = reinterpret_cast<double *>(take(8 * nn * nn));
-    s->Y = reinterpret_cast<float *>(take(4 * nn * ldy));
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < kMaxSlices; ++b) s->sl[a][b] = reinterpret_cast<__half *>(take(2 * nn * lds));
+    float *masters[5] = {};
+    for (int k = 0; k < num_masters(method); ++k) masters[k] = reinterpret_cast<float *>(take(4 * nn * ldy));
+    __half *slices[kNumMats][kMaxSlices] = {};
+    for (int m = 0; m < num_slice_sets(method); ++m)
+        for (int b = 0; b < kMaxSlices; ++b) slices[m][b] = reinterpret_cast<__half *>(take(2 * nn * lds));
+    s->Y = masters[0];
     s->Xd[0] = reinterpret_cast<double *>(take(8 * nn * ldx));
     s->Xd[1] = reinterpret_cast<double *>(take(8 * nn * ldx));
     s->Dtmp = reinterpret_cast<double *>(take(8 * nn * nn));
@@ -249,16 +260,29 @@ int acquire_slot(fe_ctx *ctx, int n, Slot **out) {
     build_tiles(s);
     // descriptor image (tensor maps are fixed for the slot's lifetime)
     memset(&s->hp, 0, sizeof(MmaProb));
-    for (int a = 0; a < 2; ++a)
+    for (int m = 0; m < num_slice_sets(method); ++m) {
+        MatSlot &ms = s->hp.mats[m];
         for (int b = 0; b < kMaxSlices; ++b) {
-            int rc = encode_map(ctx, &s->hp.tmA[a][b], s->sl[a][b], n, lds, kTileM);
-            if (rc == FE_OK) rc = encode_map(ctx, &s->hp.tmB[a][b], s->sl[a][b], n, lds, kTileN);
+            int rc = encode_map(ctx, &ms.tmA[b], slices[m][b], n, lds, kTileM);
+            if (rc == FE_OK) rc = encode_map(ctx, &ms.tmB[b], slices[m][b], n, lds, kTileN);
             if (rc != FE_OK) {
                 free_slot(ctx, s);
                 return rc;
             }
-            s->hp.sl[a][b] = s->sl[a][b];
+            ms.sl[b] = slices[m][b];
         }
+    }
+    if (method == kMethodFermi) {
+        s->hp.mats[kMatZ].master = masters[0];
+        s->hp.mats[kMatN].master = masters[1];
+        s->hp.mats[kMatM].master = masters[2];
+        s->hp.mats[kMatW0].master = masters[3];  // the two W slice sets share one master
+        s->hp.mats[kMatW1].master = masters[3];
+        s->hp.mats[kMatR].master = masters[4];
+    } else {
+        s->hp.mats[kMatY0].master = masters[0];  // both slice sets of Y share the master
+        s->hp.mats[kMatY1].master = masters[0];
+    }
     s->hp.Y = s->Y;
     s->hp.st = s->st;
     s->hp.part = s->part;
@@ -294,6 +318,16 @@ uint32_t prec_of(const fe_ctx *ctx, const fe_problem *p) {
     return pr;
 }
 
+int method_of(const fe_problem *p) {
+    const uint32_t m = p->flags & FE_METHOD_MASK;
+    return (m == FE_METHOD_FERMI || (m == FE_METHOD_AUTO && p->kT > 0.0)) ? kMethodFermi : kMethodSp2;
+}
+
+// Step cap of the finite-temperature expansion: about 12 products per
+// doubling (square, Newton-Schulz pairs, final product) for up to ~40
+// doublings, plus the shift-only refinements.
+constexpr int kFermiMaxSteps = 640;
+
 int validate(fe_ctx *ctx, const fe_problem *p) {
     if (!p) return set_err(ctx, FE_EINVAL, "problem is NULL");
     if (!p->Hp) return set_err(ctx, FE_EINVAL, "Hp is NULL");
@@ -311,10 +345,13 @@ int validate(fe_ctx *ctx, const fe_problem *p) {
     if (m == FE_METHOD_SP2 && p->kT != 0.0)
         return set_err(ctx, FE_EINVAL, "SP2 needs kT == 0");
     const bool fermi = (m == FE_METHOD_FERMI) || (m == FE_METHOD_AUTO && p->kT > 0.0);
-    if (fermi) return set_err(ctx, FE_EINVAL, "finite-temperature expansion not available in this build");
+    if (fermi && !(p->kT > 0.0)) return set_err(ctx, FE_EINVAL, "FE_METHOD_FERMI needs kT > 0");
     const uint32_t pr = p->flags & FE_PREC_MASK;
     if (pr != FE_PREC_MIXED && pr != FE_PREC_FP64 && pr != FE_PREC_FP32 && pr != FE_PREC_TRY_FP16)
         return set_err(ctx, FE_EINVAL, "unknown precision flag");
+    if (fermi && (prec_of(ctx, p) == FE_PREC_FP64 || prec_of(ctx, p) == FE_PREC_TRY_FP16))
+        return set_err(ctx, FE_EINVAL, "the finite-temperature expansion runs split-FP16 products "
+                                       "(FE_PREC_MIXED or FE_PREC_FP32)");
     if ((p->flags & ~(FE_PTR_DEVICE | FE_METHOD_MASK | FE_PREC_MASK)) != 0)
         return set_err(ctx, FE_EINVAL, "unknown flag bits");
     return FE_OK;
@@ -338,6 +375,12 @@ void init_state(const fe_ctx *ctx, const fe_problem *p, SolveState *st) {
     st->idem_hist[0] = st->idem_hist[1] = st->idem_hist[2] = DBL_MAX;
     st->fro_hist[0] = st->fro_hist[1] = st->fro_hist[2] = DBL_MAX;
     st->mu = NAN;
+    st->method = method_of(p);
+    if (st->method == kMethodFermi) {
+        st->max_iters = kFermiMaxSteps;
+        st->wcur = kMatW0;
+        st->ft_sub = 0;  // z0 fresh
+    }
 }
 
 // Run a set of validated problems on acquired slots; fills results.
@@ -378,15 +421,16 @@ int run_problems(fe_ctx *ctx, const std::vector<const fe_problem *> &ps, std::ve
         FE_CUDA(ctx, cudaMemcpyAsync(sl->st, &ctx->h_states[k], sizeof(SolveState),
                                      cudaMemcpyHostToDevice, s));
         const int pr = ctx->h_states[k].prec;
-        if (pr != kPrecFp64) {
+        const bool fermi = ctx->h_states[k].method == kMethodFermi;
+        if (pr != kPrecFp64 || fermi) {
             any_tc = true;
             for (TileEnt t : sl->tiles) { t.prob = k; tiles.push_back(t); }
         }
-        if (pr != kPrecFp32) {
+        if (pr != kPrecFp32 && !fermi) {
             any_fp64 = true;
             for (Tile64 t : sl->tiles64) { t.prob = k; tiles64.push_back(t); }
         }
-        total_iters = std::max(total_iters, ctx->max_iters);
+        total_iters = std::max(total_iters, ctx->h_states[k].max_iters);
     }
     int rc = ensure_dev(ctx, &ctx->d_probs, &ctx->probs_cap, np);
     if (rc == FE_OK) rc = ensure_dev(ctx, &ctx->d_tiles, &ctx->tiles_cap, tiles.size());
@@ -610,7 +654,7 @@ extern "C" int fe_solve(fe_ctx *ctx, const fe_problem *p, fe_result *r) {
     if (rc != FE_OK) return r->status = rc;
     cudaSetDevice(ctx->device);
     Slot *s = nullptr;
-    rc = acquire_slot(ctx, static_cast<int>(p->n), &s);
+    rc = acquire_slot(ctx, static_cast<int>(p->n), method_of(p), &s);
     if (rc != FE_OK) return r->status = rc;
     std::vector<const fe_problem *> ps{p};
     std::vector<Slot *> ss{s};
@@ -634,7 +678,7 @@ extern "C" int fe_solve_batch(fe_ctx *ctx, int count, const fe_problem *ps, fe_r
         memset(&rs[k], 0, sizeof(fe_result));
         int rc = validate(ctx, &ps[k]);
         Slot *s = nullptr;
-        if (rc == FE_OK) rc = acquire_slot(ctx, static_cast<int>(ps[k].n), &s);
+        if (rc == FE_OK) rc = acquire_slot(ctx, static_cast<int>(ps[k].n), method_of(&ps[k]), &s);
         if (rc != FE_OK) {
             rs[k].status = rc;
             if (first == FE_OK) first = rc;
@@ -667,7 +711,7 @@ extern "C" int fe_k_gershgorin(fe_ctx *ctx, const double *H, int64_t n, int64_t 
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
     Slot *s = nullptr;
-    int rc = acquire_slot(ctx, static_cast<int>(n), &s);
+    int rc = acquire_slot(ctx, static_cast<int>(n), kMethodSp2, &s);
     if (rc != FE_OK) return rc;
     MmaProb hp = s->hp;
     hp.H = H;
@@ -703,7 +747,7 @@ extern "C" int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t l
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
     Slot *s = nullptr;
-    int rc = acquire_slot(ctx, static_cast<int>(n), &s);
+    int rc = acquire_slot(ctx, static_cast<int>(n), kMethodSp2, &s);
     if (rc != FE_OK) return rc;
     cudaStream_t q = ctx->stream;
     int e2;
@@ -712,17 +756,24 @@ extern "C" int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t l
     // master <- Y (the epilogue then overwrites it with 0 * Y + 1 * Y^2)
     cudaMemcpy2DAsync(s->Y, sizeof(float) * s->ldy, Y, sizeof(float) * ldy, sizeof(float) * n, n,
                       cudaMemcpyDeviceToDevice, q);
-    k_make_slices<<<kInitBlocks, 256, 0, q>>>(s->Y, static_cast<int>(n), s->ldy, scale, s->sl[0][0],
-                                              s->sl[0][1], s->lds);
+    k_make_slices<<<kInitBlocks, 256, 0, q>>>(s->Y, static_cast<int>(n), s->ldy, scale,
+                                              s->hp.mats[kMatY0].sl[0], s->hp.mats[kMatY0].sl[1], s->lds);
     SolveState st0;
     memset(&st0, 0, sizeof(st0));
     st0.n = static_cast<int>(n);
     st0.kind = (nslices == 2) ? kTcSplit : kTcSingle;
-    st0.alpha = 0.0f;
-    st0.sigma = 1.0f;
-    st0.inv_s2 = static_cast<float>(1.0 / (static_cast<double>(scale) * scale));
-    st0.s_next = 1.0f;
-    st0.cur = 0;
+    // one output: master of slot 0 <- 1 * v + 0 * Y, slices of slot 1 (unused) at scale 1
+    ProdOp &op = st0.op;
+    op.A = op.B = kMatY0;
+    op.E1 = kMatY0;
+    op.E2 = -1;
+    op.inv = static_cast<float>(1.0 / (static_cast<double>(scale) * scale));
+    op.nout = 1;
+    op.part_out = 0;
+    op.out[0].mat = kMatY1;
+    op.out[0].flags = kOutMaster | kOutSlices;
+    op.out[0].a = 1.0f;
+    op.out[0].s = 1.0f;
     rc = ensure_dev(ctx, &ctx->d_probs, &ctx->probs_cap, 1);
     if (rc == FE_OK) rc = ensure_dev(ctx, &ctx->d_tiles, &ctx->tiles_cap, s->tiles.size());
     if (rc != FE_OK) { s->in_use = false; return rc; }

@@ -48,10 +48,34 @@ constexpr int kHistRows = 160;  // per-step history kept in the solve state
 constexpr int kHistCols = 6;
 
 // ---------------------------------------------------------------- state
-// kFp64: native FP64 products; kDf: double-float (FP32 pair) products
-enum Kind : int { kNone = 0, kTcSingle = 1, kTcSplit = 2, kFp64 = 3, kDf = 4 };
+// Which kernel does the step: the tensor-core kernel (kTcSingle / kTcSplit:
+// one or two FP16 slices per operand; kTcElem: no product, epilogue only) or
+// the FP64-accurate SIMT kernel (kFp64 native, kDf double-float).
+enum Kind : int { kNone = 0, kTcSingle = 1, kTcSplit = 2, kFp64 = 3, kDf = 4, kTcElem = 5 };
 enum Phase : int { kPhaseSingle = 0, kPhaseSplit = 1, kPhaseFp64 = 2, kPhaseDone = 3 };
 enum Prec : int { kPrecMixed = 0, kPrecFp64 = 1, kPrecFp32 = 2, kPrecTryFp16 = 3 };
+enum Method : int { kMethodSp2 = 0, kMethodFermi = 1 };
+
+// Output of one tensor-core step: value = a v + b1 E1 + b2 E2 + c [i == j],
+// v the product (A~ B~)_ij, E1/E2 FP32 masters of the epilogue inputs.
+enum OutFlags : int { kOutMaster = 1, kOutSlices = 2, kOutF64a = 4, kOutF64b = 8 };
+struct OutSpec {
+    int mat;     // target matrix slot (master and/or slices)
+    int flags;   // OutFlags
+    float a, b1, b2;
+    float s;     // slice scale of the target
+    double c;    // diagonal term, FP64 (exact for the FP64 outputs)
+};
+struct ProdOp {
+    int A, B;      // operand matrix slots (A~ and B~ slices)
+    int E1, E2;    // matrix slots whose FP32 masters enter the epilogue (-1: none)
+    float inv;     // v = accumulator * inv = accumulator / (s_A s_B)
+    int nout;      // 1..3 outputs
+    int part_out;  // output whose trace and squared Frobenius norm go to the partials
+    float ra, rb, rc;  // aux partial: sum over (ra v + rb E1 + rc [i == j])^2
+    int pad;
+    OutSpec out[3];
+};
 
 struct SolveState {
     // problem (written by the host)
@@ -60,6 +84,17 @@ struct SolveState {
     int max_iters;
     int method;
     double ne, kT, tol;
+    // the tensor-core step to run next (written by the control kernel)
+    ProdOp op;
+    // finite temperature: beta = 1/kT, tracked chemical potential, stages
+    double beta, mu_t, beta0;
+    int ft_m, ft_stage, ft_sub, ft_j, ft_nj, ft_shifts, wcur, ft_phase;
+    int ft_last_mat, ft_pad2;  // slot whose ||.||_F the last step's partials report
+    double sc[6];     // identity parts: A = sc I + A~ (W's in sc[kMatW0], shared by both W slots)
+    double fb[6];     // bounds on ||A~||_F (slice scales are derived from them)
+    float scl[6];     // slice scale s of each slot's FP16 slices (slices hold s A~)
+    double ft_t, w0;  // tanh of the current shift; Newton-Schulz start
+    double tr_d0, tr_q;  // traces of D0 = (I - z)/2 and Q = (I - z^2)/4 at the end
     // Gershgorin bounds and Hp statistics (written by the bounds kernel)
     double emin, emax, trH, hmax;
     int bad_input;
@@ -69,11 +104,10 @@ struct SolveState {
     int cur;            // current slice set (0/1)
     int xcur;           // current FP64 buffer (0/1)
     int x_fp64;         // 1: the iterate is Xd[xcur] (FP64); 0: it is c I + Y
-    // instruction for the product kernels of this step (written by control)
+    // which kernel runs this step (written by control)
     int kind;
     int sq;             // 1: X^2 branch, 0: 2X - X^2 branch
-    float alpha, sigma, inv_s2, s_next;
-    float r1, r0;       // X^2 - X = Y^2 + r1 Y + r0 I with r1 = 2c - 1, r0 = c^2 - c
+    float s_next;       // slice scale of the zero-temperature iterate after this step
     double c_next;
     double gamma;       // FP64-accurate step: X' = F(X) + gamma (X - X^2) (trace correction)
     // convergence bookkeeping

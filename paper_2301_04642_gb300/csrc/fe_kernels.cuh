@@ -4,18 +4,37 @@
 
 namespace fe {
 
-// Everything a tile of one problem needs.  Lives in device global memory
-// (64-byte aligned because of the embedded tensor maps); filled by the host.
+// One symmetric n x n matrix as the tensor-core kernel sees it: FP16 slices
+// (hi, lo) of s * A~ with their TMA descriptors, and optionally the FP32 master
+// A~.  Every matrix of the expansion is kept as (FP64 scalar) I + A~; the
+// scalar lives in the solve state.
+struct MatSlot {
+    CUtensorMap tmA[kMaxSlices];  // box 64 (K) x 128 rows
+    CUtensorMap tmB[kMaxSlices];  // box 64 (K) x 256 rows
+    __half *sl[kMaxSlices];
+    float *master;                // FP32 small part (null when not kept)
+    long long pad;
+};
+
+// Matrix slots of a problem.  Zero temperature: kMatY0/kMatY1 are the two
+// slice sets of Y (one FP32 master).  Finite temperature: z, N, M, W (two
+// slice sets, one master), R.
+enum MatId : int {
+    kMatY0 = 0, kMatY1 = 1,
+    kMatZ = 0, kMatN = 1, kMatM = 2, kMatW0 = 3, kMatW1 = 4, kMatR = 5,
+    kNumMats = 6
+};
+
+// Everything the kernels need for one problem.  Lives in device global memory
+// (the embedded tensor maps need 128-byte alignment); filled by the host.
 struct MmaProb {
-    CUtensorMap tmA[2][kMaxSlices];  // [slice set][slice]: box 64 (K) x 128 rows
-    CUtensorMap tmB[2][kMaxSlices];  // [slice set][slice]: box 64 (K) x 256 rows
-    float *Y;                        // FP32 master, n x n, leading dimension ldy
-    __half *sl[2][kMaxSlices];       // FP16 slices, n x n, leading dimension lds
+    MatSlot mats[kNumMats];
     SolveState *st;
     double *part;                    // per-tile partial slots (kPartStride doubles each)
     int n, ldy, lds, ntiles;
     int ntiles64, pad1;
-    double *Xd[2];                   // FP64 iterate buffers (FP64 phase), leading dim ldx
+    float *Y;                        // FP32 master of the zero-temperature iterate
+    double *Xd[2];                   // FP64 buffers (FP64 phase / finite-T output), ld ldx
     int ldx, pad0;
     const double *H;                 // Hp (device), leading dimension ldh
     long long ldh;
@@ -50,11 +69,11 @@ __global__ void k_bounds_rows(const MmaProb *probs, int prob, RowInfo *rowinfo, 
 // Deterministic reduction of the row info into the state (one block).
 __global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *rowinfo,
                                 const int *bad);
-// X0 -> (c, Y0) and slices; per-block partials.
+// Zero temperature: X0 -> (c, Y0) and slices.  Finite temperature: z0.  Per-block partials.
 __global__ void k_init_x0(const MmaProb *probs, int prob);
 // Step control for every problem (one block per problem).
 __global__ void k_control(const MmaProb *probs, int nprobs);
-// FP64 product + SP2 update (upper tiles, mirrored), per-tile partials.
+// FP64-accurate product + SP2 update (upper tiles, mirrored), per-tile partials.
 __global__ void k_fp64_step(const MmaProb *probs, const Tile64 *tiles, int ntiles);
 // D = X -> out (FP64, ld), partials of tr(H D) and tr D.
 __global__ void k_finalize(const MmaProb *probs, int prob, double *D, long long ldd);

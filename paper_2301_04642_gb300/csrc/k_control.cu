@@ -1,20 +1,37 @@
 // Per-step control on the device: no iteration needs a host synchronisation.
+// One block per problem reduces the per-tile FP64 partials of the last step
+// (fixed order) and writes the next step into the solve state.
 //
-// One block per problem reduces the per-tile FP64 partials of the last
-// product (fixed order), forms t1 = tr X and t2 = tr X^2 = ||X||_F^2
-// (Sec. III-B), and then
-//   * tests convergence with the relative trace change
-//     RelTr = |t1_k - t1_{k-1}| / N_e (Sec. III-A) together with an
-//     idempotency measure (the RelTr test alone leaves D^2 != D):
-//       - split-FP16 phase: ||X_k^2 - X_k||_F of the product's input, which
-//         the tensor-core epilogue accumulates; the phase ends when it has
-//         stopped shrinking (the noise floor of the split products);
-//       - FP64 phase: t1 - t2 = sum_i x_i (1 - x_i), exact enough in FP64;
-//   * walks the precision schedule (Sec. III-A: cheap products while far from
-//     convergence -- RelTr above 5e-4 -- accurate ones near it);
-//   * picks the SP2 branch of Eq. (1): X^2 if |t2 - N_e| <= |2 t1 - t2 - N_e|
-//     (the candidate whose trace is nearer N_e), else 2X - X^2;
-//   * writes the coefficients the next product kernel applies.
+// Zero temperature (SP2, Sec. II-B1 Eq. (1)):
+//   * t1 = tr X, t2 = tr X^2 = ||X||_F^2 (Sec. III-B);
+//   * convergence: relative trace change RelTr = |t1_k - t1_{k-1}| / N_e
+//     (Sec. III-A) together with an idempotency measure (the RelTr test alone
+//     leaves D^2 != D): in the split-FP16 phase ||X_k^2 - X_k||_F, which the
+//     tensor-core epilogue accumulates; in the FP64-accurate phase
+//     t1 - t2 = sum_i x_i (1 - x_i);
+//   * precision schedule (Sec. III-A: cheap products while far from
+//     convergence, accurate ones near it);
+//   * branch: X^2 if |t2 - N_e| <= |2 t1 - t2 - N_e| (the candidate whose trace
+//     is nearer N_e), else 2X - X^2.
+//
+// Finite temperature (Sec. II-A Fermi-Dirac target, recursive expansion of
+// Sec. II-B3): z = I - 2D = tanh(beta (H - mu)/2).  Starting from the
+// linearised z0 = (beta0/2)(H - mu0 I) at beta0 = beta / 2^m, every stage
+// doubles beta with the double-angle identity of tanh, folding in a shift of
+// mu (logit shift b, t = tanh b) chosen by a Newton step so that tr D tracks
+// N_e at every temperature:
+//   z' = (z - t)(I - t z)^{-1}  and  z'' = 2 z' (I + z'^2)^{-1}
+//   => z'' = N M^{-1},  N = 2 ((1 + t^2) z - t (I + z^2)),
+//                       M = (1 + t^2)(I + z^2) - 4 t z.
+// M^{-1} comes from Newton-Schulz, W <- W (2 I - M W), started at the
+// scalar w0 = 2 / (m_min + m_max) from the analytic bounds of M's spectrum.
+// After the last stage up to three shift-only steps N = z - t I, M = I - t z
+// bring tr D near N_e, and a last product writes D0 = (I - z)/2 and
+// Q = (I - z^2)/4 = D0 - D0^2 in FP64; the output kernel forms
+// D = D0 + gamma Q with gamma fixed so that tr D = N_e exactly (a first-order
+// shift of mu, since dD/dmu = beta D (I - D)).
+// All matrices are kept as (FP64 scalar) I + (FP32 small part); every
+// product is a split-FP16 tensor-core product of the small parts.
 #include <cfloat>
 
 #include "fe_dev.cuh"
@@ -28,49 +45,34 @@ namespace {
 __device__ float slice_scale(double bound) {
     if (!(bound > 0.0)) bound = 1.0;
     int e;
-    frexp(bound, &e);  // bound < 2^e
+    frexp(bound * 1.0001, &e);  // bound < 2^e
     return static_cast<float>(ldexp(1.0, 14 - e));
 }
 
-}  // namespace
+__device__ void set_out(OutSpec &o, int mat, int flags, double a, double b1, double b2, double c,
+                        double bound) {
+    o.mat = mat;
+    o.flags = flags;
+    o.a = static_cast<float>(a);
+    o.b1 = static_cast<float>(b1);
+    o.b2 = static_cast<float>(b2);
+    o.c = c;
+    o.s = slice_scale(bound);
+}
 
-__global__ void k_control(const MmaProb *probs, int nprobs) {
-    const int p = blockIdx.x;
-    if (p >= nprobs) return;
-    const MmaProb &pr = probs[p];
-    SolveState *st = pr.st;
-    if (st->done) return;
+__device__ void begin_op(ProdOp &op, int A, int B, int E1, int E2, double inv) {
+    op.A = A;
+    op.B = B;
+    op.E1 = E1;
+    op.E2 = E2;
+    op.inv = static_cast<float>(inv);
+    op.nout = 0;
+    op.part_out = 0;
+    op.ra = op.rb = op.rc = 0.0f;
+}
 
-    // number of partial slots written by the previous producer
-    int nparts;
-    if (st->kind == kNone) nparts = kInitBlocks;
-    else if (st->kind == kFp64 || st->kind == kDf) nparts = pr.ntiles64;
-    else nparts = pr.ntiles;
-
-    __shared__ double s_a[256], s_b[256], s_c[256], s_d[256];
-    const int t = threadIdx.x;
-    double a = 0, b = 0, c = 0, d = 0;
-    for (int k = t; k < nparts; k += blockDim.x) {
-        const double *slot = pr.part + static_cast<size_t>(k) * kPartStride;
-        a += slot[0];
-        b += slot[1];
-        c = fmax(c, slot[2]);
-        d += slot[3];
-    }
-    s_a[t] = a; s_b[t] = b; s_c[t] = c; s_d[t] = d;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (t < o) {
-            s_a[t] += s_a[t + o];
-            s_b[t] += s_b[t + o];
-            s_c[t] = fmax(s_c[t], s_c[t + o]);
-            s_d[t] += s_d[t + o];
-        }
-        __syncthreads();
-    }
-    if (t != 0) return;
-
-    const double trV = s_a[0], sumsq = s_b[0], rsq = s_d[0];
+// ------------------------------------------------------------------ SP2 step
+__device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq) {
     const int n = st->n;
     const double nn = static_cast<double>(n);
     const double ne = st->ne;
@@ -95,13 +97,6 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
         st->fro_hist[0] = fro;
     }
 
-    if (st->bad_input) {
-        st->status = -1;  // FE_EINVAL
-        st->done = 1;
-        st->kind = kNone;
-        return;
-    }
-
     double t1, t2;
     const double cc = st->c;
     if (st->x_fp64) {
@@ -119,7 +114,6 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
     st->idem_hist[2] = st->idem_hist[1];
     st->idem_hist[1] = st->idem_hist[0];
     st->idem_hist[0] = idem;
-
     if (st->iter < kHistRows) {
         double *h = st->hist[st->iter];
         h[0] = st->phase;
@@ -149,17 +143,15 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
         }
     } else if (phase == kPhaseFp64 && (prev_kind == kFp64 || prev_kind == kDf)) {
         const int nfp64 = st->it_phase[kPhaseFp64];
-        const bool idem_ok = fabs(idem) <= 2e-10 ||
-                             (fabs(idem) >= 0.5 * fabs(st->idem_hist[2]) && fabs(idem) <= 1e-6);
         if (st->prec == kPrecFp64) {
+            const bool idem_ok = fabs(idem) <= 2e-10 ||
+                                 (fabs(idem) >= 0.5 * fabs(st->idem_hist[2]) && fabs(idem) <= 1e-6);
             if (reltr <= st->tol && idem_ok) done = true;
         } else {
             // Polishing products come in pairs of opposite branches, the second
-            // one carrying the exact trace correction (below): after a pair the
-            // deviations are O(dx^2) on both sides and tr X = N_e to rounding.
-            // fro_hist[0] = ||X^2 - X||_F of the pair's second input; the
-            // output's deviations are about its square
-            (void)idem_ok;
+            // carrying the exact trace correction (below); after a pair the
+            // deviations are about the square of fro_hist[0] = ||X^2 - X||_F of
+            // the pair's second input.
             const double f0 = st->fro_hist[0];
             if (nfp64 >= 2 && (nfp64 & 1) == 0 &&
                 ((f0 * f0 <= 5e-9 && fabs(idem) <= 1e-8) || nfp64 >= 6))
@@ -179,20 +171,16 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
 
     // ---- SP2 branch (Eq. (1)) and the instruction for the next product
     int sq = fabs(t2 - ne) <= fabs(2.0 * t1 - t2 - ne);
-    // Polishing (mixed schedules): the second product of each pair takes the
-    // other branch, so a pair maps x -> 1 - O(dx^2) near 1 and O(dx^2) near
-    // 0 whichever side the trace rule favoured first.
     st->gamma = 0.0;
     if (phase == kPhaseFp64 && st->prec != kPrecFp64 && (st->it_phase[kPhaseFp64] & 1) == 1) {
+        // Polishing: the second product of each pair takes the other branch,
+        // so a pair maps x -> 1 - O(dx^2) near 1 and O(dx^2) near 0.
         sq = !st->sq;
         // Exact trace: the branch output F(X) has trace t2 (X^2) or 2 t1 - t2
-        // (2X - X^2), known now from the FP64 partials of X; adding
-        // gamma (X - X^2), whose trace is t1 - t2, lands tr X' on N_e.
-        // The correction moves eigenvalue x by gamma x (1 - x); |x (1 - x)| of
-        // this iterate is at most ~2 ||X_prev^2 - X_prev||_F (one side of the
-        // first product of the pair doubled).  Apply it only when a trace error
-        // remains and the largest move stays within a few times that error,
-        // i.e. when the x (1 - x) do not cancel in their sum.
+        // (2X - X^2); adding gamma (X - X^2), of trace t1 - t2, lands tr X' on
+        // N_e.  gamma moves eigenvalue x by gamma x (1 - x), at most ~2
+        // ||X_prev^2 - X_prev||_F |gamma|; it is applied only when a trace
+        // error remains and that move stays within a few times the error.
         const double trF = sq ? t2 : 2.0 * t1 - t2;
         const double dtr = ne - trF;
         const double dev = t1 - t2;
@@ -208,24 +196,298 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
         st->kind = (st->prec == kPrecFp64) ? kFp64 : kDf;
     } else {
         st->kind = (phase == kPhaseSingle) ? kTcSingle : kTcSplit;
+        // X = c I + Y:  X^2 -> c' = c^2, Y' = 2c Y + Y^2;  2X - X^2 -> c' = 2c - c^2,
+        // Y' = (2 - 2c) Y - Y^2
         const double alpha = sq ? 2.0 * cc : 2.0 - 2.0 * cc;
         const double cn = sq ? cc * cc : 2.0 * cc - cc * cc;
-        st->alpha = static_cast<float>(alpha);
-        st->sigma = sq ? 1.0f : -1.0f;
         st->c_next = cn;
-        st->r1 = static_cast<float>(2.0 * cc - 1.0);
-        st->r0 = static_cast<float>(cc * cc - cc);
-        const double s = st->s_cur;
-        st->inv_s2 = static_cast<float>(1.0 / (s * s));
         // entries of Y' = X' - c' I are bounded by its spectral radius:
         // spec(X') in [0, 1] gives max(c', 1 - c'); also ||alpha Y + sigma Y^2||_F
         const double fro = sqrt(fmax(sumsq, 0.0));
         const double bound = fmin(fmax(cn, 1.0 - cn) + 1e-3, fabs(alpha) * fro + fro * fro);
-        st->s_next = slice_scale(bound * 1.0001);
+        const int cur = st->cur;
+        ProdOp &op = st->op;
+        const double s = st->s_cur;
+        begin_op(op, cur, cur, cur, -1, 1.0 / (s * s));
+        op.nout = 1;
+        set_out(op.out[0], cur ^ 1, kOutMaster | kOutSlices, sq ? 1.0 : -1.0, alpha, 0.0, 0.0, bound);
+        st->s_next = op.out[0].s;
+        // ||X^2 - X||: X^2 - X = Y^2 + (2c - 1) Y + (c^2 - c) I
+        op.ra = 1.0f;
+        op.rb = static_cast<float>(2.0 * cc - 1.0);
+        op.rc = static_cast<float>(cc * cc - cc);
     }
     st->t1_prev = t1;
     st->it_phase[phase] += 1;
     st->iter += 1;
+}
+
+// ------------------------------------------------------------------ finite T
+// ft_sub names the step that was issued last; kFtStart is the state after X0.
+enum FtSub : int { kFtStart = 0, kFtSquare = 1, kFtShiftElem = 2, kFtMW = 3, kFtWR = 4, kFtNW = 5,
+                   kFtFinal = 6 };
+
+// Newton-Schulz steps after the closed-form first iterate so that the
+// residual bound r0^(2^(j+1)) falls below 1e-10.
+__device__ int ns_steps(double mmin, double mmax) {
+    const double r0 = (mmax - mmin) / (mmax + mmin);
+    double r = r0 * r0;
+    int j = 0;
+    while (r > 1e-10 && j < 12) {
+        r = r * r;
+        ++j;
+    }
+    return j;
+}
+
+__device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1) {
+    const int n = st->n;
+    const double nn = static_cast<double>(n);
+    const double ne = st->ne;
+    ProdOp &op = st->op;
+    const int sub = st->ft_sub;
+    double *sc = st->sc, *fb = st->fb;
+    float *scl = st->scl;
+    const int Z = kMatZ, N = kMatN, M = kMatM, R = kMatR, WS = kMatW0;  // WS: W's scalar slot
+
+    if (st->iter < kHistRows) {
+        // stage, last step, tr D - N_e (when z is fresh), mu estimate, W's
+        // identity part, ||output~||_F of the last step
+        double *h = st->hist[st->iter];
+        h[0] = st->ft_stage;
+        h[1] = sub;
+        h[2] = 0.5 * (nn - (nn * sc[Z] + tr0)) - ne;
+        h[3] = st->mu_t;
+        h[4] = sc[WS];
+        h[5] = sqrt(fmax(sq0, 0.0));
+    }
+    if (sub == kFtFinal) {
+        // the final product wrote D0 and Q: keep their exact traces
+        st->tr_d0 = tr0;
+        st->tr_q = tr1;
+        st->done = 1;
+        st->kind = kNone;
+        return;
+    }
+    if (st->iter >= st->max_iters) {
+        st->status = -3;
+        st->done = 1;
+        st->kind = kNone;
+        return;
+    }
+    // The partials carry the exact ||A~||_F of the step's reported output:
+    // replace the a-priori bound (triangle inequalities would compound over
+    // the Newton-Schulz steps and push the slice scales out of range).
+    if (sub != kFtStart) fb[st->ft_last_mat] = sqrt(fmax(sq0, 0.0));
+    st->iter += 1;
+    const int W = st->wcur;
+
+    // ---- Newton-Schulz inner steps
+    if (sub == kFtSquare || sub == kFtShiftElem || sub == kFtWR) {
+        if (sub == kFtWR) st->ft_j += 1;
+        if (st->ft_j < st->ft_nj) {
+            // R = M W:  R~ = v + Mc W~ + Wc M~,  Rc = Mc Wc
+            const double Mc = sc[M], Wc = sc[WS];
+            fb[R] = fb[M] * fb[W] + fabs(Mc) * fb[W] + fabs(Wc) * fb[M];
+            sc[R] = Mc * Wc;
+            st->kind = kTcSplit;
+            begin_op(op, M, W, W, M, 1.0 / (static_cast<double>(scl[M]) * scl[W]));
+            op.nout = 1;
+            set_out(op.out[0], R, kOutMaster | kOutSlices, 1.0, Mc, Wc, 0.0, fb[R]);
+            scl[R] = op.out[0].s;
+            st->ft_sub = kFtMW;
+            st->ft_last_mat = R;
+        } else {
+            // z'' = N W:  z~ = v + Nc W~ + Wc N~,  zc = Nc Wc
+            const double Nc = sc[N], Wc = sc[WS];
+            fb[Z] = fb[N] * fb[W] + fabs(Nc) * fb[W] + fabs(Wc) * fb[N];
+            sc[Z] = Nc * Wc;
+            st->kind = kTcSplit;
+            begin_op(op, N, W, W, N, 1.0 / (static_cast<double>(scl[N]) * scl[W]));
+            op.nout = 1;
+            set_out(op.out[0], Z, kOutMaster | kOutSlices, 1.0, Nc, Wc, 0.0, fb[Z]);
+            scl[Z] = op.out[0].s;
+            op.part_out = 0;  // tr z~ and ||z~||_F^2 for the next Newton step on mu
+            st->ft_sub = kFtNW;
+            st->ft_last_mat = Z;
+        }
+        return;
+    }
+    if (sub == kFtMW) {
+        // W' = 2 W - W R:  W'~ = (2 - Rc) W~ - Wc R~ - v,  W'c = Wc (2 - Rc)
+        const double Rc = sc[R], Wc = sc[WS];
+        const int Wn = (W == kMatW0) ? kMatW1 : kMatW0;
+        fb[Wn] = fabs(2.0 - Rc) * fb[W] + fabs(Wc) * fb[R] + fb[W] * fb[R];
+        sc[WS] = Wc * (2.0 - Rc);
+        st->kind = kTcSplit;
+        begin_op(op, W, R, W, R, 1.0 / (static_cast<double>(scl[W]) * scl[R]));
+        op.nout = 1;
+        set_out(op.out[0], Wn, kOutMaster | kOutSlices, -1.0, 2.0 - Rc, -Wc, 0.0, fb[Wn]);
+        scl[Wn] = op.out[0].s;
+        st->wcur = Wn;
+        st->ft_sub = kFtWR;
+        st->ft_last_mat = Wn;
+        return;
+    }
+
+    // ---- z is fresh (after X0 or after N W): decide the next step
+    // Phases of the chemical-potential control:
+    //   A  plain doublings while z is nearly linear in H (rms of z < 0.25):
+    //      tr D stays near n/2 whatever mu is, so nothing is tracked yet;
+    //   B  (entered when z turns nonlinear) shift-only Newton steps until
+    //      tr D = N_e at the current temperature;
+    //   C  doublings with the Newton shift of the current trace error folded
+    //      in (mu(T) moves by less than kT per halving of T from here on);
+    //      a large error falls back to shift-only steps;
+    //   D  after the last doubling, shift-only Newton steps until
+    //      |tr D - N_e| <= 1e-3, then the final trace-exact product.
+    const double zc = sc[Z];
+    const double trz = nn * zc + tr0;
+    const double zz = nn * zc * zc + 2.0 * zc * tr0 + sq0;
+    fb[Z] = sqrt(fmax(sq0, 0.0));
+    const double trD = 0.5 * (nn - trz);
+    const double slope = 0.5 * (nn - zz);  // d tr D / d b with b the logit shift
+    double b = (slope > 1e-300) ? (ne - trD) / slope : 0.0;
+    const double dN = ne - trD;
+    const bool stages_done = st->ft_stage >= st->ft_m;
+    const double z_rms = sqrt(fmax(zz, 0.0) / nn);
+    if (st->ft_phase == 0 && (z_rms >= 0.25 || stages_done)) st->ft_phase = 1;
+    bool shift_only;
+    if (stages_done) {
+        shift_only = true;
+    } else if (st->ft_phase == 0) {
+        shift_only = false;
+        b = 0.0;
+    } else {
+        // large errors (entering phase B, or after a big drift) are removed by
+        // shift-only steps; small ones ride along with the next doubling
+        shift_only = fabs(dN) > 0.05 * sqrt(fmax(ne, 1.0)) && st->ft_shifts < 6;
+    }
+    if (stages_done && (fabs(dN) <= 1e-3 || st->ft_shifts >= 6)) {
+        // ---- final product: D0 = (I - z)/2 and Q = (I - z^2)/4 in FP64
+        st->kind = kTcSplit;
+        begin_op(op, Z, Z, Z, -1, 1.0 / (static_cast<double>(scl[Z]) * scl[Z]));
+        op.nout = 2;
+        set_out(op.out[0], Z, kOutF64a, 0.0, -0.5, 0.0, 0.5 * (1.0 - zc), 1.0);
+        set_out(op.out[1], Z, kOutF64b, -0.25, -0.5 * zc, 0.0, 0.25 * (1.0 - zc * zc), 1.0);
+        op.part_out = 0;
+        st->ft_sub = kFtFinal;
+        return;
+    }
+    const double beta_k = st->beta0 * ldexp(1.0, st->ft_stage);  // z = tanh(beta_k (H - mu)/2)
+    b = shift_only ? fmax(-1.0, fmin(1.0, b)) : fmax(-0.5, fmin(0.5, b));
+    const double t = tanh(b);
+    st->ft_t = t;
+    st->mu_t += 2.0 * b / beta_k;
+    st->ft_j = 0;
+    const double fz = fb[Z];
+    if (!shift_only) {
+        st->ft_shifts = 0;
+        // ---- shift + double: s = z^2 = zc^2 I + 2 zc z~ + v with v = z~ z~
+        const double t2 = t * t;
+        const double Mc = (1.0 + t2) * (1.0 + zc * zc) - 4.0 * t * zc;
+        const double Nc = 2.0 * (1.0 + t2) * zc - 2.0 * t * (1.0 + zc * zc);
+        // spectrum of M = (1 - t z)^2 + (z - t)^2 for z in [-1, 1]
+        const double mmin = (1.0 - t2) * (1.0 - t2) / (1.0 + t2);
+        const double mmax = 2.0 * (1.0 + fabs(t)) * (1.0 + fabs(t));
+        const double w0 = 2.0 / (mmin + mmax);
+        st->w0 = w0;
+        st->ft_nj = ns_steps(mmin, mmax);
+        const double bM1 = 2.0 * (1.0 + t2) * zc - 4.0 * t;  // M~ = (1 + t^2) v + bM1 z~
+        const double bN1 = 2.0 * (1.0 + t2) - 4.0 * t * zc;  // N~ = -2t v + bN1 z~
+        fb[M] = (1.0 + t2) * fz * fz + fabs(bM1) * fz;
+        fb[N] = 2.0 * fabs(t) * fz * fz + fabs(bN1) * fz;
+        fb[W] = w0 * w0 * fb[M];
+        sc[M] = Mc;
+        sc[N] = Nc;
+        sc[WS] = 2.0 * w0 - w0 * w0 * Mc;  // first Newton-Schulz iterate W1 = 2 w0 I - w0^2 M
+        st->kind = kTcSplit;
+        begin_op(op, Z, Z, Z, -1, 1.0 / (static_cast<double>(scl[Z]) * scl[Z]));
+        op.nout = 3;
+        set_out(op.out[0], M, kOutMaster | kOutSlices, 1.0 + t2, bM1, 0.0, 0.0, fb[M]);
+        set_out(op.out[1], N, kOutMaster | kOutSlices, -2.0 * t, bN1, 0.0, 0.0, fb[N]);
+        set_out(op.out[2], W, kOutMaster | kOutSlices, -w0 * w0 * (1.0 + t2), -w0 * w0 * bM1, 0.0,
+                0.0, fb[W]);
+        scl[M] = op.out[0].s;
+        scl[N] = op.out[1].s;
+        scl[W] = op.out[2].s;
+        st->ft_stage += 1;
+        st->ft_sub = kFtSquare;
+        st->ft_last_mat = M;
+    } else {
+        // ---- shift only: N = z - t I, M = I - t z, spectrum of M in [1 - |t|, 1 + |t|]
+        const double Mc = 1.0 - t * zc;
+        const double Nc = zc - t;
+        const double mmin = 1.0 - fabs(t), mmax = 1.0 + fabs(t);
+        const double w0 = 2.0 / (mmin + mmax);
+        st->w0 = w0;
+        st->ft_nj = ns_steps(mmin, mmax);
+        fb[M] = fabs(t) * fz;
+        fb[N] = fz;
+        fb[W] = w0 * w0 * fb[M];
+        sc[M] = Mc;
+        sc[N] = Nc;
+        sc[WS] = 2.0 * w0 - w0 * w0 * Mc;
+        st->kind = kTcElem;
+        begin_op(op, Z, Z, Z, -1, 0.0);
+        op.nout = 3;
+        set_out(op.out[0], M, kOutMaster | kOutSlices, 0.0, -t, 0.0, 0.0, fb[M]);
+        set_out(op.out[1], N, kOutMaster | kOutSlices, 0.0, 1.0, 0.0, 0.0, fb[N]);
+        set_out(op.out[2], W, kOutMaster | kOutSlices, 0.0, w0 * w0 * t, 0.0, 0.0, fb[W]);
+        scl[M] = op.out[0].s;
+        scl[N] = op.out[1].s;
+        scl[W] = op.out[2].s;
+        st->ft_shifts += 1;
+        st->ft_sub = kFtShiftElem;
+        st->ft_last_mat = M;
+    }
+}
+
+}  // namespace
+
+__global__ void k_control(const MmaProb *probs, int nprobs) {
+    const int p = blockIdx.x;
+    if (p >= nprobs) return;
+    const MmaProb &pr = probs[p];
+    SolveState *st = pr.st;
+    if (st->done) return;
+
+    // number of partial slots written by the previous producer
+    int nparts;
+    if (st->kind == kNone) nparts = kInitBlocks;
+    else if (st->kind == kFp64 || st->kind == kDf) nparts = pr.ntiles64;
+    else nparts = pr.ntiles;
+
+    __shared__ double s_a[256], s_b[256], s_c[256], s_d[256];
+    const int t = threadIdx.x;
+    double a = 0, b = 0, c = 0, d = 0;
+    for (int k = t; k < nparts; k += blockDim.x) {
+        const double *slot = pr.part + static_cast<size_t>(k) * kPartStride;
+        a += slot[0];
+        b += slot[1];
+        c += slot[2];
+        d += slot[3];
+    }
+    s_a[t] = a; s_b[t] = b; s_c[t] = c; s_d[t] = d;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            s_a[t] += s_a[t + o];
+            s_b[t] += s_b[t + o];
+            s_c[t] += s_c[t + o];
+            s_d[t] += s_d[t + o];
+        }
+        __syncthreads();
+    }
+    if (t != 0) return;
+    if (st->bad_input) {
+        st->status = -1;  // FE_EINVAL
+        st->done = 1;
+        st->kind = kNone;
+        return;
+    }
+    if (st->method == kMethodFermi) control_fermi(st, s_a[0], s_b[0], s_c[0]);
+    else control_sp2(st, s_a[0], s_b[0], s_d[0]);
 }
 
 }  // namespace fe

@@ -1,12 +1,22 @@
-// Symmetric product Y^2 on the 5th-generation tensor cores with the SP2
-// update fused into the epilogue (Sec. II-B1 Eq. (1); Sec. III-B: the product
-// dominates the cost).
+// Symmetric products on the 5th-generation tensor cores with the update of
+// the expansion fused into the epilogue (Sec. II-B1 Eq. (1), Sec. II-B3;
+// Sec. III-B: the matrix product dominates the cost).
 //
-// One persistent CTA per SM walks a list of upper-triangle tiles (of one or
-// many problems).  A tile is 128 rows (block I) x 256 columns (blocks 2Jp,
-// 2Jp+1); only 128x128 blocks with J >= I are written.  Because Y is
-// symmetric, (Y^2)_ij = sum_k Y_ik Y_jk: both operands are row panels of the
-// same K-major FP16 slice arrays, loaded by TMA with 128-byte swizzling.
+// Every step multiplies two symmetric, mutually commuting matrices given by
+// their small parts A~, B~ (the identity parts are FP64 scalars in the solve
+// state), so the product is symmetric and only upper-triangle 128x128 blocks
+// are computed.  (A~ B~)_ij = sum_k A~_ik B~_jk: both operands are row panels
+// of K-major FP16 slice arrays, loaded by TMA with 128-byte swizzling.  The
+// epilogue evaluates up to three outputs  a v + b1 E1 + b2 E2 + c [i == j]
+// (v the product, E1/E2 FP32 masters), writes them as FP32 masters, FP16
+// slices for the next step and/or FP64 matrices, mirrors every value to the
+// lower triangle, and leaves per-tile FP64 partials (trace and squared
+// Frobenius norm of one output, trace of another, and an auxiliary sum of
+// squares used as the idempotency measure ||X^2 - X||_F^2).  The step to run
+// is described by the ProdOp the control kernel wrote into the solve state.
+//
+// One persistent CTA per SM walks a list of tiles (of one or many problems):
+// 128 rows (block I) x 256 columns (blocks 2Jp, 2Jp+1).
 //
 // Accuracy: the tensor core adds every MMA into its FP32 accumulator with a
 // one-sided rounding, so an accumulator that lives for the whole K loop
@@ -23,11 +33,7 @@
 //   warp 1      TMEM owner and MMA issuer: per chunk 4 x (1 or 3) MMAs
 //               M128 N256 K16 into one of two chunk buffers (2 x 256 cols).
 //   warps 2-9   drain + epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
-//               and columns 128 ((w - 2) / 4) .. +127; after the last chunk
-//               of a tile it applies Y' = alpha Y + sigma P / s^2 to its
-//               128x128 block, updates the FP32 master in place (+ mirror),
-//               writes the next FP16 slices (+ mirror) and the per-tile FP64
-//               partials of tr Y' and ||Y'||_F^2 (Sec. III-B, fused).
+//               and columns 128 ((w - 2) / 4) .. +127, i.e. one 128x128 block.
 // Every wait is bounded; on a timeout the kernel records an error code,
 // drains its own copies and MMAs, frees TMEM and returns.
 #include "fe_dev.cuh"
@@ -55,15 +61,30 @@ struct MmaSmemTail {
 
 constexpr size_t kMmaSmemBytes = 1024 + sizeof(StageSmem) * kStages + sizeof(MmaSmemTail);
 
+__device__ __forceinline__ int step_kind(const SolveState *st) {
+    return *reinterpret_cast<const volatile int *>(&st->kind);
+}
+
 __device__ __forceinline__ bool tile_active(const SolveState *st) {
-    const int kind = *reinterpret_cast<const volatile int *>(&st->kind);
-    return kind == kTcSingle || kind == kTcSplit;
+    const int kind = step_kind(st);
+    return kind == kTcSingle || kind == kTcSplit || kind == kTcElem;
+}
+
+// K chunks of this step (0 for an epilogue-only step)
+__device__ __forceinline__ int step_chunks(const SolveState *st, int n) {
+    return step_kind(st) == kTcElem ? 0 : (n + kTileK - 1) / kTileK;
 }
 
 __device__ __forceinline__ void record_error(int *err, int code) { atomicCAS(err, 0, code); }
 
 // named barrier of the 8 drain/epilogue warps
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ void put_slices(const MatSlot &m, size_t at, float ys) {
+    const __half hh = __float2half_rn(ys);
+    m.sl[0][at] = hh;
+    m.sl[1][at] = __float2half_rn(ys - __half2float(hh));
+}
 
 }  // namespace
 
@@ -109,9 +130,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             const MmaProb &pr = probs[te.prob];
             if (!tile_active(pr.st)) continue;
             const SolveState *st = pr.st;
-            const int S = (st->kind == kTcSplit) ? 2 : 1;
-            const int set = st->cur;
-            const int nk = (pr.n + kTileK - 1) / kTileK;
+            const int S = (step_kind(st) == kTcSplit) ? 2 : 1;
+            const MatSlot &ma = pr.mats[st->op.A];
+            const MatSlot &mb = pr.mats[st->op.B];
+            const int nk = step_chunks(st, pr.n);
             const uint32_t bytes = static_cast<uint32_t>(S * (kSliceABytes + kSliceBBytes));
             for (int kc = 0; kc < nk; ++kc) {
                 bool got = true;
@@ -125,9 +147,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                 if (lane == 0) {
                     mbar_expect_tx(&tail->full[stage], bytes);
                     for (int s = 0; s < S; ++s) {
-                        tma_load_2d(stages[stage].a[s], &pr.tmA[set][s], &tail->full[stage],
+                        tma_load_2d(stages[stage].a[s], &ma.tmA[s], &tail->full[stage],
                                     kc * kTileK, te.I * kTileM);
-                        tma_load_2d(stages[stage].b[s], &pr.tmB[set][s], &tail->full[stage],
+                        tma_load_2d(stages[stage].b[s], &mb.tmB[s], &tail->full[stage],
                                     kc * kTileK, te.Jp * kTileN);
                     }
                 }
@@ -158,8 +180,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             const MmaProb &pr = probs[te.prob];
             if (!tile_active(pr.st)) continue;
             const SolveState *st = pr.st;
-            const int S = (st->kind == kTcSplit) ? 2 : 1;
-            const int nk = (pr.n + kTileK - 1) / kTileK;
+            const int S = (step_kind(st) == kTcSplit) ? 2 : 1;
+            const int nk = step_chunks(st, pr.n);
             for (int kc = 0; kc < nk; ++kc) {
                 const uint32_t buf = chunk & 1u;
                 const uint32_t cph = (chunk >> 1) & 1u;
@@ -235,7 +257,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             if (!tile_active(pr.st)) continue;
             const SolveState *st = pr.st;
             const int n = pr.n;
-            const int nk = (n + kTileK - 1) / kTileK;
+            const int nk = step_chunks(st, n);
             float acc[128];
 #pragma unroll
             for (int c = 0; c < 128; ++c) acc[c] = 0.0f;
@@ -277,20 +299,18 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             }
 
             // ---- store phase for block J = 2 Jp + h
-            const float alpha = st->alpha, sigma = st->sigma, inv_s2 = st->inv_s2;
-            const float s_next = st->s_next;
-            const float r1 = st->r1, r0 = st->r0;
-            const int oset = st->cur ^ 1;
-            float *__restrict__ Y = pr.Y;
-            const int ldy = pr.ldy, lds = pr.lds;
-            __half *__restrict__ o0 = pr.sl[oset][0];
-            __half *__restrict__ o1 = pr.sl[oset][1];
+            const ProdOp &op = st->op;
+            const float inv = op.inv;
+            const int ldy = pr.ldy, lds = pr.lds, ldx = pr.ldx;
+            const float *E1 = (op.E1 >= 0) ? pr.mats[op.E1].master : nullptr;
+            const float *E2 = (op.E2 >= 0) ? pr.mats[op.E2].master : nullptr;
+            const int nout = op.nout, pout = op.part_out;
+            const float ra = op.ra, rb = op.rb, rc = op.rc;
             const int i = te.I * kTileM + row_local;
             const int J = 2 * te.Jp + h;
-            double tr = 0.0, sq = 0.0, mx = 0.0, rr = 0.0;
+            double tr = 0.0, sq = 0.0, tr1 = 0.0, rr = 0.0;
             if (J >= te.I && J * kTileM < n && i < n) {
                 const bool diag = (J == te.I);
-                float *yrow = Y + static_cast<size_t>(i) * ldy;
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) {
                     const int j0 = J * kTileM + c4 * 32;
@@ -299,29 +319,51 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                     for (int u = 0; u < 32; ++u) {
                         const int j = j0 + u;
                         if (j < n && (!diag || j >= i)) {
-                            const float yo = yrow[j];
-                            const float p2 = acc[c4 * 32 + u] * inv_s2;  // (Y^2)_ij
-                            const float yn = fmaf(alpha, yo, sigma * p2);
-                            // (X^2 - X)_ij of the input iterate X = c I + Y
-                            const float r = fmaf(r1, yo, p2) + ((j == i) ? r0 : 0.0f);
-                            const float ys = yn * s_next;
-                            const __half hh = __float2half_rn(ys);
-                            const __half ll = __float2half_rn(ys - __half2float(hh));
-                            yrow[j] = yn;
-                            o0[static_cast<size_t>(i) * lds + j] = hh;
-                            o1[static_cast<size_t>(i) * lds + j] = ll;
-                            if (j != i) {
-                                Y[static_cast<size_t>(j) * ldy + i] = yn;
-                                o0[static_cast<size_t>(j) * lds + i] = hh;
-                                o1[static_cast<size_t>(j) * lds + i] = ll;
-                                csq = fmaf(2.0f * yn, yn, csq);
-                                crr = fmaf(2.0f * r, r, crr);
-                            } else {
-                                tr += static_cast<double>(yn);
-                                csq = fmaf(yn, yn, csq);
-                                crr = fmaf(r, r, crr);
+                            const bool on_diag = (j == i);
+                            const float w2 = on_diag ? 1.0f : 2.0f;  // off-diagonal counts twice
+                            const size_t at = static_cast<size_t>(i) * ldy + j;
+                            const size_t mt = static_cast<size_t>(j) * ldy + i;
+                            const float v = acc[c4 * 32 + u] * inv;
+                            const float e1 = E1 ? E1[at] : 0.0f;
+                            const float e2 = E2 ? E2[at] : 0.0f;
+                            for (int o = 0; o < nout; ++o) {
+                                const OutSpec &os = op.out[o];
+                                const int fl = os.flags;
+                                if (fl & (kOutF64a | kOutF64b)) {
+                                    const double d = static_cast<double>(os.a) * v +
+                                                     static_cast<double>(os.b1) * e1 +
+                                                     static_cast<double>(os.b2) * e2 +
+                                                     (on_diag ? os.c : 0.0);
+                                    double *X = pr.Xd[(fl & kOutF64a) ? 0 : 1];
+                                    X[static_cast<size_t>(i) * ldx + j] = d;
+                                    if (!on_diag) X[static_cast<size_t>(j) * ldx + i] = d;
+                                    if (o == pout) {
+                                        if (on_diag) tr += d;
+                                        sq += w2 * d * d;
+                                    }
+                                    if (o == 1 && on_diag) tr1 += d;
+                                    continue;
+                                }
+                                const float val = fmaf(os.a, v, fmaf(os.b1, e1, os.b2 * e2)) +
+                                                  (on_diag ? static_cast<float>(os.c) : 0.0f);
+                                const MatSlot &m = pr.mats[os.mat];
+                                if (fl & kOutMaster) {
+                                    m.master[at] = val;
+                                    if (!on_diag) m.master[mt] = val;
+                                }
+                                if (fl & kOutSlices) {
+                                    const float ys = val * os.s;
+                                    put_slices(m, static_cast<size_t>(i) * lds + j, ys);
+                                    if (!on_diag) put_slices(m, static_cast<size_t>(j) * lds + i, ys);
+                                }
+                                if (o == pout) {
+                                    if (on_diag) tr += static_cast<double>(val);
+                                    csq = fmaf(w2 * val, val, csq);
+                                }
+                                if (o == 1 && on_diag) tr1 += static_cast<double>(val);
                             }
-                            mx = fmax(mx, static_cast<double>(fabsf(yn)));
+                            const float r = fmaf(ra, v, rb * e1) + (on_diag ? rc : 0.0f);
+                            crr = fmaf(w2 * r, r, crr);
                         }
                     }
                     sq += static_cast<double>(csq);
@@ -331,12 +373,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             // deterministic per-tile partials: warp tree, then the 8 warps in order
             tr = warp_sum(tr);
             sq = warp_sum(sq);
-            mx = warp_max(mx);
+            tr1 = warp_sum(tr1);
             rr = warp_sum(rr);
             if (lane == 0) {
                 tail->red[ew][0] = tr;
                 tail->red[ew][1] = sq;
-                tail->red[ew][2] = mx;
+                tail->red[ew][2] = tr1;
                 tail->red[ew][3] = rr;
             }
             epi_bar();
@@ -345,7 +387,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                 for (int w = 0; w < kEpiWarps; ++w) {
                     a += tail->red[w][0];
                     b += tail->red[w][1];
-                    c = fmax(c, tail->red[w][2]);
+                    c += tail->red[w][2];
                     d += tail->red[w][3];
                 }
                 double *slot = pr.part + static_cast<size_t>(te.slot) * kPartStride;

@@ -85,6 +85,26 @@ __global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *r
         st->cur = 0;
         st->xcur = 0;
         st->x_fp64 = (st->prec == kPrecFp64) ? 1 : 0;
+        if (st->method == kMethodFermi) {
+            // z0 = (beta0 / 2)(H - mu0 I) with mu0 = tr H / n and the number of
+            // doublings m chosen so that |z0| <= t0 = 1e-3 on the Gershgorin
+            // interval: then z0 = tanh(beta0 (H - mu0)/2) to a relative 1e-7/3
+            // in the logit, an error the doublings carry over unchanged.
+            const double mu0 = s_tr[0] / n;
+            const double rad = fmax(fabs(s_lo[0] - mu0), fabs(s_hi[0] - mu0));
+            const double beta = 1.0 / st->kT;
+            const double t0 = 1e-3;
+            int m = 0;
+            if (beta * rad / 2.0 > t0) m = static_cast<int>(ceil(log2(beta * rad / (2.0 * t0))));
+            st->beta = beta;
+            st->ft_m = m;
+            st->beta0 = ldexp(beta, -m);
+            st->mu_t = mu0;
+            st->sc[kMatZ] = 0.0;
+            int ez;
+            frexp(fmax(st->beta0 * rad / 2.0, 1e-300) * 1.0001, &ez);
+            st->scl[kMatZ] = static_cast<float>(ldexp(1.0, 14 - ez));
+        }
     }
 }
 
@@ -100,6 +120,9 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
     const double dshift = st->emax * inv_w - st->c;  // diagonal of Y0 gets +dshift
     const float s0 = st->s_cur;
     const bool fp64 = (st->prec == kPrecFp64);
+    const bool fermi = (st->method == kMethodFermi);
+    const double hb0 = 0.5 * st->beta0, mu0 = st->mu_t;
+    const float sz = st->scl[kMatZ];
     double tr = 0.0, sq = 0.0, mx = 0.0;
     const long long total = static_cast<long long>(n) * n;
     for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
@@ -107,7 +130,18 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
         const int i = static_cast<int>(e / n);
         const int j = static_cast<int>(e - static_cast<long long>(i) * n);
         const double h = pr.H[static_cast<long long>(i) * pr.ldh + j];
-        if (fp64) {
+        if (fermi) {
+            // z0~ = (beta0 / 2)(H - mu0 I); its identity part is 0
+            const float zf = static_cast<float>(hb0 * (h - ((i == j) ? mu0 : 0.0)));
+            const MatSlot &mz = pr.mats[kMatZ];
+            mz.master[static_cast<long long>(i) * pr.ldy + j] = zf;
+            const float zs = zf * sz;
+            const __half hh = __float2half_rn(zs);
+            mz.sl[0][static_cast<long long>(i) * pr.lds + j] = hh;
+            mz.sl[1][static_cast<long long>(i) * pr.lds + j] = __float2half_rn(zs - __half2float(hh));
+            if (i == j) tr += zf;
+            sq += static_cast<double>(zf) * zf;
+        } else if (fp64) {
             const double x = ((i == j) ? st->emax - h : -h) * inv_w;
             pr.Xd[0][static_cast<long long>(i) * pr.ldx + j] = x;
             if (i == j) tr += x;
@@ -119,8 +153,9 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
             pr.Y[static_cast<long long>(i) * pr.ldy + j] = yf;
             const float ys = yf * s0;
             const __half hh = __float2half_rn(ys);
-            pr.sl[0][0][static_cast<long long>(i) * pr.lds + j] = hh;
-            pr.sl[0][1][static_cast<long long>(i) * pr.lds + j] = __float2half_rn(ys - __half2float(hh));
+            const MatSlot &my = pr.mats[kMatY0];
+            my.sl[0][static_cast<long long>(i) * pr.lds + j] = hh;
+            my.sl[1][static_cast<long long>(i) * pr.lds + j] = __float2half_rn(ys - __half2float(hh));
             if (i == j) tr += yf;
             sq += static_cast<double>(yf) * yf;
             mx = fmax(mx, fabs(static_cast<double>(yf)));
@@ -143,8 +178,9 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
         double *slot = pr.part + static_cast<size_t>(blockIdx.x) * kPartStride;
         slot[0] = a;
         slot[1] = b;
-        slot[2] = c;
+        slot[2] = 0.0;
         slot[3] = 0.0;
+        (void)c;
     }
 }
 
@@ -153,9 +189,14 @@ __global__ void k_finalize(const MmaProb *probs, int prob, double *D, long long 
     const MmaProb &pr = probs[prob];
     const SolveState *st = pr.st;
     const int n = pr.n;
+    const bool fermi = st->method == kMethodFermi;
     const bool from_x = st->x_fp64 != 0;
     const double *X = pr.Xd[st->xcur];
     const double c = st->c;
+    // finite temperature: D = D0 + gamma Q (D0 = (I - z)/2 in Xd[0], Q = D0 - D0^2
+    // in Xd[1]); gamma from the exact FP64 traces of the stored D0 and Q makes
+    // tr D = N_e.  It is the first-order change of D for mu -> mu + gamma/beta.
+    const double gamma = (fermi && st->tr_q > 0.0) ? (st->ne - st->tr_d0) / st->tr_q : 0.0;
     double tr = 0.0, eb = 0.0;
     const long long total = static_cast<long long>(n) * n;
     for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
@@ -163,7 +204,10 @@ __global__ void k_finalize(const MmaProb *probs, int prob, double *D, long long 
         const int i = static_cast<int>(e / n);
         const int j = static_cast<int>(e - static_cast<long long>(i) * n);
         double d;
-        if (from_x) {
+        if (fermi) {
+            const long long at = static_cast<long long>(i) * pr.ldx + j;
+            d = pr.Xd[0][at] + gamma * pr.Xd[1][at];
+        } else if (from_x) {
             d = X[static_cast<long long>(i) * pr.ldx + j];
         } else {
             d = static_cast<double>(pr.Y[static_cast<long long>(i) * pr.ldy + j]) + (i == j ? c : 0.0);
@@ -207,6 +251,8 @@ __global__ void k_finalize_reduce(const MmaProb *probs, int prob) {
     if (t == 0) {
         st->trace = s_tr[0];
         st->e_band = s_eb[0];
+        if (st->method == kMethodFermi && st->tr_q > 0.0)
+            st->mu = st->mu_t + (st->ne - st->tr_d0) / st->tr_q / st->beta;
     }
 }
 

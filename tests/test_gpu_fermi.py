@@ -1,0 +1,85 @@
+"""Finite-temperature expansion through the C ABI against the oracle's exact
+Fermi-Dirac density matrix (Sec. II-A).
+
+Tolerances: ||D - D_ref||_F / sqrt(N_e) <= 1e-6, |E_band - E_ref| / N_e <= 1e-7,
+|tr D - N_e| <= 1e-9.  D_ref = Q f Q^T from the oracle's own eigensolver at
+small n, from the known construction of Hp otherwise (sampled entries and
+random probes at the full size)."""
+import math
+
+import numpy as np
+import pytest
+
+import hp_synth
+import oracle
+from gpu_util import ctx, torch
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
+
+TOL_EPS1, TOL_E, TOL_TR = 1e-6, 1e-7, 1e-9
+
+
+@pytest.mark.parametrize("n,ne,kT,seed", [(300, 255.0, 0.02, 7), (517, 440.5, 0.01, 8),
+                                          (1000, 850.0, 0.003, 9)])
+def test_fermi_matches_oracle(n, ne, kT, seed):
+    p = hp_synth.smeared(n, ne, kT, -2.0, 1.0, seed)
+    D = np.zeros_like(p.H)
+    r = ctx().solve(p.H, ne, kT=kT, D=D)
+    ref = oracle.density(p.H, ne, kT)            # own eigensolver + bisection for mu
+    eps1 = np.linalg.norm(D - ref["D"]) / math.sqrt(ne)
+    e_err = abs(r["e_band"] - ref["e_band"]) / ne
+    print(n, kT, r["iters"], eps1, e_err, r["mu"], ref["mu"])
+    assert r["status"] == 0
+    assert eps1 <= TOL_EPS1 and e_err <= TOL_E
+    assert abs(np.trace(D) - ne) <= TOL_TR
+    assert abs(r["trace"] - ne) <= TOL_TR
+    assert abs(r["mu"] - ref["mu"]) <= 1e-2 * kT    # chemical potential reported
+    ev = np.linalg.eigvalsh(D)
+    assert ev.min() > -1e-6 and ev.max() < 1 + 1e-6
+
+
+def test_fermi_high_temperature_and_device_pointers():
+    p = hp_synth.smeared(256, 100.25, 0.5, -2.0, 1.0, 12)
+    Hd = torch.from_numpy(p.H).cuda()
+    Dd = torch.empty_like(Hd)
+    r = ctx().solve(Hd, p.ne, kT=0.5, D=Dd)
+    ref = oracle.density(p.H, p.ne, 0.5)
+    assert np.linalg.norm(Dd.cpu().numpy() - ref["D"]) / math.sqrt(p.ne) <= TOL_EPS1
+    assert abs(r["trace"] - p.ne) <= TOL_TR
+
+
+def test_fermi_rejects_zero_temperature():
+    import paper_2301_04642_gb300 as fe
+    p = hp_synth.gapped(64, 32, (-3.0, -0.01), (0.01, 1.0), 3)
+    with pytest.raises(fe.FeError) as ei:
+        ctx().solve(p.H, 32, kT=0.0, method=fe.FE_METHOD_FERMI)
+    assert ei.value.status == fe.FE_EINVAL
+
+
+def test_fermi_config_n16384():
+    """The full finite-temperature workload: n=16384, semicircle [-2, 1] Ha,
+    N_e=14000, kT=0.003 Ha.  Checked by the exact trace, the band energy
+    against sum f_i lambda_i, sampled entries of Q f Q^T, and ||D - D_ref||_F
+    estimated with random probes (E ||(D - D_ref) v||^2 = ||D - D_ref||_F^2)."""
+    p = hp_synth.workload_n16384_ft(device="cuda")
+    lam = p.lam
+    f, mu = oracle.occupations(lam, p.ne, p.kT)
+    H = p.H
+    D = torch.empty_like(H)
+    r = ctx().solve(H, p.ne, kT=p.kT, D=D)
+    assert r["status"] == 0
+    assert abs(r["trace"] - p.ne) <= TOL_TR
+    e_ref = float(np.sum(f * lam))
+    assert abs(r["e_band"] - e_ref) / p.ne <= TOL_E
+    Q = p.Q.cpu().numpy()
+    Dh = D.cpu().numpy()
+    rng = np.random.default_rng(5)
+    rows, cols = rng.integers(0, p.n, 2000), rng.integers(0, p.n, 2000)
+    want = oracle.density_entries(Q, f, rows, cols)
+    assert np.abs(Dh[rows, cols] - want).max() <= 1e-6
+    V = rng.standard_normal((p.n, 4))
+    err = Dh @ V - Q @ (f[:, None] * (Q.T @ V))
+    eps1 = math.sqrt(np.sum(err ** 2) / 4) / math.sqrt(p.ne)
+    print(r, eps1, abs(r["mu"] - mu))
+    assert eps1 <= TOL_EPS1

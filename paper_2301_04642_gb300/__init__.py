@@ -182,6 +182,43 @@ class Context:
             raise FeError(rc, self.last_error())
         return rc, [r.as_dict() for r in res]
 
+    # ---- continuous batching -------------------------------------------------
+    def submit(self, H, ne, kT=0.0, tol=0.0, D=None, precision="mixed", method=FE_METHOD_AUTO):
+        """Queue one problem; returns its ticket.  H may be reused at once; D
+        (if given) must stay alive until poll() returns a final status."""
+        p, keep = self._problem(H, ne, kT, tol, D, precision, method)
+        t = ctypes.c_uint64()
+        rc = self.L.fe_submit(self.h, ctypes.byref(p), ctypes.byref(t))
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+        self._keep = getattr(self, "_keep", {})
+        self._keep[t.value] = keep[1]
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending; else the result dict (with 'rc')."""
+        r = FeResult()
+        rc = self.L.fe_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if rc == FE_PENDING:
+            return None
+        if rc == FE_EINVAL and r.status == 0:
+            raise FeError(rc, self.last_error())
+        getattr(self, "_keep", {}).pop(ticket, None)
+        out = r.as_dict()
+        out["rc"] = rc
+        return out
+
+    def wait(self, ticket, timeout_s=600.0, sleep_s=0.0005):
+        import time
+        t0 = time.time()
+        while True:
+            res = self.poll(ticket)
+            if res is not None:
+                return res
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError("ticket %d still pending" % ticket)
+            time.sleep(sleep_s)
+
     # ---- single kernels (device buffers) -------------------------------------
     def gershgorin(self, H):
         hp, hdev, _ = _ptr(H)

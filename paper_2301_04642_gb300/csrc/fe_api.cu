@@ -36,7 +36,8 @@ using namespace fe;
 
 namespace {
 
-thread_local std::string g_create_err;
+// last failure of a call made by this thread (any context)
+thread_local std::string g_err;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -73,17 +74,11 @@ struct Slot {
     MmaProb hp;  // host image of the device descriptor (H filled per solve)
 };
 
-}  // namespace
-
-struct fe_ctx {
-    int device = 0;
+// Launch state of one stream of work: device copies of the problem table and
+// tile lists, pinned images of the solve states, error word, events.
+struct Engine {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    size_t budget = 0, used = 0;
-    int max_iters = 100;
-    uint32_t prec_default = FE_PREC_MIXED;
-    int num_sms = 148;
-    std::string err;
     int *d_err = nullptr;
     MmaProb *d_probs = nullptr;
     size_t probs_cap = 0;
@@ -91,31 +86,61 @@ struct fe_ctx {
     size_t tiles_cap = 0;
     Tile64 *d_tiles64 = nullptr;
     size_t tiles64_cap = 0;
-    SolveState *h_states = nullptr;  // pinned copies read back at the end
+    SolveState *h_states = nullptr;  // pinned
     size_t h_states_cap = 0;
-    std::vector<Slot *> slots;
+    int *h_done = nullptr;           // pinned copies of the done flags (serving)
+    size_t h_done_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int ntc = 0, n64 = 0;            // tile counts of the uploaded lists
+    bool any_tc = false, any_fp64 = false;
+};
+
+// One fe_submit request.
+struct Req {
+    fe_ticket id = 0;
+    fe_problem p{};                 // Hp points at hbuf (host) or at the slot's copy (device)
+    std::vector<double> hbuf;       // host copy of Hp while no slot is free
+    Slot *slot = nullptr;
+    bool staged = false;            // Hp already copied into slot->Hcopy
+    bool done = false;
+    fe_result res{};
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+}  // namespace
+
+struct fe_ctx {
+    int device = 0;
+    size_t budget = 0, used = 0;
+    int max_iters = 100;
+    uint32_t prec_default = FE_PREC_MIXED;
+    int num_sms = 148;
+    Engine eng;                      // blocking solves and batches
+    std::mutex smu;                  // slots, used
+    std::vector<Slot *> slots;
     // optional per-launch timing of the expansion kernels (fe_k_profile)
     bool prof = false;
     std::vector<cudaEvent_t> pev;
     double prof_out[8] = {};
-    long long launches = 0;  // kernels launched by this context
-    std::recursive_mutex mu;
-    // continuous batching (fe_submit / fe_poll)
-    struct Req;
-    std::deque<Req *> queue;
-    std::map<fe_ticket, Req *> reqs;
+    std::atomic<long long> launches{0};  // kernels launched by this context
+    std::recursive_mutex mu;  // eng, profiling state (blocking calls)
+    // continuous batching (fe_submit / fe_poll): a worker thread with its own engine
+    Engine seng;
+    cudaStream_t copy_stream = nullptr;
+    std::mutex qmu;
+    std::condition_variable qcv;
+    std::deque<Req *> waiting;       // submitted, not yet started
+    std::map<fe_ticket, Req *> reqs; // every ticket not yet collected by fe_poll
     fe_ticket next_ticket = 1;
     std::thread worker;
-    std::condition_variable_any cv;
+    bool worker_started = false;
     bool stop = false;
 };
 
 namespace {
 
-int set_err(fe_ctx *ctx, int code, const std::string &msg) {
-    if (ctx) ctx->err = msg;
-    else g_create_err = msg;
+int set_err(fe_ctx *, int code, const std::string &msg) {
+    g_err = msg;
     return code;
 }
 
@@ -191,6 +216,12 @@ int encode_map(fe_ctx *ctx, CUtensorMap *m, void *base, int n, int ld_elems, int
     return FE_OK;
 }
 
+void release_slot(fe_ctx *ctx, Slot *s) {
+    std::lock_guard<std::mutex> lk(ctx->smu);
+    s->in_use = false;
+}
+
+// caller holds ctx->smu
 void free_slot(fe_ctx *ctx, Slot *s) {
     if (s->arena) cudaFree(s->arena);
     ctx->used -= s->bytes;
@@ -198,8 +229,9 @@ void free_slot(fe_ctx *ctx, Slot *s) {
 }
 
 // A free slot for dimension n and method (reused if cached), or an error
-// status with ctx->err set.
+// status with the error string set.
 int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
+    std::lock_guard<std::mutex> lk(ctx->smu);
     for (Slot *s : ctx->slots)
         if (!s->in_use && s->n == n && s->method == method) {
             s->in_use = true;
@@ -382,150 +414,266 @@ void init_state(const fe_ctx *ctx, const fe_problem *p, SolveState *st) {
         st->ft_sub = 0;  // z0 fresh
     }
 }
+// ---------------------------------------------------------------- engine
+// A set of problems on acquired slots runs as: eng_upload (problem table and
+// tile lists of every problem in the set), eng_setup per newly started
+// problem (Hp staging, state, bounds and X0 kernels, first control step),
+// eng_steps (tensor-core step, FP64-accurate step, control step; repeated),
+// eng_finish per finished problem (output kernels, read-back of its state).
+// Kernels reach a problem's buffers and state through its table entry, so the
+// table can be rebuilt between steps as problems join and leave; the tiles of
+// one problem are computed the same way whatever else is in the table, so a
+// problem's result does not depend on its batch.
 
-// Run a set of validated problems on acquired slots; fills results.
-int run_problems(fe_ctx *ctx, const std::vector<const fe_problem *> &ps, std::vector<Slot *> &ss,
-                 fe_result *rs) {
-    const int np = static_cast<int>(ps.size());
-    cudaStream_t s = ctx->stream;
-    // pinned state images
-    if (ctx->h_states_cap < static_cast<size_t>(np)) {
-        if (ctx->h_states) cudaFreeHost(ctx->h_states);
-        ctx->h_states = nullptr;
-        ctx->h_states_cap = 0;
-        FE_CUDA(ctx, cudaMallocHost(&ctx->h_states, sizeof(SolveState) * np));
-        ctx->h_states_cap = np;
+// One problem bound to a slot.
+struct Job {
+    const fe_problem *p = nullptr;  // the caller's problem (D and its flag, n_e, kT, tol)
+    Slot *slot = nullptr;
+    const double *H = nullptr;      // device Hp the kernels read
+    int64_t ldh = 0;
+    const double *stage = nullptr;  // host Hp copied into slot->Hcopy at set-up, or null
+    int64_t ldstage = 0;
+};
+
+Job make_job(const fe_problem *p, Slot *s) {
+    Job j;
+    j.p = p;
+    j.slot = s;
+    if (p->flags & FE_PTR_DEVICE) {
+        j.H = p->Hp;
+        j.ldh = p->ld;
+    } else {
+        j.H = s->Hcopy;
+        j.ldh = p->n;
+        j.stage = p->Hp;
+        j.ldstage = p->ld;
     }
+    return j;
+}
+
+template <typename T>
+int ensure_pinned(fe_ctx *ctx, T **ptr, size_t *cap, size_t count) {
+    if (count <= *cap) return FE_OK;
+    if (*ptr) cudaFreeHost(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    const size_t c = std::max<size_t>(count, 4);
+    FE_CUDA(ctx, cudaMallocHost(reinterpret_cast<void **>(ptr), sizeof(T) * c));
+    *cap = c;
+    return FE_OK;
+}
+
+int eng_init(fe_ctx *ctx, Engine &e, cudaStream_t user_stream) {
+    if (user_stream) {
+        e.stream = user_stream;
+    } else {
+        FE_CUDA(ctx, cudaStreamCreateWithFlags(&e.stream, cudaStreamNonBlocking));
+        e.own_stream = true;
+    }
+    FE_CUDA(ctx, cudaMalloc(&e.d_err, sizeof(int)));
+    FE_CUDA(ctx, cudaEventCreate(&e.ev0));
+    FE_CUDA(ctx, cudaEventCreate(&e.ev1));
+    return FE_OK;
+}
+
+void eng_free(Engine &e) {
+    if (e.stream) cudaStreamSynchronize(e.stream);
+    if (e.d_err) cudaFree(e.d_err);
+    if (e.d_probs) cudaFree(e.d_probs);
+    if (e.d_tiles) cudaFree(e.d_tiles);
+    if (e.d_tiles64) cudaFree(e.d_tiles64);
+    if (e.h_states) cudaFreeHost(e.h_states);
+    if (e.h_done) cudaFreeHost(e.h_done);
+    if (e.ev0) cudaEventDestroy(e.ev0);
+    if (e.ev1) cudaEventDestroy(e.ev1);
+    if (e.own_stream && e.stream) cudaStreamDestroy(e.stream);
+    e = Engine();
+}
+
+int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
+    const int np = static_cast<int>(jobs.size());
     std::vector<MmaProb> hprobs(np);
     std::vector<TileEnt> tiles;
     std::vector<Tile64> tiles64;
-    bool any_tc = false, any_fp64 = false;
-    int total_iters = 0;
+    e.any_tc = e.any_fp64 = false;
     for (int k = 0; k < np; ++k) {
-        const fe_problem *p = ps[k];
-        Slot *sl = ss[k];
-        hprobs[k] = sl->hp;
-        const int n = static_cast<int>(p->n);
-        // Hp: use the caller's device buffer in place, otherwise stage a copy
-        if (p->flags & FE_PTR_DEVICE) {
-            hprobs[k].H = p->Hp;
-            hprobs[k].ldh = p->ld;
-        } else {
-            FE_CUDA(ctx, cudaMemcpy2DAsync(sl->Hcopy, sizeof(double) * n, p->Hp,
-                                           sizeof(double) * p->ld, sizeof(double) * n, n,
-                                           cudaMemcpyHostToDevice, s));
-            hprobs[k].H = sl->Hcopy;
-            hprobs[k].ldh = n;
+        const Job &j = jobs[k];
+        hprobs[k] = j.slot->hp;
+        hprobs[k].H = j.H;
+        hprobs[k].ldh = j.ldh;
+        const bool fermi = method_of(j.p) == kMethodFermi;
+        const uint32_t pr = prec_of(ctx, j.p);
+        if (pr != FE_PREC_FP64 || fermi) {
+            e.any_tc = true;
+            for (TileEnt t : j.slot->tiles) { t.prob = k; tiles.push_back(t); }
         }
-        init_state(ctx, p, &ctx->h_states[k]);
-        FE_CUDA(ctx, cudaMemcpyAsync(sl->st, &ctx->h_states[k], sizeof(SolveState),
-                                     cudaMemcpyHostToDevice, s));
-        const int pr = ctx->h_states[k].prec;
-        const bool fermi = ctx->h_states[k].method == kMethodFermi;
-        if (pr != kPrecFp64 || fermi) {
-            any_tc = true;
-            for (TileEnt t : sl->tiles) { t.prob = k; tiles.push_back(t); }
+        if (pr != FE_PREC_FP32 && !fermi) {
+            e.any_fp64 = true;
+            for (Tile64 t : j.slot->tiles64) { t.prob = k; tiles64.push_back(t); }
         }
-        if (pr != kPrecFp32 && !fermi) {
-            any_fp64 = true;
-            for (Tile64 t : sl->tiles64) { t.prob = k; tiles64.push_back(t); }
-        }
-        total_iters = std::max(total_iters, ctx->h_states[k].max_iters);
     }
-    int rc = ensure_dev(ctx, &ctx->d_probs, &ctx->probs_cap, np);
-    if (rc == FE_OK) rc = ensure_dev(ctx, &ctx->d_tiles, &ctx->tiles_cap, tiles.size());
-    if (rc == FE_OK) rc = ensure_dev(ctx, &ctx->d_tiles64, &ctx->tiles64_cap, tiles64.size());
+    int rc = ensure_dev(ctx, &e.d_probs, &e.probs_cap, np);
+    if (rc == FE_OK) rc = ensure_dev(ctx, &e.d_tiles, &e.tiles_cap, tiles.size());
+    if (rc == FE_OK) rc = ensure_dev(ctx, &e.d_tiles64, &e.tiles64_cap, tiles64.size());
+    if (rc == FE_OK) rc = ensure_pinned(ctx, &e.h_states, &e.h_states_cap, np);
+    if (rc == FE_OK) rc = ensure_pinned(ctx, &e.h_done, &e.h_done_cap, np + 1);  // + error word
     if (rc != FE_OK) return rc;
-    FE_CUDA(ctx, cudaMemcpyAsync(ctx->d_probs, hprobs.data(), sizeof(MmaProb) * np,
-                                 cudaMemcpyHostToDevice, s));
+    FE_CUDA(ctx, cudaMemcpyAsync(e.d_probs, hprobs.data(), sizeof(MmaProb) * np,
+                                 cudaMemcpyHostToDevice, e.stream));
     if (!tiles.empty())
-        FE_CUDA(ctx, cudaMemcpyAsync(ctx->d_tiles, tiles.data(), sizeof(TileEnt) * tiles.size(),
-                                     cudaMemcpyHostToDevice, s));
+        FE_CUDA(ctx, cudaMemcpyAsync(e.d_tiles, tiles.data(), sizeof(TileEnt) * tiles.size(),
+                                     cudaMemcpyHostToDevice, e.stream));
     if (!tiles64.empty())
-        FE_CUDA(ctx, cudaMemcpyAsync(ctx->d_tiles64, tiles64.data(),
-                                     sizeof(Tile64) * tiles64.size(), cudaMemcpyHostToDevice, s));
-    FE_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+        FE_CUDA(ctx, cudaMemcpyAsync(e.d_tiles64, tiles64.data(), sizeof(Tile64) * tiles64.size(),
+                                     cudaMemcpyHostToDevice, e.stream));
+    // the copies read host vectors that go out of scope here
+    FE_CUDA(ctx, cudaStreamSynchronize(e.stream));
+    e.ntc = static_cast<int>(tiles.size());
+    e.n64 = static_cast<int>(tiles64.size());
+    return FE_OK;
+}
 
-    FE_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
-    for (int k = 0; k < np; ++k) {
-        const int n = static_cast<int>(ps[k]->n);
-        FE_CUDA(ctx, cudaMemsetAsync(ss[k]->bad, 0, sizeof(int), s));
-        k_bounds_rows<<<ceil_div(n, 8), 256, 0, s>>>(ctx->d_probs, k, ss[k]->rowinfo, ss[k]->bad);
+// Set-up of the problems at table positions [k0, k1): Hp staging, initial
+// state, bounds, X0 and the first control step.
+int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int k1) {
+    if (k1 <= k0) return FE_OK;
+    cudaStream_t s = e.stream;
+    for (int k = k0; k < k1; ++k) {
+        const Job &j = jobs[k];
+        const int n = static_cast<int>(j.p->n);
+        if (j.stage)
+            FE_CUDA(ctx, cudaMemcpy2DAsync(j.slot->Hcopy, sizeof(double) * n, j.stage,
+                                           sizeof(double) * j.ldstage, sizeof(double) * n, n,
+                                           cudaMemcpyHostToDevice, s));
+        init_state(ctx, j.p, &e.h_states[k]);
+        FE_CUDA(ctx, cudaMemcpyAsync(j.slot->st, &e.h_states[k], sizeof(SolveState),
+                                     cudaMemcpyHostToDevice, s));
+        FE_CUDA(ctx, cudaMemsetAsync(j.slot->bad, 0, sizeof(int), s));
+        k_bounds_rows<<<ceil_div(n, 8), 256, 0, s>>>(e.d_probs, k, j.slot->rowinfo, j.slot->bad);
+        k_bounds_reduce<<<1, 1024, 0, s>>>(e.d_probs, k, j.slot->rowinfo, j.slot->bad);
+        k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
         ctx->launches += 3;
-        k_bounds_reduce<<<1, 1024, 0, s>>>(ctx->d_probs, k, ss[k]->rowinfo, ss[k]->bad);
-        k_init_x0<<<kInitBlocks, 256, 0, s>>>(ctx->d_probs, k);
     }
-    const int ntc = static_cast<int>(tiles.size());
-    const int n64 = static_cast<int>(tiles64.size());
-    const int grid_tc = std::max(1, std::min(ntc, ctx->num_sms));
-    const int grid_64 = std::max(1, std::min(n64, 4 * ctx->num_sms));
+    k_control<<<k1 - k0, 256, 0, s>>>(e.d_probs + k0, k1 - k0);
+    ++ctx->launches;
+    // the state images must stay valid until their copies ran
+    FE_CUDA(ctx, cudaStreamSynchronize(s));
+    return FE_OK;
+}
+
+// `count` expansion steps over every problem in the table; with `pev` each
+// tensor-core and FP64 launch is bracketed by events (4 per step).
+void eng_steps(fe_ctx *ctx, Engine &e, int np, int count, const std::vector<cudaEvent_t> *pev) {
+    cudaStream_t s = e.stream;
+    const int grid_tc = std::max(1, std::min(e.ntc, ctx->num_sms));
+    const int grid_64 = std::max(1, std::min(e.n64, 4 * ctx->num_sms));
     const size_t smem = mma_smem_bytes();
-    // one loop iteration = control + product; +8 covers the phase hand-offs
+    for (int it = 0; it < count; ++it) {
+        if (pev) cudaEventRecord((*pev)[4 * it + 0], s);
+        if (e.any_tc) {
+            k_sym_mma<<<grid_tc, kMmaThreads, smem, s>>>(e.d_probs, e.d_tiles, e.ntc, e.d_err);
+            ++ctx->launches;
+        }
+        if (pev) cudaEventRecord((*pev)[4 * it + 1], s);
+        if (pev) cudaEventRecord((*pev)[4 * it + 2], s);
+        if (e.any_fp64) {
+            k_fp64_step<<<grid_64, 256, 0, s>>>(e.d_probs, e.d_tiles64, e.n64);
+            ++ctx->launches;
+        }
+        if (pev) cudaEventRecord((*pev)[4 * it + 3], s);
+        k_control<<<np, 256, 0, s>>>(e.d_probs, np);
+        ++ctx->launches;
+    }
+}
+
+// Output kernels of the problem at table position k and the read-back of its
+// state into e.h_states[k] (asynchronous).
+int eng_finish(fe_ctx *ctx, Engine &e, int k, const Job &j) {
+    cudaStream_t s = e.stream;
+    const fe_problem *p = j.p;
+    double *dout = nullptr;
+    long long ldd = p->n;
+    if (p->D) {
+        if (p->flags & FE_PTR_DEVICE) {
+            dout = p->D;
+            ldd = p->ld;
+        } else {
+            dout = j.slot->Dtmp;
+        }
+    }
+    k_finalize<<<kFinBlocks, 256, 0, s>>>(e.d_probs, k, dout, ldd);
+    k_finalize_reduce<<<1, 512, 0, s>>>(e.d_probs, k);
+    ctx->launches += 2;
+    if (p->D && !(p->flags & FE_PTR_DEVICE))
+        FE_CUDA(ctx, cudaMemcpy2DAsync(p->D, sizeof(double) * p->ld, j.slot->Dtmp,
+                                       sizeof(double) * p->n, sizeof(double) * p->n, p->n,
+                                       cudaMemcpyDeviceToHost, s));
+    FE_CUDA(ctx, cudaMemcpyAsync(&e.h_states[k], j.slot->st, sizeof(SolveState),
+                                 cudaMemcpyDeviceToHost, s));
+    return FE_OK;
+}
+
+void fill_result(const SolveState &st, int herr, double ms, fe_result &r) {
+    memset(&r, 0, sizeof(r));
+    r.status = st.status == 0 ? FE_OK : st.status;
+    if (herr != 0) r.status = FE_ETIMEOUT;
+    r.iters = st.iter;
+    for (int q = 0; q < 3; ++q) r.iters_by_phase[q] = st.it_phase[q];
+    if (st.method == kMethodFermi) r.iters_by_phase[3] = st.ft_stage;
+    r.e_band = st.e_band;
+    r.trace = st.trace;
+    r.idem_fro = st.idem_fro;
+    r.mu = st.mu;
+    r.eps_min = st.emin;
+    r.eps_max = st.emax;
+    r.ms = ms;
+}
+
+// Run validated problems on acquired slots to completion (blocking calls).
+int run_problems(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) {
+    Engine &e = ctx->eng;
+    const int np = static_cast<int>(jobs.size());
+    cudaStream_t s = e.stream;
+    int rc = eng_upload(ctx, e, jobs);
+    if (rc != FE_OK) return rc;
+    FE_CUDA(ctx, cudaMemsetAsync(e.d_err, 0, sizeof(int), s));
+    FE_CUDA(ctx, cudaEventRecord(e.ev0, s));
+    rc = eng_setup(ctx, e, jobs, 0, np);
+    if (rc != FE_OK) return rc;
+    int total_iters = 0;
+    for (int k = 0; k < np; ++k) total_iters = std::max(total_iters, e.h_states[k].max_iters);
+    // one step = product + control; +8 covers the phase hand-offs
     const int nloop = total_iters + 8;
     if (ctx->prof) {
         while (ctx->pev.size() < static_cast<size_t>(4 * nloop)) {
-            cudaEvent_t e;
-            FE_CUDA(ctx, cudaEventCreate(&e));
-            ctx->pev.push_back(e);
+            cudaEvent_t ev;
+            FE_CUDA(ctx, cudaEventCreate(&ev));
+            ctx->pev.push_back(ev);
         }
     }
-    for (int it = 0; it < nloop; ++it) {
-        k_control<<<np, 256, 0, s>>>(ctx->d_probs, np);
-        ++ctx->launches;
-        if (ctx->prof) cudaEventRecord(ctx->pev[4 * it + 0], s);
-        if (any_tc) {
-            k_sym_mma<<<grid_tc, kMmaThreads, smem, s>>>(ctx->d_probs, ctx->d_tiles, ntc, ctx->d_err);
-            ++ctx->launches;
-        }
-        if (ctx->prof) cudaEventRecord(ctx->pev[4 * it + 1], s);
-        if (ctx->prof) cudaEventRecord(ctx->pev[4 * it + 2], s);
-        if (any_fp64) {
-            k_fp64_step<<<grid_64, 256, 0, s>>>(ctx->d_probs, ctx->d_tiles64, n64);
-            ++ctx->launches;
-        }
-        if (ctx->prof) cudaEventRecord(ctx->pev[4 * it + 3], s);
-    }
-    k_control<<<np, 256, 0, s>>>(ctx->d_probs, np);
-    ctx->launches += 1 + 3 * static_cast<long long>(np) + 1;
+    eng_steps(ctx, e, np, nloop, ctx->prof ? &ctx->pev : nullptr);
     for (int k = 0; k < np; ++k) {
-        const fe_problem *p = ps[k];
-        double *dout = nullptr;
-        long long ldd = p->n;
-        if (p->D) {
-            if (p->flags & FE_PTR_DEVICE) {
-                dout = p->D;
-                ldd = p->ld;
-            } else {
-                dout = ss[k]->Dtmp;
-            }
-        }
-        k_finalize<<<kFinBlocks, 256, 0, s>>>(ctx->d_probs, k, dout, ldd);
-        k_finalize_reduce<<<1, 512, 0, s>>>(ctx->d_probs, k);
+        rc = eng_finish(ctx, e, k, jobs[k]);
+        if (rc != FE_OK) return rc;
     }
-    FE_CUDA(ctx, cudaEventRecord(ctx->ev1, s));
+    FE_CUDA(ctx, cudaEventRecord(e.ev1, s));
     FE_CUDA(ctx, cudaGetLastError());
-    for (int k = 0; k < np; ++k) {
-        const fe_problem *p = ps[k];
-        if (p->D && !(p->flags & FE_PTR_DEVICE))
-            FE_CUDA(ctx, cudaMemcpy2DAsync(p->D, sizeof(double) * p->ld, ss[k]->Dtmp,
-                                           sizeof(double) * p->n, sizeof(double) * p->n, p->n,
-                                           cudaMemcpyDeviceToHost, s));
-        FE_CUDA(ctx, cudaMemcpyAsync(&ctx->h_states[k], ss[k]->st, sizeof(SolveState),
-                                     cudaMemcpyDeviceToHost, s));
-    }
     int herr = 0;
-    FE_CUDA(ctx, cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(ctx, cudaMemcpyAsync(&herr, e.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     FE_CUDA(ctx, cudaStreamSynchronize(s));
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    cudaEventElapsedTime(&ms, e.ev0, e.ev1);
     if (ctx->prof) {
         // launches that did work: the phases run in order (single FP16, split,
         // FP64), so the first it_phase[0] + it_phase[1] tensor-core launches
-        // and the it_phase[2] FP64 launches after them were active
+        // and the it_phase[2] FP64 launches after them were active; a
+        // finite-temperature solve uses the tensor cores for every step
         int tc_active = 0, fp_active = 0;
         for (int k = 0; k < np; ++k) {
-            tc_active = std::max(tc_active, ctx->h_states[k].it_phase[0] + ctx->h_states[k].it_phase[1]);
-            fp_active = std::max(fp_active, ctx->h_states[k].it_phase[2]);
+            const SolveState &st = e.h_states[k];
+            const int tc = (st.method == kMethodFermi) ? st.iter : st.it_phase[0] + st.it_phase[1];
+            tc_active = std::max(tc_active, tc);
+            fp_active = std::max(fp_active, st.method == kMethodFermi ? 0 : st.it_phase[2]);
         }
         double tc_ms = 0, fp_ms = 0, tc_all = 0;
         for (int it = 0; it < nloop; ++it) {
@@ -541,32 +689,179 @@ int run_problems(fe_ctx *ctx, const std::vector<const fe_problem *> &ps, std::ve
         ctx->prof_out[2] = fp_ms;
         ctx->prof_out[3] = fp_active;
         ctx->prof_out[4] = ms;
-        ctx->prof_out[5] = static_cast<double>(ctx->launches);
+        ctx->prof_out[5] = static_cast<double>(ctx->launches.load());
         ctx->prof_out[6] = tc_all;
-        ctx->prof_out[7] = any_tc ? nloop : 0;
+        ctx->prof_out[7] = e.any_tc ? nloop : 0;
     }
     int first_bad = FE_OK;
     for (int k = 0; k < np; ++k) {
-        const SolveState &st = ctx->h_states[k];
-        fe_result &r = rs[k];
-        memset(&r, 0, sizeof(r));
-        r.status = st.status == 0 ? FE_OK : st.status;
-        if (herr != 0) r.status = FE_ETIMEOUT;
-        r.iters = st.iter;
-        for (int q = 0; q < 3; ++q) r.iters_by_phase[q] = st.it_phase[q];
-        r.e_band = st.e_band;
-        r.trace = st.trace;
-        r.idem_fro = st.idem_fro;
-        r.mu = st.mu;
-        r.eps_min = st.emin;
-        r.eps_max = st.emax;
-        r.ms = ms;
-        if (r.status != FE_OK && first_bad == FE_OK) first_bad = r.status;
+        fill_result(e.h_states[k], herr, ms, rs[k]);
+        if (rs[k].status != FE_OK && first_bad == FE_OK) first_bad = rs[k].status;
     }
     if (herr != 0) set_err(ctx, FE_ETIMEOUT, "device wait timed out (code " + std::to_string(herr) + ")");
     else if (first_bad == FE_EINVAL) set_err(ctx, FE_EINVAL, "NaN or Inf in Hp");
     else if (first_bad == FE_ENOTCONV) set_err(ctx, FE_ENOTCONV, "iteration cap reached");
     return first_bad;
+}
+
+// ---------------------------------------------------------------- serving
+// Continuous batching behind fe_submit / fe_poll.  One worker thread owns a
+// second engine (its own stream).  Each tick it starts the waiting requests
+// that fit the free part of the HBM budget (first fit, in submission order),
+// runs kServeSteps expansion steps over every running request at once, reads
+// the done flags, and finishes the requests that converged (D written, slot
+// released, result published for fe_poll).  Requests therefore join and
+// leave the batch at step granularity, and short solves are not held back by
+// long ones.
+
+constexpr int kServeSteps = 8;
+constexpr size_t kMaxTickets = 1 << 16;
+constexpr double kAdmitWaitMs = 60000.0;
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Publish a final result; the worker does not touch r afterwards.
+void publish(fe_ctx *ctx, Req *r, const fe_result &res) {
+    std::lock_guard<std::mutex> lk(ctx->qmu);
+    r->res = res;
+    r->res.ms = ms_since(r->t_submit);
+    r->done = true;
+}
+
+void fail_req(fe_ctx *ctx, Req *r, int status) {
+    if (r->slot) release_slot(ctx, r->slot);
+    r->slot = nullptr;
+    fe_result res;
+    memset(&res, 0, sizeof(res));
+    res.status = status;
+    publish(ctx, r, res);
+}
+
+Job job_of(Req *r) {
+    Job j;
+    j.p = &r->p;
+    j.slot = r->slot;
+    j.H = r->slot->Hcopy;
+    j.ldh = r->p.n;
+    if (!r->staged) {
+        j.stage = r->hbuf.data();
+        j.ldstage = r->p.n;
+    }
+    return j;
+}
+
+void serve_loop(fe_ctx *ctx) {
+    cudaSetDevice(ctx->device);
+    Engine &e = ctx->seng;
+    std::vector<Req *> running;
+    for (;;) {
+        std::vector<Req *> cand;
+        {
+            std::unique_lock<std::mutex> lk(ctx->qmu);
+            ctx->qcv.wait(lk, [&] { return ctx->stop || !ctx->waiting.empty() || !running.empty(); });
+            if (ctx->stop) break;
+            cand.assign(ctx->waiting.begin(), ctx->waiting.end());
+        }
+        // admission, outside the queue lock (slot allocation may call cudaMalloc)
+        std::vector<Req *> started, failed;
+        for (Req *r : cand) {
+            if (!r->slot) {
+                Slot *s = nullptr;
+                if (acquire_slot(ctx, static_cast<int>(r->p.n), method_of(&r->p), &s) != FE_OK) {
+                    // blocking solves may hold the memory for a while; with
+                    // nothing of ours running, give up after kAdmitWaitMs
+                    if (running.empty() && ms_since(r->t_submit) > kAdmitWaitMs) failed.push_back(r);
+                    continue;
+                }
+                r->slot = s;
+            }
+            started.push_back(r);
+        }
+        if (!started.empty() || !failed.empty()) {
+            std::lock_guard<std::mutex> lk(ctx->qmu);
+            auto gone = [&](Req *r) {
+                return std::find(started.begin(), started.end(), r) != started.end() ||
+                       std::find(failed.begin(), failed.end(), r) != failed.end();
+            };
+            ctx->waiting.erase(std::remove_if(ctx->waiting.begin(), ctx->waiting.end(), gone),
+                               ctx->waiting.end());
+        }
+        for (Req *r : failed) fail_req(ctx, r, FE_ENOMEM);
+        if (running.empty() && started.empty()) {
+            // requests wait for memory held elsewhere: poll again shortly
+            std::unique_lock<std::mutex> lk(ctx->qmu);
+            ctx->qcv.wait_for(lk, std::chrono::milliseconds(2));
+            continue;
+        }
+
+        const int k0 = static_cast<int>(running.size());
+        std::vector<Req *> all = running;
+        all.insert(all.end(), started.begin(), started.end());
+        std::vector<Job> jobs;
+        for (Req *r : all) jobs.push_back(job_of(r));
+        const int np = static_cast<int>(all.size());
+        int rc = FE_OK;
+        if (!started.empty()) {
+            rc = eng_upload(ctx, e, jobs);
+            if (rc == FE_OK) rc = eng_setup(ctx, e, jobs, k0, np);
+        }
+        int herr = 0;
+        if (rc == FE_OK) {
+            cudaMemsetAsync(e.d_err, 0, sizeof(int), e.stream);
+            eng_steps(ctx, e, np, kServeSteps, nullptr);
+            for (int k = 0; k < np; ++k)
+                cudaMemcpyAsync(&e.h_done[k], &all[k]->slot->st->done, sizeof(int),
+                                cudaMemcpyDeviceToHost, e.stream);
+            cudaMemcpyAsync(&e.h_done[np], e.d_err, sizeof(int), cudaMemcpyDeviceToHost, e.stream);
+            const cudaError_t ce = cudaStreamSynchronize(e.stream);
+            if (ce != cudaSuccess) rc = cuda_fail(ctx, ce, "serving step");
+            else herr = e.h_done[np];
+        }
+        if (rc != FE_OK || herr != 0) {
+            for (Req *r : all) fail_req(ctx, r, rc != FE_OK ? rc : FE_ETIMEOUT);
+            running.clear();
+            continue;
+        }
+        // finish the converged ones
+        std::vector<Req *> next;
+        std::vector<int> fin;
+        for (int k = 0; k < np; ++k) {
+            if (e.h_done[k]) fin.push_back(k);
+            else next.push_back(all[k]);
+        }
+        for (int k : fin) {
+            rc = eng_finish(ctx, e, k, jobs[k]);
+            if (rc != FE_OK) break;
+        }
+        if (rc == FE_OK && !fin.empty()) {
+            const cudaError_t ce = cudaStreamSynchronize(e.stream);
+            if (ce != cudaSuccess) rc = cuda_fail(ctx, ce, "serving finish");
+        }
+        for (int k : fin) {
+            Req *r = all[k];
+            fe_result res;
+            fill_result(e.h_states[k], 0, 0.0, res);
+            if (rc != FE_OK) res.status = rc;
+            release_slot(ctx, r->slot);
+            r->slot = nullptr;
+            publish(ctx, r, res);
+        }
+        running.swap(next);
+        if (!fin.empty() && !running.empty()) {
+            // rebuild the table without the finished requests
+            std::vector<Job> rest;
+            for (Req *r : running) rest.push_back(job_of(r));
+            if (eng_upload(ctx, e, rest) != FE_OK) {
+                for (Req *r : running) fail_req(ctx, r, FE_ECUDA);
+                running.clear();
+            }
+        }
+    }
+    // shutting down: let queued work drain from the stream; fe_destroy frees the rest
+    cudaStreamSynchronize(e.stream);
+    for (Req *r : running) release_slot(ctx, r->slot);
 }
 
 }  // namespace
@@ -599,19 +894,17 @@ extern "C" int fe_create(fe_ctx **out, const fe_config *cfg) {
     size_t freeb = 0, totalb = 0;
     cudaMemGetInfo(&freeb, &totalb);
     ctx->budget = c.hbm_budget_bytes ? c.hbm_budget_bytes : static_cast<size_t>(0.8 * freeb);
-    if (c.cuda_stream) {
-        ctx->stream = static_cast<cudaStream_t>(c.cuda_stream);
-    } else {
-        cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
-        ctx->own_stream = true;
-    }
-    if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
-        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
-        cudaFuncSetAttribute(k_sym_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(mma_smem_bytes())) != cudaSuccess) {
-        const cudaError_t e2 = cudaGetLastError();
+    int rc = eng_init(ctx, ctx->eng, static_cast<cudaStream_t>(c.cuda_stream));
+    if (rc == FE_OK) rc = eng_init(ctx, ctx->seng, nullptr);
+    if (rc == FE_OK && cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = set_err(nullptr, FE_ECUDA, "copy stream");
+    if (rc == FE_OK && cudaFuncSetAttribute(k_sym_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(mma_smem_bytes())) != cudaSuccess)
+        rc = set_err(nullptr, FE_ECUDA, std::string("context setup: ") + cudaGetErrorString(cudaGetLastError()));
+    if (rc != FE_OK) {
+        const std::string why = g_err;
         fe_destroy(ctx);
-        return set_err(nullptr, FE_ECUDA, std::string("context setup: ") + cudaGetErrorString(e2));
+        return set_err(nullptr, rc, why);
     }
     *out = ctx;
     return FE_OK;
@@ -620,26 +913,26 @@ extern "C" int fe_create(fe_ctx **out, const fe_config *cfg) {
 extern "C" int fe_destroy(fe_ctx *ctx) {
     if (!ctx) return FE_OK;
     {
-        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        std::lock_guard<std::mutex> lk(ctx->qmu);
         ctx->stop = true;
     }
-    ctx->cv.notify_all();
+    ctx->qcv.notify_all();
     if (ctx->worker.joinable()) ctx->worker.join();
     cudaSetDevice(ctx->device);
-    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    eng_free(ctx->eng);
+    eng_free(ctx->seng);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    for (auto &kv : ctx->reqs) delete kv.second;
+    ctx->reqs.clear();
     for (Slot *s : ctx->slots) {
         if (s->arena) cudaFree(s->arena);
         delete s;
     }
     ctx->slots.clear();
-    if (ctx->d_err) cudaFree(ctx->d_err);
-    if (ctx->d_probs) cudaFree(ctx->d_probs);
-    if (ctx->d_tiles) cudaFree(ctx->d_tiles);
-    if (ctx->d_tiles64) cudaFree(ctx->d_tiles64);
-    if (ctx->h_states) cudaFreeHost(ctx->h_states);
-    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
-    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
-    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    for (cudaEvent_t ev : ctx->pev) cudaEventDestroy(ev);
     delete ctx;
     return FE_OK;
 }
@@ -656,10 +949,9 @@ extern "C" int fe_solve(fe_ctx *ctx, const fe_problem *p, fe_result *r) {
     Slot *s = nullptr;
     rc = acquire_slot(ctx, static_cast<int>(p->n), method_of(p), &s);
     if (rc != FE_OK) return r->status = rc;
-    std::vector<const fe_problem *> ps{p};
-    std::vector<Slot *> ss{s};
-    rc = run_problems(ctx, ps, ss, r);
-    s->in_use = false;
+    std::vector<Job> jobs{make_job(p, s)};
+    rc = run_problems(ctx, jobs, r);
+    release_slot(ctx, s);
     if (r->status == FE_OK && rc != FE_OK) r->status = rc;
     return rc;
 }
@@ -670,8 +962,7 @@ extern "C" int fe_solve_batch(fe_ctx *ctx, int count, const fe_problem *ps, fe_r
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     if (count == 0) return FE_OK;
     cudaSetDevice(ctx->device);
-    std::vector<const fe_problem *> pv;
-    std::vector<Slot *> sv;
+    std::vector<Job> jobs;
     std::vector<int> idx;
     int first = FE_OK;
     for (int k = 0; k < count; ++k) {
@@ -684,25 +975,102 @@ extern "C" int fe_solve_batch(fe_ctx *ctx, int count, const fe_problem *ps, fe_r
             if (first == FE_OK) first = rc;
             continue;
         }
-        pv.push_back(&ps[k]);
-        sv.push_back(s);
+        jobs.push_back(make_job(&ps[k], s));
         idx.push_back(k);
     }
-    if (!pv.empty()) {
-        std::vector<fe_result> tmp(pv.size());
-        const int rc = run_problems(ctx, pv, sv, tmp.data());
-        for (size_t q = 0; q < pv.size(); ++q) {
+    if (!jobs.empty()) {
+        std::vector<fe_result> tmp(jobs.size());
+        const int rc = run_problems(ctx, jobs, tmp.data());
+        for (size_t q = 0; q < jobs.size(); ++q) {
             rs[idx[q]] = tmp[q];
-            sv[q]->in_use = false;
+            release_slot(ctx, jobs[q].slot);
         }
         if (first == FE_OK) first = rc;
     }
     return first;
 }
 
-extern "C" const char *fe_last_error_string(const fe_ctx *ctx) {
-    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+extern "C" int fe_submit(fe_ctx *ctx, const fe_problem *p, fe_ticket *t) {
+    if (!ctx || !t) return set_err(nullptr, FE_EINVAL, "ctx or ticket pointer is NULL");
+    *t = 0;
+    int rc = validate(ctx, p);
+    if (rc != FE_OK) return rc;
+    const int n = static_cast<int>(p->n);
+    const int method = method_of(p);
+    {
+        int a, b, c;
+        size_t np;
+        if (slot_bytes(n, method, &a, &b, &c, &np) > ctx->budget)
+            return set_err(ctx, FE_ENOMEM, "problem needs more than the whole HBM budget");
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        if (ctx->stop) return set_err(ctx, FE_EINVAL, "context is shutting down");
+        if (ctx->reqs.size() >= kMaxTickets) return set_err(ctx, FE_EBUSY, "too many outstanding tickets");
+    }
+    cudaSetDevice(ctx->device);
+    Req *r = new Req();
+    r->p = *p;
+    r->t_submit = std::chrono::steady_clock::now();
+    const bool dev = (p->flags & FE_PTR_DEVICE) != 0;
+    const size_t row = sizeof(double) * n;
+    Slot *s = nullptr;
+    cudaError_t ce = cudaSuccess;
+    if (acquire_slot(ctx, n, method, &s) == FE_OK) {
+        // copy Hp straight into the slot
+        ce = cudaMemcpy2DAsync(s->Hcopy, row, p->Hp, sizeof(double) * p->ld, row, n,
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->copy_stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->copy_stream);
+        r->slot = s;
+        r->staged = true;
+    } else {
+        // no room now: keep a host copy until a slot frees up
+        r->hbuf.resize(static_cast<size_t>(n) * n);
+        if (dev) {
+            ce = cudaMemcpy2DAsync(r->hbuf.data(), row, p->Hp, sizeof(double) * p->ld, row, n,
+                                   cudaMemcpyDeviceToHost, ctx->copy_stream);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->copy_stream);
+        } else {
+            for (int i = 0; i < n; ++i)
+                memcpy(r->hbuf.data() + static_cast<size_t>(i) * n, p->Hp + static_cast<size_t>(i) * p->ld, row);
+        }
+    }
+    if (ce != cudaSuccess) {
+        if (r->slot) release_slot(ctx, r->slot);
+        delete r;
+        return cuda_fail(ctx, ce, "fe_submit copy of Hp");
+    }
+    r->p.Hp = nullptr;  // the caller's Hp is not referenced after this point
+    {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        r->id = ctx->next_ticket++;
+        ctx->reqs[r->id] = r;
+        ctx->waiting.push_back(r);
+        if (!ctx->worker_started) {
+            ctx->worker = std::thread(serve_loop, ctx);
+            ctx->worker_started = true;
+        }
+        *t = r->id;
+    }
+    ctx->qcv.notify_one();
+    return FE_OK;
 }
+
+extern "C" int fe_poll(fe_ctx *ctx, fe_ticket t, fe_result *r) {
+    if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->qmu);
+    auto it = ctx->reqs.find(t);
+    if (it == ctx->reqs.end()) return set_err(ctx, FE_EINVAL, "unknown ticket");
+    Req *q = it->second;
+    if (!q->done) return FE_PENDING;
+    if (r) *r = q->res;
+    const int status = q->res.status;
+    ctx->reqs.erase(it);
+    delete q;
+    return status;
+}
+
+extern "C" const char *fe_last_error_string(const fe_ctx *) { return g_err.c_str(); }
 
 // ============================================================== kernel-level entry points
 
@@ -710,6 +1078,7 @@ extern "C" int fe_k_gershgorin(fe_ctx *ctx, const double *H, int64_t n, int64_t 
     if (!ctx || !H || !out4 || n < 1 || ld < n) return set_err(ctx, FE_EINVAL, "bad arguments");
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
+    Engine &eg = ctx->eng;
     Slot *s = nullptr;
     int rc = acquire_slot(ctx, static_cast<int>(n), kMethodSp2, &s);
     if (rc != FE_OK) return rc;
@@ -719,18 +1088,19 @@ extern "C" int fe_k_gershgorin(fe_ctx *ctx, const double *H, int64_t n, int64_t 
     SolveState st0;
     memset(&st0, 0, sizeof(st0));
     st0.n = static_cast<int>(n);
-    rc = ensure_dev(ctx, &ctx->d_probs, &ctx->probs_cap, 1);
-    if (rc != FE_OK) { s->in_use = false; return rc; }
-    cudaStream_t q = ctx->stream;
+    rc = ensure_dev(ctx, &eg.d_probs, &eg.probs_cap, 1);
+    if (rc != FE_OK) { release_slot(ctx, s); return rc; }
+    cudaStream_t q = eg.stream;
     SolveState res;
-    cudaMemcpyAsync(ctx->d_probs, &hp, sizeof(MmaProb), cudaMemcpyHostToDevice, q);
+    cudaMemcpyAsync(eg.d_probs, &hp, sizeof(MmaProb), cudaMemcpyHostToDevice, q);
     cudaMemcpyAsync(s->st, &st0, sizeof(SolveState), cudaMemcpyHostToDevice, q);
     cudaMemsetAsync(s->bad, 0, sizeof(int), q);
-    k_bounds_rows<<<ceil_div(static_cast<int>(n), 8), 256, 0, q>>>(ctx->d_probs, 0, s->rowinfo, s->bad);
-    k_bounds_reduce<<<1, 1024, 0, q>>>(ctx->d_probs, 0, s->rowinfo, s->bad);
+    k_bounds_rows<<<ceil_div(static_cast<int>(n), 8), 256, 0, q>>>(eg.d_probs, 0, s->rowinfo, s->bad);
+    k_bounds_reduce<<<1, 1024, 0, q>>>(eg.d_probs, 0, s->rowinfo, s->bad);
+    ctx->launches += 2;
     cudaMemcpyAsync(&res, s->st, sizeof(SolveState), cudaMemcpyDeviceToHost, q);
     const cudaError_t e = cudaStreamSynchronize(q);
-    s->in_use = false;
+    release_slot(ctx, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gershgorin");
     out4[0] = res.emin;
     out4[1] = res.emax;
@@ -746,14 +1116,15 @@ extern "C" int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t l
         return set_err(ctx, FE_EINVAL, "bad arguments");
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
+    Engine &eg = ctx->eng;
     Slot *s = nullptr;
     int rc = acquire_slot(ctx, static_cast<int>(n), kMethodSp2, &s);
     if (rc != FE_OK) return rc;
-    cudaStream_t q = ctx->stream;
+    cudaStream_t q = eg.stream;
     int e2;
     frexp(bound, &e2);
     const float scale = static_cast<float>(ldexp(1.0, 14 - e2));
-    // master <- Y (the epilogue then overwrites it with 0 * Y + 1 * Y^2)
+    // master <- Y (the epilogue then overwrites it with 1 * Y^2)
     cudaMemcpy2DAsync(s->Y, sizeof(float) * s->ldy, Y, sizeof(float) * ldy, sizeof(float) * n, n,
                       cudaMemcpyDeviceToDevice, q);
     k_make_slices<<<kInitBlocks, 256, 0, q>>>(s->Y, static_cast<int>(n), s->ldy, scale,
@@ -774,35 +1145,28 @@ extern "C" int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t l
     op.out[0].flags = kOutMaster | kOutSlices;
     op.out[0].a = 1.0f;
     op.out[0].s = 1.0f;
-    rc = ensure_dev(ctx, &ctx->d_probs, &ctx->probs_cap, 1);
-    if (rc == FE_OK) rc = ensure_dev(ctx, &ctx->d_tiles, &ctx->tiles_cap, s->tiles.size());
-    if (rc != FE_OK) { s->in_use = false; return rc; }
+    rc = ensure_dev(ctx, &eg.d_probs, &eg.probs_cap, 1);
+    if (rc == FE_OK) rc = ensure_dev(ctx, &eg.d_tiles, &eg.tiles_cap, s->tiles.size());
+    if (rc != FE_OK) { release_slot(ctx, s); return rc; }
     MmaProb hp = s->hp;
-    cudaMemcpyAsync(ctx->d_probs, &hp, sizeof(MmaProb), cudaMemcpyHostToDevice, q);
-    cudaMemcpyAsync(ctx->d_tiles, s->tiles.data(), sizeof(TileEnt) * s->tiles.size(),
+    cudaMemcpyAsync(eg.d_probs, &hp, sizeof(MmaProb), cudaMemcpyHostToDevice, q);
+    cudaMemcpyAsync(eg.d_tiles, s->tiles.data(), sizeof(TileEnt) * s->tiles.size(),
                     cudaMemcpyHostToDevice, q);
     cudaMemcpyAsync(s->st, &st0, sizeof(SolveState), cudaMemcpyHostToDevice, q);
-    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), q);
+    cudaMemsetAsync(eg.d_err, 0, sizeof(int), q);
     const int nt = static_cast<int>(s->tiles.size());
     k_sym_mma<<<std::min(nt, ctx->num_sms), kMmaThreads, mma_smem_bytes(), q>>>(
-        ctx->d_probs, ctx->d_tiles, nt, ctx->d_err);
+        eg.d_probs, eg.d_tiles, nt, eg.d_err);
+    ctx->launches += 2;
     cudaMemcpy2DAsync(C, sizeof(float) * ldc, s->Y, sizeof(float) * s->ldy, sizeof(float) * n, n,
                       cudaMemcpyDeviceToDevice, q);
     int herr = 0;
-    cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, q);
+    cudaMemcpyAsync(&herr, eg.d_err, sizeof(int), cudaMemcpyDeviceToHost, q);
     const cudaError_t e = cudaStreamSynchronize(q);
-    s->in_use = false;
+    release_slot(ctx, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sym_square");
     if (herr) return set_err(ctx, FE_ETIMEOUT, "device wait timed out (code " + std::to_string(herr) + ")");
     return FE_OK;
-}
-
-extern "C" int fe_submit(fe_ctx *ctx, const fe_problem *, fe_ticket *) {
-    return set_err(ctx, FE_EINVAL, "fe_submit not available in this build");
-}
-
-extern "C" int fe_poll(fe_ctx *ctx, fe_ticket, fe_result *) {
-    return set_err(ctx, FE_EINVAL, "fe_poll not available in this build");
 }
 
 extern "C" int fe_k_profile(fe_ctx *ctx, int enable) {
@@ -821,17 +1185,17 @@ extern "C" int fe_k_profile_read(fe_ctx *ctx, double *out8) {
 
 extern "C" int fe_k_launch_count(fe_ctx *ctx, int64_t *out) {
     if (!ctx || !out) return set_err(ctx, FE_EINVAL, "bad arguments");
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    *out = ctx->launches;
+    *out = ctx->launches.load();
     return FE_OK;
 }
 
 extern "C" int fe_k_history(fe_ctx *ctx, int index, double *out, int max_rows, int *rows) {
     if (!ctx || !out || !rows || max_rows < 0 || index < 0) return set_err(ctx, FE_EINVAL, "bad arguments");
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (!ctx->h_states || static_cast<size_t>(index) >= ctx->h_states_cap)
+    const Engine &eg = ctx->eng;
+    if (!eg.h_states || static_cast<size_t>(index) >= eg.h_states_cap)
         return set_err(ctx, FE_EINVAL, "no such problem in the last solve");
-    const SolveState &st = ctx->h_states[index];
+    const SolveState &st = eg.h_states[index];
     const int r = std::min({st.iter + 1, kHistRows, max_rows});
     for (int i = 0; i < r; ++i)
         for (int j = 0; j < kHistCols; ++j) out[i * kHistCols + j] = st.hist[i][j];

@@ -151,10 +151,12 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
             // Polishing products come in pairs of opposite branches, the second
             // carrying the exact trace correction (below); after a pair the
             // deviations are about the square of fro_hist[0] = ||X^2 - X||_F of
-            // the pair's second input.
+            // the pair's second input.  The trace must also have landed: when
+            // the correction was not admissible (deviations of both signs
+            // cancel in tr(X - X^2)), the next pair squares what is left.
             const double f0 = st->fro_hist[0];
             if (nfp64 >= 2 && (nfp64 & 1) == 0 &&
-                ((f0 * f0 <= 5e-9 && fabs(idem) <= 1e-8) || nfp64 >= 6))
+                ((f0 * f0 <= 5e-9 && fabs(idem) <= 1e-8 && fabs(t1 - ne) <= 2e-10) || nfp64 >= 6))
                 done = true;
         }
     }

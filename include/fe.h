@@ -23,7 +23,10 @@
  *   - Hp must be symmetric with both triangles stored (rows are read whole).
  *   - Pointers are host or device pointers as the problem's flags say
  *     (FE_PTR_HOST / FE_PTR_DEVICE); device pointers must belong to the
- *     context's device.  The caller owns Hp and D.
+ *     context's device.  The caller owns Hp and D.  A context's work is
+ *     ordered only after earlier work on its own stream (fe_config's
+ *     cuda_stream, else a non-blocking stream it creates): device inputs
+ *     written on other streams must be complete before the call.
  *   - Every call returns an FE_* status; no call exits, throws or traps.
  *     fe_last_error_string() gives a one-line reason for the last failure.
  *   - A context is used by one host thread at a time, except fe_submit /

@@ -24,6 +24,24 @@ extern "C" {
  * NaN/Inf else 0.0. */
 FE_API int fe_k_gershgorin(fe_ctx *ctx, const double *H, int64_t n, int64_t ld, double *out4);
 
+/* The Gershgorin bounds of fe_k_gershgorin without a context, through a path
+ * that allocates nothing.  No counterpart in the paper: it serves callers that
+ * cannot allocate device memory where they need the bounds (a framework whose
+ * caching pool owns the GPU's memory, or a latency-critical loop that must not
+ * hit the device-wide synchronisation of cudaMalloc / cudaFree).
+ * H and out4 are DEVICE pointers on the current device; out4 receives the
+ * same 4 doubles as fe_k_gershgorin.  The work is queued on cuda_stream (NULL:
+ * the legacy default stream) and the call returns without waiting; out4 is
+ * ready when that stream reaches this point.  Per-row scratch lives in one
+ * fixed device array of 32768 rows (1 MiB) per device: n > 32768 returns
+ * FE_EINVAL.  All calls on a device share that array, so calls that overlap
+ * in time race; calls ordered on one stream do not.  The first call on a
+ * device (with it current) looks up the array's address, which may load the
+ * module; make that first call before any stream capture.
+ * Errors: FE_EINVAL (NULL pointers, n < 1, ld < n, n too large), FE_ECUDA. */
+FE_API int fe_k_gershgorin_noalloc(const double *H, int64_t n, int64_t ld, double *out4,
+                                   void *cuda_stream);
+
 /* C = Y * Y for a symmetric FP32 matrix Y, computed by the tensor-core kernel
  * of the SP2 step (Sec. II-B1 Eq. (1); the product is the dominant cost,
  * Sec. III-B): Y is scaled by a power of two s with s * bound <= 2^14 and

@@ -73,13 +73,14 @@ def load(build=True):
     L.fe_last_error_string.restype = ctypes.c_char_p
     L.fe_k_gershgorin.argtypes = [P, P, i64, i64, ctypes.POINTER(dbl)]
     L.fe_k_sym_square.argtypes = [P, P, i64, i64, P, i64, ctypes.c_int, dbl]
+    L.fe_k_gershgorin_noalloc.argtypes = [P, i64, i64, P, P]
     L.fe_k_profile.argtypes = [P, ctypes.c_int]
     L.fe_k_profile_read.argtypes = [P, ctypes.POINTER(dbl)]
     L.fe_k_launch_count.argtypes = [P, ctypes.POINTER(i64)]
     L.fe_k_history.argtypes = [P, ctypes.c_int, ctypes.POINTER(dbl), ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int)]
     for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
-                 "fe_k_gershgorin", "fe_k_sym_square", "fe_k_profile", "fe_k_profile_read",
+                 "fe_k_gershgorin", "fe_k_gershgorin_noalloc", "fe_k_sym_square", "fe_k_profile", "fe_k_profile_read",
                  "fe_k_launch_count", "fe_k_history"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -100,6 +101,40 @@ def _ptr(x):
     if isinstance(x, torch.Tensor):
         return x.data_ptr(), x.is_cuda, x
     raise TypeError("expected a numpy array or torch tensor")
+
+
+def _ready(*xs):
+    """A context runs on its own non-blocking stream, which is not ordered
+    after torch's: wait until torch's current stream has written the device
+    tensors handed to the library."""
+    import sys
+    torch = sys.modules.get("torch")
+    if torch is None:
+        return
+    for x in xs:
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            torch.cuda.current_stream(x.device).synchronize()
+            return
+
+
+def gershgorin_noalloc(H, out4, stream=None):
+    """Gershgorin bounds of a device FP64 matrix H into the device tensor out4
+    (4 doubles), through the entry point that allocates nothing and needs no
+    context (for callers whose memory is owned by their own pool, or who must
+    not trigger cudaMalloc's device-wide synchronisation).  Queued on `stream`
+    (a raw cudaStream_t; default: torch's current stream) without waiting.
+    Calls that overlap in time share one scratch array and race."""
+    L = load()
+    hp, hdev, _ = _ptr(H)
+    op, odev, _ = _ptr(out4)
+    if not (hdev and odev):
+        raise ValueError("device tensors expected")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = L.fe_k_gershgorin_noalloc(hp, H.shape[0], H.stride(0), op, ctypes.c_void_p(stream))
+    if rc != FE_OK:
+        raise FeError(rc, L.fe_last_error_string(None).decode())
 
 
 class Context:
@@ -151,6 +186,7 @@ class Context:
                 raise ValueError("Hp and D must share the leading dimension")
         flags = (FE_PTR_DEVICE if hdev else FE_PTR_HOST) | PREC[precision] | method
         p = FeProblem(hp, n, ld, float(ne), float(kT), float(tol), dp, flags)
+        _ready(H, D)
         return p, (keep_h, keep_d)
 
     def solve(self, H, ne, kT=0.0, tol=0.0, D=None, precision="mixed", method=FE_METHOD_AUTO,
@@ -224,6 +260,7 @@ class Context:
         hp, hdev, _ = _ptr(H)
         assert hdev, "device tensor expected"
         out = (ctypes.c_double * 4)()
+        _ready(H)
         rc = self.L.fe_k_gershgorin(self.h, hp, H.shape[0], H.stride(0), out)
         if rc != FE_OK:
             raise FeError(rc, self.last_error())
@@ -235,6 +272,7 @@ class Context:
         assert ydev and cdev, "device tensors expected"
         if bound is None:
             bound = float(Y.abs().max())
+        _ready(Y, C)
         rc = self.L.fe_k_sym_square(self.h, yp, Y.shape[0], Y.stride(0), cp, C.stride(0),
                                     int(nslices), float(bound))
         if rc != FE_OK:

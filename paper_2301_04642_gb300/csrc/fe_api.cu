@@ -1072,6 +1072,11 @@ extern "C" int fe_poll(fe_ctx *ctx, fe_ticket t, fe_result *r) {
 
 extern "C" const char *fe_last_error_string(const fe_ctx *) { return g_err.c_str(); }
 
+int fe::set_error_string(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
 // ============================================================== kernel-level entry points
 
 extern "C" int fe_k_gershgorin(fe_ctx *ctx, const double *H, int64_t n, int64_t ld, double *out4) {

@@ -1,5 +1,7 @@
 // Kernel entry points and the device-visible problem descriptors.
 #pragma once
+#include <string>
+
 #include "fe_dev.cuh"
 
 namespace fe {
@@ -86,5 +88,8 @@ __global__ void k_make_slices(const float *Y, int n, int ldy, float s, __half *h
 constexpr int kInitBlocks = 304;   // 2 x 152 SMs
 constexpr int kFinBlocks = 304;
 constexpr int kTile64 = 64;
+
+// Record msg as the calling thread's last error (fe_last_error_string); returns code.
+int set_error_string(int code, const std::string &msg);
 
 }  // namespace fe

@@ -57,6 +57,7 @@ struct MmaSmemTail {
     int abort_flag;
     double red[kEpiWarps][4];
     int vote[kEpiWarps];
+    double stage[kEpiWarps][32 * 9];  // per-warp staging of 32 rows x 8 columns (direct writes)
 };
 
 constexpr size_t kMmaSmemBytes = 1024 + sizeof(StageSmem) * kStages + sizeof(MmaSmemTail);
@@ -299,6 +300,14 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             }
 
             // ---- store phase for block J = 2 Jp + h
+            // Lane = row i of the warp's 32-row strip.  The masters E1/E2 are
+            // symmetric, so they are read at (j, i): lanes on consecutive
+            // addresses.  Mirrored writes (j, i) are coalesced the same way;
+            // direct writes (i, j) go through a per-warp staging buffer so that
+            // each store instruction covers 4 rows x 8 consecutive columns.
+            // Columns are taken 8 at a time.  E1/E2 are re-read per output (L1
+            // hits): the control kernel lets an output overwrite E1/E2 in place
+            // only when it is the step's single output.
             const ProdOp &op = st->op;
             const float inv = op.inv;
             const int ldy = pr.ldy, lds = pr.lds, ldx = pr.ldx;
@@ -306,68 +315,162 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             const float *E2 = (op.E2 >= 0) ? pr.mats[op.E2].master : nullptr;
             const int nout = op.nout, pout = op.part_out;
             const float ra = op.ra, rb = op.rb, rc = op.rc;
-            const int i = te.I * kTileM + row_local;
+            const int i0 = te.I * kTileM + q * 32;
+            const int i = i0 + lane;
             const int J = 2 * te.Jp + h;
             double tr = 0.0, sq = 0.0, tr1 = 0.0, rr = 0.0;
-            if (J >= te.I && J * kTileM < n && i < n) {
+            double *stg = tail->stage[ew];
+            float *stf = reinterpret_cast<float *>(stg);
+            const int rsub = lane >> 3, csub = lane & 7;  // direct-write lane layout
+            const bool lean = nout == 1 && pout == 0 && !E2 && op.out[0].flags == (kOutMaster | kOutSlices);
+            if (lean && J >= te.I && J * kTileM < n && i0 < n) {
+                // the zero-temperature step: one output a v + b1 E1 + c [i == j]
                 const bool diag = (J == te.I);
+                const OutSpec &os = op.out[0];
+                const MatSlot &m = pr.mats[os.mat];
+                const float oa = os.a, ob = os.b1, oc = static_cast<float>(os.c), osc = os.s;
+                float *Mo = m.master;
+                __half *S0 = m.sl[0], *S1 = m.sl[1];
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    const int j0 = J * kTileM + c4 * 32;
+                for (int c8 = 0; c8 < kTileM / 8; ++c8) {
+                    const int j0 = J * kTileM + c8 * 8;
+                    if (j0 >= n) break;
+                    if (diag && j0 + 7 < i0) continue;
                     float csq = 0.0f, crr = 0.0f;
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) {
+                    for (int u = 0; u < 8; ++u) {
                         const int j = j0 + u;
-                        if (j < n && (!diag || j >= i)) {
+                        float val = 0.0f;
+                        if (i < n && j < n && (!diag || j >= i)) {
                             const bool on_diag = (j == i);
-                            const float w2 = on_diag ? 1.0f : 2.0f;  // off-diagonal counts twice
-                            const size_t at = static_cast<size_t>(i) * ldy + j;
                             const size_t mt = static_cast<size_t>(j) * ldy + i;
-                            const float v = acc[c4 * 32 + u] * inv;
-                            const float e1 = E1 ? E1[at] : 0.0f;
-                            const float e2 = E2 ? E2[at] : 0.0f;
-                            for (int o = 0; o < nout; ++o) {
-                                const OutSpec &os = op.out[o];
-                                const int fl = os.flags;
-                                if (fl & (kOutF64a | kOutF64b)) {
-                                    const double d = static_cast<double>(os.a) * v +
-                                                     static_cast<double>(os.b1) * e1 +
-                                                     static_cast<double>(os.b2) * e2 +
-                                                     (on_diag ? os.c : 0.0);
-                                    double *X = pr.Xd[(fl & kOutF64a) ? 0 : 1];
-                                    X[static_cast<size_t>(i) * ldx + j] = d;
-                                    if (!on_diag) X[static_cast<size_t>(j) * ldx + i] = d;
-                                    if (o == pout) {
-                                        if (on_diag) tr += d;
-                                        sq += w2 * d * d;
-                                    }
-                                    if (o == 1 && on_diag) tr1 += d;
-                                    continue;
-                                }
-                                const float val = fmaf(os.a, v, fmaf(os.b1, e1, os.b2 * e2)) +
-                                                  (on_diag ? static_cast<float>(os.c) : 0.0f);
-                                const MatSlot &m = pr.mats[os.mat];
-                                if (fl & kOutMaster) {
-                                    m.master[at] = val;
-                                    if (!on_diag) m.master[mt] = val;
-                                }
-                                if (fl & kOutSlices) {
-                                    const float ys = val * os.s;
-                                    put_slices(m, static_cast<size_t>(i) * lds + j, ys);
-                                    if (!on_diag) put_slices(m, static_cast<size_t>(j) * lds + i, ys);
-                                }
-                                if (o == pout) {
-                                    if (on_diag) tr += static_cast<double>(val);
-                                    csq = fmaf(w2 * val, val, csq);
-                                }
-                                if (o == 1 && on_diag) tr1 += static_cast<double>(val);
-                            }
+                            const float v = acc[c8 * 8 + u] * inv;
+                            const float e1 = E1 ? E1[mt] : 0.0f;
+                            val = fmaf(oa, v, ob * e1) + (on_diag ? oc : 0.0f);
                             const float r = fmaf(ra, v, rb * e1) + (on_diag ? rc : 0.0f);
-                            crr = fmaf(w2 * r, r, crr);
+                            if (!on_diag) {
+                                Mo[mt] = val;
+                                const float ys = val * osc;
+                                const __half hh = __float2half_rn(ys);
+                                const size_t ms = static_cast<size_t>(j) * lds + i;
+                                S0[ms] = hh;
+                                S1[ms] = __float2half_rn(ys - __half2float(hh));
+                            } else {
+                                tr += static_cast<double>(val);
+                            }
+                            csq = fmaf(on_diag ? val : 2.0f * val, val, csq);
+                            crr = fmaf(on_diag ? r : 2.0f * r, r, crr);
                         }
+                        stf[lane * 9 + u] = val;
                     }
                     sq += static_cast<double>(csq);
                     rr += static_cast<double>(crr);
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int ii = i0 + 4 * k + rsub, jj = j0 + csub;
+                        if (ii < n && jj < n && (!diag || jj >= ii)) {
+                            const float val = stf[(4 * k + rsub) * 9 + csub];
+                            Mo[static_cast<size_t>(ii) * ldy + jj] = val;
+                            const float ys = val * osc;
+                            const __half hh = __float2half_rn(ys);
+                            const size_t ms = static_cast<size_t>(ii) * lds + jj;
+                            S0[ms] = hh;
+                            S1[ms] = __float2half_rn(ys - __half2float(hh));
+                        }
+                    }
+                    __syncwarp();
+                }
+            } else if (J >= te.I && J * kTileM < n && i0 < n) {
+                const bool diag = (J == te.I);
+#pragma unroll
+                for (int c8 = 0; c8 < kTileM / 8; ++c8) {
+                    const int j0 = J * kTileM + c8 * 8;
+                    if (j0 >= n) break;
+                    if (diag && j0 + 7 < i0) continue;  // strictly below the diagonal
+                    // element (i, j0 + u) exists in this block's upper part
+                    auto okf = [&](int u) { return i < n && j0 + u < n && (!diag || j0 + u >= i); };
+                    auto e1f = [&](int u) { return E1 ? E1[static_cast<size_t>(j0 + u) * ldy + i] : 0.0f; };
+                    auto e2f = [&](int u) { return E2 ? E2[static_cast<size_t>(j0 + u) * ldy + i] : 0.0f; };
+                    float crr = 0.0f;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (okf(u)) {
+                            const bool on_diag = (j0 + u == i);
+                            const float r = fmaf(ra, acc[c8 * 8 + u] * inv, rb * e1f(u)) + (on_diag ? rc : 0.0f);
+                            crr = fmaf(on_diag ? r : 2.0f * r, r, crr);
+                        }
+                    }
+                    rr += static_cast<double>(crr);
+                    for (int o = 0; o < nout; ++o) {
+                        const OutSpec &os = op.out[o];
+                        const int fl = os.flags;
+                        if (fl & (kOutF64a | kOutF64b)) {
+                            double *X = pr.Xd[(fl & kOutF64a) ? 0 : 1];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const int j = j0 + u;
+                                const bool on_diag = (j == i);
+                                double d = 0.0;
+                                if (okf(u)) {
+                                    d = static_cast<double>(os.a) * (acc[c8 * 8 + u] * inv) +
+                                        static_cast<double>(os.b1) * e1f(u) +
+                                        static_cast<double>(os.b2) * e2f(u) + (on_diag ? os.c : 0.0);
+                                    if (!on_diag) X[static_cast<size_t>(j) * ldx + i] = d;
+                                    if (o == pout) {
+                                        if (on_diag) tr += d;
+                                        sq += (on_diag ? 1.0 : 2.0) * d * d;
+                                    }
+                                    if (o == 1 && on_diag) tr1 += d;
+                                }
+                                stg[lane * 9 + u] = d;
+                            }
+                            __syncwarp();
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const int ii = i0 + 4 * k + rsub, jj = j0 + csub;
+                                if (ii < n && jj < n && (!diag || jj >= ii))
+                                    X[static_cast<size_t>(ii) * ldx + jj] = stg[(4 * k + rsub) * 9 + csub];
+                            }
+                            __syncwarp();
+                            continue;
+                        }
+                        const MatSlot &m = pr.mats[os.mat];
+                        const float cdiag = static_cast<float>(os.c);
+                        float csq = 0.0f;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int j = j0 + u;
+                            const bool on_diag = (j == i);
+                            float val = 0.0f;
+                            if (okf(u)) {
+                                val = fmaf(os.a, acc[c8 * 8 + u] * inv, fmaf(os.b1, e1f(u), os.b2 * e2f(u))) +
+                                      (on_diag ? cdiag : 0.0f);
+                                if (!on_diag) {
+                                    if (fl & kOutMaster) m.master[static_cast<size_t>(j) * ldy + i] = val;
+                                    if (fl & kOutSlices) put_slices(m, static_cast<size_t>(j) * lds + i, val * os.s);
+                                }
+                                if (o == pout) {
+                                    if (on_diag) tr += static_cast<double>(val);
+                                    csq = fmaf(on_diag ? val : 2.0f * val, val, csq);
+                                }
+                                if (o == 1 && on_diag) tr1 += static_cast<double>(val);
+                            }
+                            stf[lane * 9 + u] = val;
+                        }
+                        if (o == pout) sq += static_cast<double>(csq);
+                        __syncwarp();
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int ii = i0 + 4 * k + rsub, jj = j0 + csub;
+                            if (ii < n && jj < n && (!diag || jj >= ii)) {
+                                const float val = stf[(4 * k + rsub) * 9 + csub];
+                                if (fl & kOutMaster) m.master[static_cast<size_t>(ii) * ldy + jj] = val;
+                                if (fl & kOutSlices) put_slices(m, static_cast<size_t>(ii) * lds + jj, val * os.s);
+                            }
+                        }
+                        __syncwarp();
+                    }
                 }
             }
             // deterministic per-tile partials: warp tree, then the 8 warps in order

@@ -52,6 +52,16 @@ FE_API int fe_k_gershgorin_noalloc(const double *H, int64_t n, int64_t ld, doubl
 FE_API int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t ldy, float *C, int64_t ldc,
                     int nslices, double bound);
 
+/* P = X * X for a symmetric FP64 matrix X with ||X||_2 <= 2, computed by the
+ * FP64-accurate tensor-core kernel of the polishing steps (Sec. III-A: the
+ * last SP2 iterations run in FP64): X/4 is split into 7 balanced base-256
+ * digit matrices held exactly in FP16, the 28 digit products of levels
+ * a + c <= 6 are summed exactly in FP32 tensor memory per K block of 128 and
+ * drained into int64 fixed point (unit 2^-60 of P).  Error of each entry
+ * about n^(1/2) 2^-64 beyond FP64 rounding.  P (FP64, ldp) is written whole
+ * and exactly symmetric. */
+FE_API int fe_k_digit_square(fe_ctx *ctx, const double *X, int64_t n, int64_t ld, double *P, int64_t ldp);
+
 /* Measurement hooks (no counterpart in the paper; they time the hot path).
  * fe_k_profile(ctx, 1) makes every following solve record CUDA events around
  * each tensor-core and FP64 step launch on the context's stream.

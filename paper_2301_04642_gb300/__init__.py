@@ -74,13 +74,15 @@ def load(build=True):
     L.fe_k_gershgorin.argtypes = [P, P, i64, i64, ctypes.POINTER(dbl)]
     L.fe_k_sym_square.argtypes = [P, P, i64, i64, P, i64, ctypes.c_int, dbl]
     L.fe_k_gershgorin_noalloc.argtypes = [P, i64, i64, P, P]
+    L.fe_k_digit_square.argtypes = [P, P, i64, i64, P, i64]
     L.fe_k_profile.argtypes = [P, ctypes.c_int]
     L.fe_k_profile_read.argtypes = [P, ctypes.POINTER(dbl)]
     L.fe_k_launch_count.argtypes = [P, ctypes.POINTER(i64)]
     L.fe_k_history.argtypes = [P, ctypes.c_int, ctypes.POINTER(dbl), ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int)]
     for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
-                 "fe_k_gershgorin", "fe_k_gershgorin_noalloc", "fe_k_sym_square", "fe_k_profile", "fe_k_profile_read",
+                 "fe_k_gershgorin", "fe_k_gershgorin_noalloc", "fe_k_sym_square", "fe_k_digit_square",
+                 "fe_k_profile", "fe_k_profile_read",
                  "fe_k_launch_count", "fe_k_history"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -275,6 +277,16 @@ class Context:
         _ready(Y, C)
         rc = self.L.fe_k_sym_square(self.h, yp, Y.shape[0], Y.stride(0), cp, C.stride(0),
                                     int(nslices), float(bound))
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+
+    def digit_square(self, X, P):
+        """P = X @ X (FP64 device tensors) by the FP64-accurate digit kernel."""
+        xp, xdev, _ = _ptr(X)
+        pp, pdev, _ = _ptr(P)
+        assert xdev and pdev, "device tensors expected"
+        _ready(X, P)
+        rc = self.L.fe_k_digit_square(self.h, xp, X.shape[0], X.stride(0), pp, P.stride(0))
         if rc != FE_OK:
             raise FeError(rc, self.last_error())
 

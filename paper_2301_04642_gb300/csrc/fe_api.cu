@@ -71,6 +71,7 @@ struct Slot {
     int ldy = 0, lds = 0, ldx = 0;
     std::vector<TileEnt> tiles;
     std::vector<Tile64> tiles64;
+    std::vector<TileEnt> tilesD;  // digit-product tiles (zero temperature)
     MmaProb hp;  // host image of the device descriptor (H filled per solve)
 };
 
@@ -86,13 +87,15 @@ struct Engine {
     size_t tiles_cap = 0;
     Tile64 *d_tiles64 = nullptr;
     size_t tiles64_cap = 0;
+    TileEnt *d_tilesD = nullptr;
+    size_t tilesD_cap = 0;
     SolveState *h_states = nullptr;  // pinned
     size_t h_states_cap = 0;
     int *h_done = nullptr;           // pinned copies of the done flags (serving)
     size_t h_done_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    int ntc = 0, n64 = 0;            // tile counts of the uploaded lists
-    bool any_tc = false, any_fp64 = false;
+    int ntc = 0, n64 = 0, nD = 0;    // tile counts of the uploaded lists
+    bool any_tc = false, any_fp64 = false, any_digit = false;
 };
 
 // One fe_submit request.
@@ -168,6 +171,13 @@ void build_tiles(Slot *s) {
     slot = 0;
     for (int I = 0; I < T64; ++I)
         for (int J = I; J < T64; ++J) s->tiles64.push_back(Tile64{0, I, J, slot++});
+    s->tilesD.clear();
+    if (s->method == kMethodSp2) {
+        const int TD = ceil_div(s->n, kDigitN);
+        slot = 0;
+        for (int I = 0; I < T; ++I)
+            for (int J = 2 * I; J < TD; ++J) s->tilesD.push_back(TileEnt{0, I, J, slot++});
+    }
 }
 
 // Matrices held per method: zero temperature keeps one FP32 master (Y) and two
@@ -184,7 +194,10 @@ size_t slot_bytes(int n, int method, int *ldy, int *lds, int *ldx, size_t *npart
     const int T64 = ceil_div(n, kTile64);
     const size_t ntiles = static_cast<size_t>(T) * ceil_div(T, 2);
     const size_t nt64 = static_cast<size_t>(T64) * (T64 + 1) / 2;
-    *nparts = std::max<size_t>({static_cast<size_t>(kInitBlocks), ntiles, nt64,
+    const size_t TD = static_cast<size_t>(ceil_div(n, kDigitN));
+    size_t ntD = 0;
+    for (size_t I = 0; I < static_cast<size_t>(T); ++I) ntD += (TD > 2 * I) ? TD - 2 * I : 0;
+    *nparts = std::max<size_t>({static_cast<size_t>(kInitBlocks), ntiles, nt64, ntD,
                                 static_cast<size_t>(kFinBlocks)});
     const size_t nn = static_cast<size_t>(n);
     size_t b = 0;
@@ -195,6 +208,8 @@ size_t slot_bytes(int n, int method, int *ldy, int *lds, int *ldx, size_t *npart
     add(8 * nn * (*ldx));                            // Xd[0]
     add(8 * nn * (*ldx));                            // Xd[1]
     add(8 * nn * nn);                                // Dtmp
+    if (method == kMethodSp2)
+        for (int a = 0; a < kDigits; ++a) add(2 * nn * (*lds));  // digits of X/4
     add(8 * kPartStride * (*nparts));                // partials
     add(sizeof(SolveState));
     add(sizeof(RowInfo) * nn);
@@ -202,15 +217,16 @@ size_t slot_bytes(int n, int method, int *ldy, int *lds, int *ldx, size_t *npart
     return b;
 }
 
-int encode_map(fe_ctx *ctx, CUtensorMap *m, void *base, int n, int ld_elems, int box_rows) {
+int encode_map(fe_ctx *ctx, CUtensorMap *m, void *base, int n, int ld_elems, int box_rows,
+               int box_k = kTileK, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
     auto enc = get_encode();
     if (!enc) return set_err(ctx, FE_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
     cuuint64_t gdim[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};
     cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld_elems) * 2};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(kTileK), static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(box_k), static_cast<cuuint32_t>(box_rows)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, gdim, gstride, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_err(ctx, FE_ECUDA, "cuTensorMapEncodeTiled failed");
     return FE_OK;
@@ -285,6 +301,9 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
     s->Xd[0] = reinterpret_cast<double *>(take(8 * nn * ldx));
     s->Xd[1] = reinterpret_cast<double *>(take(8 * nn * ldx));
     s->Dtmp = reinterpret_cast<double *>(take(8 * nn * nn));
+    __half *digs[kDigits] = {};
+    if (method == kMethodSp2)
+        for (int a = 0; a < kDigits; ++a) digs[a] = reinterpret_cast<__half *>(take(2 * nn * lds));
     s->part = reinterpret_cast<double *>(take(8 * kPartStride * nparts));
     s->st = reinterpret_cast<SolveState *>(take(sizeof(SolveState)));
     s->rowinfo = reinterpret_cast<RowInfo *>(take(sizeof(RowInfo) * nn));
@@ -302,6 +321,20 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
                 return rc;
             }
             ms.sl[b] = slices[m][b];
+        }
+    }
+    if (method == kMethodSp2) {
+        for (int a = 0; a < kDigits; ++a) {
+            int rc = encode_map(ctx, &s->hp.dA[a], digs[a], n, lds, kTileM, kDigitK,
+                                CU_TENSOR_MAP_SWIZZLE_64B);
+            if (rc == FE_OK)
+                rc = encode_map(ctx, &s->hp.dB[a], digs[a], n, lds, kDigitN, kDigitK,
+                                CU_TENSOR_MAP_SWIZZLE_64B);
+            if (rc != FE_OK) {
+                free_slot(ctx, s);
+                return rc;
+            }
+            s->hp.dig[a] = digs[a];
         }
     }
     if (method == kMethodFermi) {
@@ -323,6 +356,7 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
     s->hp.lds = lds;
     s->hp.ntiles = static_cast<int>(s->tiles.size());
     s->hp.ntiles64 = static_cast<int>(s->tiles64.size());
+    s->hp.ntilesD = static_cast<int>(s->tilesD.size());
     s->hp.Xd[0] = s->Xd[0];
     s->hp.Xd[1] = s->Xd[1];
     s->hp.ldx = ldx;
@@ -482,6 +516,7 @@ void eng_free(Engine &e) {
     if (e.d_probs) cudaFree(e.d_probs);
     if (e.d_tiles) cudaFree(e.d_tiles);
     if (e.d_tiles64) cudaFree(e.d_tiles64);
+    if (e.d_tilesD) cudaFree(e.d_tilesD);
     if (e.h_states) cudaFreeHost(e.h_states);
     if (e.h_done) cudaFreeHost(e.h_done);
     if (e.ev0) cudaEventDestroy(e.ev0);
@@ -495,7 +530,8 @@ int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
     std::vector<MmaProb> hprobs(np);
     std::vector<TileEnt> tiles;
     std::vector<Tile64> tiles64;
-    e.any_tc = e.any_fp64 = false;
+    std::vector<TileEnt> tilesD;
+    e.any_tc = e.any_fp64 = e.any_digit = false;
     for (int k = 0; k < np; ++k) {
         const Job &j = jobs[k];
         hprobs[k] = j.slot->hp;
@@ -507,14 +543,19 @@ int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
             e.any_tc = true;
             for (TileEnt t : j.slot->tiles) { t.prob = k; tiles.push_back(t); }
         }
-        if (pr != FE_PREC_FP32 && !fermi) {
+        if (pr == FE_PREC_FP64 && !fermi) {
             e.any_fp64 = true;
             for (Tile64 t : j.slot->tiles64) { t.prob = k; tiles64.push_back(t); }
+        }
+        if ((pr == FE_PREC_MIXED || pr == FE_PREC_TRY_FP16) && !fermi) {
+            e.any_digit = true;
+            for (TileEnt t : j.slot->tilesD) { t.prob = k; tilesD.push_back(t); }
         }
     }
     int rc = ensure_dev(ctx, &e.d_probs, &e.probs_cap, np);
     if (rc == FE_OK) rc = ensure_dev(ctx, &e.d_tiles, &e.tiles_cap, tiles.size());
     if (rc == FE_OK) rc = ensure_dev(ctx, &e.d_tiles64, &e.tiles64_cap, tiles64.size());
+    if (rc == FE_OK) rc = ensure_dev(ctx, &e.d_tilesD, &e.tilesD_cap, tilesD.size());
     if (rc == FE_OK) rc = ensure_pinned(ctx, &e.h_states, &e.h_states_cap, np);
     if (rc == FE_OK) rc = ensure_pinned(ctx, &e.h_done, &e.h_done_cap, np + 1);  // + error word
     if (rc != FE_OK) return rc;
@@ -526,10 +567,14 @@ int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
     if (!tiles64.empty())
         FE_CUDA(ctx, cudaMemcpyAsync(e.d_tiles64, tiles64.data(), sizeof(Tile64) * tiles64.size(),
                                      cudaMemcpyHostToDevice, e.stream));
+    if (!tilesD.empty())
+        FE_CUDA(ctx, cudaMemcpyAsync(e.d_tilesD, tilesD.data(), sizeof(TileEnt) * tilesD.size(),
+                                     cudaMemcpyHostToDevice, e.stream));
     // the copies read host vectors that go out of scope here
     FE_CUDA(ctx, cudaStreamSynchronize(e.stream));
     e.ntc = static_cast<int>(tiles.size());
     e.n64 = static_cast<int>(tiles64.size());
+    e.nD = static_cast<int>(tilesD.size());
     return FE_OK;
 }
 
@@ -568,6 +613,7 @@ void eng_steps(fe_ctx *ctx, Engine &e, int np, int count, const std::vector<cuda
     const int grid_tc = std::max(1, std::min(e.ntc, ctx->num_sms));
     const int grid_64 = std::max(1, std::min(e.n64, 4 * ctx->num_sms));
     const size_t smem = mma_smem_bytes();
+    const int grid_d = std::max(1, std::min(e.nD, ctx->num_sms));
     for (int it = 0; it < count; ++it) {
         if (pev) cudaEventRecord((*pev)[4 * it + 0], s);
         if (e.any_tc) {
@@ -579,6 +625,12 @@ void eng_steps(fe_ctx *ctx, Engine &e, int np, int count, const std::vector<cuda
         if (e.any_fp64) {
             k_fp64_step<<<grid_64, 256, 0, s>>>(e.d_probs, e.d_tiles64, e.n64);
             ++ctx->launches;
+        }
+        if (e.any_digit) {
+            k_digit_prep<<<2 * ctx->num_sms, 256, 0, s>>>(e.d_probs, np);
+            k_digit_mma<<<grid_d, kMmaThreads, digit_smem_bytes(), s>>>(e.d_probs, e.d_tilesD, e.nD,
+                                                                        e.d_err);
+            ctx->launches += 2;
         }
         if (pev) cudaEventRecord((*pev)[4 * it + 3], s);
         k_control<<<np, 256, 0, s>>>(e.d_probs, np);
@@ -898,8 +950,10 @@ extern "C" int fe_create(fe_ctx **out, const fe_config *cfg) {
     if (rc == FE_OK) rc = eng_init(ctx, ctx->seng, nullptr);
     if (rc == FE_OK && cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = set_err(nullptr, FE_ECUDA, "copy stream");
-    if (rc == FE_OK && cudaFuncSetAttribute(k_sym_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            static_cast<int>(mma_smem_bytes())) != cudaSuccess)
+    if (rc == FE_OK && (cudaFuncSetAttribute(k_sym_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(mma_smem_bytes())) != cudaSuccess ||
+                        cudaFuncSetAttribute(k_digit_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(digit_smem_bytes())) != cudaSuccess))
         rc = set_err(nullptr, FE_ECUDA, std::string("context setup: ") + cudaGetErrorString(cudaGetLastError()));
     if (rc != FE_OK) {
         const std::string why = g_err;
@@ -1170,6 +1224,53 @@ extern "C" int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t l
     const cudaError_t e = cudaStreamSynchronize(q);
     release_slot(ctx, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sym_square");
+    if (herr) return set_err(ctx, FE_ETIMEOUT, "device wait timed out (code " + std::to_string(herr) + ")");
+    return FE_OK;
+}
+
+extern "C" int fe_k_digit_square(fe_ctx *ctx, const double *X, int64_t n, int64_t ld, double *P,
+                                 int64_t ldp) {
+    if (!ctx || !X || !P || n < 1 || ld < n || ldp < n) return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    Engine &eg = ctx->eng;
+    Slot *s = nullptr;
+    int rc = acquire_slot(ctx, static_cast<int>(n), kMethodSp2, &s);
+    if (rc != FE_OK) return rc;
+    rc = ensure_dev(ctx, &eg.d_probs, &eg.probs_cap, 1);
+    if (rc == FE_OK) rc = ensure_dev(ctx, &eg.d_tilesD, &eg.tilesD_cap, s->tilesD.size());
+    if (rc != FE_OK) { release_slot(ctx, s); return rc; }
+    cudaStream_t q = eg.stream;
+    // input X as the FP64 iterate; one X^2 step with gamma = 0 writes X^2 to the other buffer
+    cudaMemcpy2DAsync(s->Xd[0], sizeof(double) * s->ldx, X, sizeof(double) * ld, sizeof(double) * n, n,
+                      cudaMemcpyDeviceToDevice, q);
+    SolveState st0;
+    memset(&st0, 0, sizeof(st0));
+    st0.n = static_cast<int>(n);
+    st0.kind = kDigit;
+    st0.x_fp64 = 1;
+    st0.xcur = 0;
+    st0.sq = 1;
+    MmaProb hp = s->hp;
+    hp.H = X;
+    hp.ldh = ld;
+    cudaMemcpyAsync(eg.d_probs, &hp, sizeof(MmaProb), cudaMemcpyHostToDevice, q);
+    cudaMemcpyAsync(eg.d_tilesD, s->tilesD.data(), sizeof(TileEnt) * s->tilesD.size(),
+                    cudaMemcpyHostToDevice, q);
+    cudaMemcpyAsync(s->st, &st0, sizeof(SolveState), cudaMemcpyHostToDevice, q);
+    cudaMemsetAsync(eg.d_err, 0, sizeof(int), q);
+    const int nt = static_cast<int>(s->tilesD.size());
+    k_digit_prep<<<2 * ctx->num_sms, 256, 0, q>>>(eg.d_probs, 1);
+    k_digit_mma<<<std::min(nt, ctx->num_sms), kMmaThreads, digit_smem_bytes(), q>>>(eg.d_probs, eg.d_tilesD,
+                                                                                    nt, eg.d_err);
+    ctx->launches += 2;
+    cudaMemcpy2DAsync(P, sizeof(double) * ldp, s->Xd[1], sizeof(double) * s->ldx, sizeof(double) * n, n,
+                      cudaMemcpyDeviceToDevice, q);
+    int herr = 0;
+    cudaMemcpyAsync(&herr, eg.d_err, sizeof(int), cudaMemcpyDeviceToHost, q);
+    const cudaError_t e = cudaStreamSynchronize(q);
+    release_slot(ctx, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "digit_square");
     if (herr) return set_err(ctx, FE_ETIMEOUT, "device wait timed out (code " + std::to_string(herr) + ")");
     return FE_OK;
 }

@@ -32,6 +32,17 @@ constexpr int kEpiWarps = 8;
 constexpr int kPartStride = 4;    // doubles per partial slot: tr, sumsq, maxabs, spare
 constexpr float kSliceTop = 16384.0f;  // slices are scaled so |s Y| <= 2^14 < fp16 max
 
+// FP64-accurate products on the tensor cores (kind kDigit): X/4 is written in
+// fixed point as kDigits balanced base-256 digits S_a in [-128, 127], each held
+// exactly in FP16, X/4 = sum_a S_a 2^(-8(a+1)).  Level L of the product
+// collects the digit pairs a + c = L; per K block of kDigitKBlock its integer
+// sum is below 7 * 128 * 2^14 < 2^24, so the FP32 accumulator is exact.
+constexpr int kDigits = 7;
+constexpr int kDigitN = 64;       // tile columns (7 level buffers x 64 TMEM columns)
+constexpr int kDigitK = 32;       // K per pipeline stage (one 64-byte swizzle row of FP16)
+constexpr int kDigitStages = 2;
+constexpr int kDigitKBlock = 128; // K per drain of the level buffers
+
 // error codes written by kernels into the context's device error word
 enum DevErr : int {
     kErrNone = 0,
@@ -49,9 +60,11 @@ constexpr int kHistCols = 6;
 
 // ---------------------------------------------------------------- state
 // Which kernel does the step: the tensor-core kernel (kTcSingle / kTcSplit:
-// one or two FP16 slices per operand; kTcElem: no product, epilogue only) or
-// the FP64-accurate SIMT kernel (kFp64 native, kDf double-float).
-enum Kind : int { kNone = 0, kTcSingle = 1, kTcSplit = 2, kFp64 = 3, kDf = 4, kTcElem = 5 };
+// one or two FP16 slices per operand; kTcElem: no product, epilogue only),
+// the FP64-accurate SIMT kernel (kFp64 native, kDf double-float), or the
+// FP64-accurate digit product on the tensor cores (kDigit).
+enum Kind : int { kNone = 0, kTcSingle = 1, kTcSplit = 2, kFp64 = 3, kDf = 4, kTcElem = 5,
+                  kDigit = 6 };
 enum Phase : int { kPhaseSingle = 0, kPhaseSplit = 1, kPhaseFp64 = 2, kPhaseDone = 3 };
 enum Prec : int { kPrecMixed = 0, kPrecFp64 = 1, kPrecFp32 = 2, kPrecTryFp16 = 3 };
 enum Method : int { kMethodSp2 = 0, kMethodFermi = 1 };
@@ -256,6 +269,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(const void *tile) {
     d |= static_cast<uint64_t>((1024u >> 4) & 0x3FFFu) << 32;   // stride offset: 8 rows x 128 B
     d |= static_cast<uint64_t>(1u) << 46;                        // descriptor version (sm_100 family)
     d |= static_cast<uint64_t>(2u) << 61;                        // swizzle mode: 128 B
+    return d;
+}
+
+// The same for 64-byte swizzling: rows of 64 bytes, 8-row atoms 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(const void *tile) {
+    const uint32_t addr = smem_u32(tile);
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>(1u) << 16;
+    d |= static_cast<uint64_t>((512u >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;
+    d |= static_cast<uint64_t>(4u) << 61;                        // swizzle mode: 64 B
     return d;
 }
 

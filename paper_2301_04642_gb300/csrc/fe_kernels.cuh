@@ -40,6 +40,11 @@ struct MmaProb {
     int ldx, pad0;
     const double *H;                 // Hp (device), leading dimension ldh
     long long ldh;
+    // digit arrays of the FP64-accurate tensor-core product (kDigit), ld lds
+    CUtensorMap dA[kDigits];         // box 32 (K) x 128 rows, 64-byte swizzle
+    CUtensorMap dB[kDigits];         // box 32 (K) x 64 rows
+    __half *dig[kDigits];
+    int ntilesD, padD;
 };
 
 // One tensor-core tile: rows [I*128, I*128+128) x columns [Jp*256, Jp*256+256).
@@ -49,6 +54,9 @@ struct TileEnt {
     int Jp;
     int slot;  // partial slot index within the problem
 };
+
+// A digit-product tile uses TileEnt with Jp = J: rows [I*128, +128) x
+// columns [J*64, +64), J >= 2I.
 
 // One FP64 tile: rows [I*64, +64) x columns [J*64, +64), J >= I.
 struct Tile64 {
@@ -80,6 +88,13 @@ __global__ void k_fp64_step(const MmaProb *probs, const Tile64 *tiles, int ntile
 // D = X -> out (FP64, ld), partials of tr(H D) and tr D.
 __global__ void k_finalize(const MmaProb *probs, int prob, double *D, long long ldd);
 __global__ void k_finalize_reduce(const MmaProb *probs, int prob);
+
+// FP64-accurate X^2 on the tensor cores from digit-split operands (kind kDigit).
+__global__ void k_digit_mma(const MmaProb *__restrict__ probs, const TileEnt *__restrict__ tiles,
+                            int ntiles, int *err);
+size_t digit_smem_bytes();
+// Digits of the current iterate for every problem whose next step is kDigit.
+__global__ void k_digit_prep(const MmaProb *probs, int nprobs);
 
 // FP32 -> FP16 slices of s*Y for a standalone product (kernel tests).
 __global__ void k_make_slices(const float *Y, int n, int ldy, float s, __half *hi, __half *lo,

@@ -84,7 +84,7 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
         st->c = st->c_next;
         st->s_cur = st->s_next;
         st->cur ^= 1;
-    } else if (prev_kind == kFp64 || prev_kind == kDf) {
+    } else if (prev_kind == kFp64 || prev_kind == kDf || prev_kind == kDigit) {
         st->xcur ^= 1;
         st->x_fp64 = 1;
     }
@@ -141,7 +141,7 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
             if (st->prec == kPrecFp32) done = true;
             else phase = kPhaseFp64;
         }
-    } else if (phase == kPhaseFp64 && (prev_kind == kFp64 || prev_kind == kDf)) {
+    } else if (phase == kPhaseFp64 && (prev_kind == kFp64 || prev_kind == kDf || prev_kind == kDigit)) {
         const int nfp64 = st->it_phase[kPhaseFp64];
         if (st->prec == kPrecFp64) {
             const bool idem_ok = fabs(idem) <= 2e-10 ||
@@ -195,7 +195,7 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
     st->sq = sq;
     st->phase = phase;
     if (phase == kPhaseFp64) {
-        st->kind = (st->prec == kPrecFp64) ? kFp64 : kDf;
+        st->kind = (st->prec == kPrecFp64) ? kFp64 : kDigit;
     } else {
         st->kind = (phase == kPhaseSingle) ? kTcSingle : kTcSplit;
         // X = c I + Y:  X^2 -> c' = c^2, Y' = 2c Y + Y^2;  2X - X^2 -> c' = 2c - c^2,
@@ -458,6 +458,7 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
     int nparts;
     if (st->kind == kNone) nparts = kInitBlocks;
     else if (st->kind == kFp64 || st->kind == kDf) nparts = pr.ntiles64;
+    else if (st->kind == kDigit) nparts = pr.ntilesD;
     else nparts = pr.ntiles;
 
     __shared__ double s_a[256], s_b[256], s_c[256], s_d[256];

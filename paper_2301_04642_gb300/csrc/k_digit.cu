@@ -1,0 +1,390 @@
+// FP64-accurate SP2 step on the tensor cores (the polishing products of the
+// mixed schedule; Sec. III-A runs the last iterations in FP64).
+//
+// GB300's FP64 units deliver about 1.25 TFLOP/s, so the FP64-accurate
+// product X^2 is computed on the FP16 tensor cores instead, in exact integer
+// arithmetic.  X/4 is written in fixed point with kDigits = 7 balanced
+// base-256 digits,
+//     X/4 = sum_{a=0}^{6} S_a 2^(-8(a+1)),   S_a integer in [-128, 127],
+// each digit matrix held exactly in FP16.  Then
+//     (X/4)^2 = sum_L 2^(-8(L+2)) sum_{a+c=L} S_a S_c^T
+// and the levels L = 0..6 (28 digit products) are kept; the dropped levels
+// are below 2^-64 relative to the leading one.  A digit product is an exact
+// integer below 2^14, and a level sums at most 7 pairs, so over a K block of
+// 128 its value stays below 7 * 128 * 2^14 < 2^24: the FP32 tensor-memory
+// accumulator holds it exactly whatever its rounding.  Every K block each
+// level buffer is drained into a per-element int64 fixed-point sum (unit
+// 2^-64), and the epilogue forms P = X^2 = sum * 2^-60 in FP64.
+//
+// The epilogue is the SP2 update of the FP64-accurate step:
+//     X' = (X^2 or 2X - X^2) + gamma (X - X^2)
+// written to the other FP64 buffer (and mirrored), with per-tile partials
+// tr X', ||X'||_F^2 and ||X^2 - X||_F^2 (same slots as the SIMT FP64 step).
+//
+// Tiles: 128 rows (block I) x 64 columns (block J), J >= 2I, one persistent
+// CTA per SM.  Warp roles as in the split-FP16 kernel: warp 0 TMA (per K
+// stage of 32 one box per digit for A and for B), warp 1 TMEM owner and MMA
+// issuer (7 level buffers of 64 columns), warps 2-9 drain + epilogue (warp w:
+// TMEM lanes 32 (w % 4) .., columns 32 ((w - 2) / 4) .. of each level).
+// Every wait is bounded; on a timeout the kernel records an error code,
+// drains its own copies and MMAs, frees TMEM and returns.
+#include "fe_dev.cuh"
+#include "fe_kernels.cuh"
+
+namespace fe {
+
+namespace {
+
+constexpr int kDA = kTileM * kDigitK * 2;   // 8 KiB: one digit, 128 rows x 32 K
+constexpr int kDB = kDigitN * kDigitK * 2;  // 4 KiB: one digit, 64 rows x 32 K
+constexpr int kStagesPerBlock = kDigitKBlock / kDigitK;
+
+struct alignas(1024) DigitStage {
+    uint8_t a[kDigits][kDA];
+    uint8_t b[kDigits][kDB];
+};
+
+struct DigitTail {
+    uint64_t full[kDigitStages];
+    uint64_t empty[kDigitStages];
+    uint64_t lfull[kDigits];
+    uint64_t lfree[kDigits];
+    uint64_t abort_bar;
+    uint32_t tmem_base;
+    int abort_flag;
+    double red[kEpiWarps][4];
+    int vote[kEpiWarps];
+    double stage[kEpiWarps][32 * 9];
+};
+
+constexpr size_t kDigitSmemBytes = 1024 + sizeof(DigitStage) * kDigitStages + sizeof(DigitTail);
+
+__device__ __forceinline__ int step_kind(const SolveState *st) {
+    return *reinterpret_cast<const volatile int *>(&st->kind);
+}
+
+__device__ __forceinline__ void record_error(int *err, int code) { atomicCAS(err, 0, code); }
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// The current iterate at (i, j): Xd[xcur] once FP64, else c I + Y.
+__device__ __forceinline__ double x_at(const MmaProb &pr, const SolveState *st, int i, int j) {
+    if (st->x_fp64) return pr.Xd[st->xcur][static_cast<size_t>(i) * pr.ldx + j];
+    return static_cast<double>(pr.Y[static_cast<size_t>(i) * pr.ldy + j]) + (i == j ? st->c : 0.0);
+}
+
+}  // namespace
+
+__global__ void k_digit_prep(const MmaProb *probs, int nprobs) {
+    for (int p = 0; p < nprobs; ++p) {
+        const MmaProb &pr = probs[p];
+        const SolveState *st = pr.st;
+        if (step_kind(st) != kDigit) continue;
+        const int n = pr.n;
+        for (int i = blockIdx.x; i < n; i += gridDim.x) {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                // V = round(X/4 * 2^56); |X| <= 1.98 keeps the top digit in [-128, 127]
+                const double x = fmin(fmax(x_at(pr, st, i, j), -1.98), 1.98);
+                long long V = __double2ll_rn(x * 18014398509481984.0);  // 2^54
+                const size_t at = static_cast<size_t>(i) * pr.lds + j;
+#pragma unroll
+                for (int a = kDigits - 1; a >= 0; --a) {
+                    const long long d = ((V + 128) & 255) - 128;
+                    pr.dig[a][at] = __int2half_rn(static_cast<int>(d));
+                    V = (V - d) >> 8;
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kMmaThreads, 1)
+    k_digit_mma(const MmaProb *__restrict__ probs, const TileEnt *__restrict__ tiles, int ntiles,
+                int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t base_u32 = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
+    DigitStage *stages = reinterpret_cast<DigitStage *>(smem);
+    DigitTail *tail = reinterpret_cast<DigitTail *>(smem + sizeof(DigitStage) * kDigitStages);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kDigitStages; ++s) {
+            mbar_init(&tail->full[s], 1);
+            mbar_init(&tail->empty[s], 1);
+        }
+        for (int l = 0; l < kDigits; ++l) {
+            mbar_init(&tail->lfull[l], 1);
+            mbar_init(&tail->lfree[l], kEpiWarps);
+        }
+        mbar_init(&tail->abort_bar, 1);
+        tail->abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(&tail->tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tail->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        uint32_t stage = 0, phase = 0;
+        bool ok = true;
+        uint32_t last_phase[kDigitStages];
+        bool issued[kDigitStages];
+        for (int s = 0; s < kDigitStages; ++s) { issued[s] = false; last_phase[s] = 0; }
+        constexpr uint32_t bytes = static_cast<uint32_t>(kDigits * (kDA + kDB));
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileEnt te = tiles[t];
+            const MmaProb &pr = probs[te.prob];
+            if (step_kind(pr.st) != kDigit) continue;
+            const int nk = (pr.n + kDigitK - 1) / kDigitK;
+            for (int kc = 0; kc < nk; ++kc) {
+                bool got = true;
+                if (lane == 0) got = mbar_wait_bounded(&tail->empty[stage], phase ^ 1u);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    if (lane == 0) record_error(err, kErrTimeoutEmpty);
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) {
+                    mbar_expect_tx(&tail->full[stage], bytes);
+                    for (int a = 0; a < kDigits; ++a) {
+                        tma_load_2d(stages[stage].a[a], &pr.dA[a], &tail->full[stage], kc * kDigitK,
+                                    te.I * kTileM);
+                        tma_load_2d(stages[stage].b[a], &pr.dB[a], &tail->full[stage], kc * kDigitK,
+                                    te.Jp * kDigitN);
+                    }
+                }
+                __syncwarp();
+                issued[stage] = true;
+                last_phase[stage] = phase;
+                if (++stage == kDigitStages) { stage = 0; phase ^= 1u; }
+            }
+        }
+        if (!ok) {
+            tail->abort_flag = 1;
+            if (lane == 0)
+                for (int s = 0; s < kDigitStages; ++s)
+                    if (issued[s]) (void)mbar_wait_bounded(&tail->full[s], last_phase[s]);
+            __syncwarp();
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        uint32_t stage = 0, phase = 0;
+        uint32_t blk = 0;  // K blocks of this CTA: level-buffer phase = blk & 1
+        bool ok = true;
+        bool any_commit = false;
+        constexpr uint32_t idesc = idesc_f16(kTileM, kDigitN, 0);
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileEnt te = tiles[t];
+            const MmaProb &pr = probs[te.prob];
+            if (step_kind(pr.st) != kDigit) continue;
+            const int nk = (pr.n + kDigitK - 1) / kDigitK;
+            for (int kc = 0; kc < nk; ++kc) {
+                const int sb = kc % kStagesPerBlock;
+                const bool first = (sb == 0);
+                const bool last = (sb == kStagesPerBlock - 1) || (kc == nk - 1);
+                bool got = true;
+                if (lane == 0) got = mbar_wait_bounded(&tail->full[stage], phase);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    if (lane == 0) record_error(err, kErrTimeoutFull);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (lane == 0) {
+                    uint64_t da[kDigits], db[kDigits];
+#pragma unroll
+                    for (int a = 0; a < kDigits; ++a) {
+                        da[a] = smem_desc_sw64(stages[stage].a[a]);
+                        db[a] = smem_desc_sw64(stages[stage].b[a]);
+                    }
+#pragma unroll
+                    for (int L = 0; L < kDigits; ++L) {
+                        if (first && got) {
+                            // the drain of this level's previous block must be done
+                            got = mbar_wait_bounded(&tail->lfree[L], (blk & 1u) ^ 1u);
+                            if (!got) record_error(err, kErrTimeoutTmem);
+                        }
+                        if (got) {
+                            const uint32_t tmem_d = tmem_base + static_cast<uint32_t>(L * kDigitN);
+#pragma unroll
+                            for (int a = 0; a <= L; ++a) {
+#pragma unroll
+                                for (int kk = 0; kk < kDigitK / 16; ++kk) {
+                                    const uint64_t off = static_cast<uint64_t>(kk * 2);  // 32 B along K
+                                    const uint32_t acc = (first && a == 0 && kk == 0) ? 0u : 1u;
+                                    tc_mma_f16(tmem_d, da[a] + off, db[L - a] + off, idesc, acc);
+                                }
+                            }
+                            if (last) tc_commit(&tail->lfull[L]);
+                            any_commit = true;
+                        }
+                    }
+                    tc_commit(&tail->empty[stage]);
+                }
+                got = __shfl_sync(0xffffffffu, got, 0);
+                __syncwarp();
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                if (++stage == kDigitStages) { stage = 0; phase ^= 1u; }
+                if (last) ++blk;
+            }
+        }
+        if (!ok) {
+            tail->abort_flag = 1;
+            // every issued MMA must finish before TMEM is released
+            if (lane == 0 && any_commit) {
+                tc_commit(&tail->abort_bar);
+                (void)mbar_wait_bounded(&tail->abort_bar, 0);
+            }
+            __syncwarp();
+        }
+    } else {
+        // ------------------------------------------------------------ drain + epilogue
+        const int ew = warp - 2;
+        const int q = warp & 3;                // TMEM lane quadrant (warp % 4)
+        const int h = ew >> 2;                 // column half: 32 of the tile's 64
+        uint32_t blk = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileEnt te = tiles[t];
+            const MmaProb &pr = probs[te.prob];
+            const SolveState *st = pr.st;
+            if (step_kind(st) != kDigit) continue;
+            const int n = pr.n;
+            const int nk = (n + kDigitK - 1) / kDigitK;
+            const int nb = (nk + kStagesPerBlock - 1) / kStagesPerBlock;
+            long long acc[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) acc[u] = 0;
+            for (int b = 0; b < nb && ok; ++b) {
+#pragma unroll 1
+                for (int L = 0; L < kDigits; ++L) {
+                    bool got = mbar_wait_bounded(&tail->lfull[L], blk & 1u);
+                    got = __all_sync(0xffffffffu, got);
+                    if (!got) {
+                        if (lane == 0) record_error(err, kErrTimeoutTmem);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    float v[32];
+                    tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                                  static_cast<uint32_t>(L * kDigitN + h * 32),
+                              v);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tail->lfree[L]);
+                    // level L carries unit 2^(-8(L+2)); the sum's unit is 2^-64
+                    const int shift = 8 * (kDigits - 1 - L);
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const long long iv = static_cast<long long>(__float2int_rn(v[u]));
+                        acc[u] += static_cast<long long>(static_cast<unsigned long long>(iv) << shift);
+                    }
+                }
+                ++blk;
+            }
+            if (lane == 0) tail->vote[ew] = ok ? 1 : 0;
+            epi_bar();
+            bool all_ok = true;
+            for (int w = 0; w < kEpiWarps; ++w) all_ok = all_ok && (tail->vote[w] != 0);
+            epi_bar();
+            if (!all_ok) {
+                ok = false;
+                break;
+            }
+
+            // ---- epilogue: X' = (X^2 or 2X - X^2) + gamma (X - X^2)
+            const int sq = st->sq;
+            const double gamma = st->gamma;
+            double *Xo = pr.Xd[st->xcur ^ 1];  // the control kernel flips xcur afterwards
+            const int ldx = pr.ldx;
+            const int i0 = te.I * kTileM + q * 32;
+            const int i = i0 + lane;
+            const int j0 = te.Jp * kDigitN + h * 32;
+            const int rsub = lane >> 3, csub = lane & 7;
+            double tr = 0.0, s2 = 0.0, id = 0.0;
+            double *stg = tail->stage[ew];
+            if (i0 < n && j0 < n && j0 + 31 >= i0) {
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int jg = j0 + 8 * g;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = jg + u;
+                        double xn = 0.0;
+                        if (i < n && j < n && j >= i) {
+                            const double P = static_cast<double>(acc[8 * g + u]) * 8.673617379884035e-19;  // 2^-60
+                            const double xo = x_at(pr, st, j, i);  // symmetric: coalesced read
+                            xn = (sq ? P : 2.0 * xo - P) + gamma * (xo - P);
+                            const double dd = P - xo;
+                            if (j != i) {
+                                Xo[static_cast<size_t>(j) * ldx + i] = xn;
+                                s2 += 2.0 * xn * xn;
+                                id += 2.0 * dd * dd;
+                            } else {
+                                tr += xn;
+                                s2 += xn * xn;
+                                id += dd * dd;
+                            }
+                        }
+                        stg[lane * 9 + u] = xn;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int ii = i0 + 4 * k + rsub, jj = jg + csub;
+                        if (ii < n && jj < n && jj >= ii)
+                            Xo[static_cast<size_t>(ii) * ldx + jj] = stg[(4 * k + rsub) * 9 + csub];
+                    }
+                    __syncwarp();
+                }
+            }
+            tr = warp_sum(tr);
+            s2 = warp_sum(s2);
+            id = warp_sum(id);
+            if (lane == 0) {
+                tail->red[ew][0] = tr;
+                tail->red[ew][1] = s2;
+                tail->red[ew][2] = id;
+            }
+            epi_bar();
+            if (ew == 0 && lane == 0) {
+                double a = 0, b2 = 0, c = 0;
+                for (int w = 0; w < kEpiWarps; ++w) {
+                    a += tail->red[w][0];
+                    b2 += tail->red[w][1];
+                    c += tail->red[w][2];
+                }
+                double *slot = pr.part + static_cast<size_t>(te.slot) * kPartStride;
+                slot[0] = a;
+                slot[1] = b2;
+                slot[2] = 0.0;
+                slot[3] = c;
+            }
+            epi_bar();
+        }
+        if (!ok) tail->abort_flag = 1;
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 512);
+    }
+}
+
+size_t digit_smem_bytes() { return kDigitSmemBytes; }
+
+}  // namespace fe

@@ -71,3 +71,36 @@ def test_sym_square_leading_dimension_and_scale():
     rel = 2.0 ** -21 + 4 * 2.0 ** -23 + math.ceil(n / 64) * 2.0 ** -24
     assert np.all(np.abs(Ch[:, :n] - ref) <= rel * absprod)
     assert np.all(Ch[:, n:] == 7.0)             # padding untouched
+
+
+def _sym_from_spectrum(n, lam, seed):
+    Q = hp_synth.haar_q(n, seed)
+    return hp_synth.assemble(Q, lam)
+
+
+@pytest.mark.parametrize("n,ld,kind", [(100, 100, "proj"), (300, 304, "proj"), (1000, 1000, "proj"),
+                                       (1290, 1296, "proj"), (517, 520, "wide"), (64, 64, "wide")])
+def test_digit_square_is_fp64_accurate(n, ld, kind):
+    """The FP64-accurate tensor-core product against the oracle's FP64 matmul:
+    a near-projector (the polishing input: eigenvalues 0/1 off by ~1e-6) and a
+    symmetric matrix with spectrum spread over [-1.9, 1.9]."""
+    g = np.random.default_rng(n)
+    if kind == "proj":
+        lam = (np.arange(n) < int(0.8 * n)).astype(float) + 1e-6 * g.standard_normal(n)
+    else:
+        lam = g.uniform(-1.9, 1.9, n)
+    X = _sym_from_spectrum(n, lam, 3000 + n)
+    Xd = torch.zeros((n, ld), dtype=torch.float64, device="cuda")
+    Xd[:, :n] = torch.from_numpy(X).cuda()
+    Pd = torch.full((n, ld), float("nan"), dtype=torch.float64, device="cuda")
+    ctx().digit_square(Xd[:, :n], Pd[:, :n])
+    P = Pd[:, :n].cpu().numpy()
+    ref = oracle.matmul(X, X)
+    err = np.abs(P - ref).max()
+    print(n, kind, err, np.linalg.norm(P - ref))
+    assert np.array_equal(P, P.T)                    # mirrored: exactly symmetric
+    # the reference's own FP64 rounding bound gamma_n |X||X| (u = 2^-53), plus
+    # the kernel's final conversion to FP64 and its dropped digit levels
+    absx = np.abs(X)
+    bound = 2 * n * 2.0 ** -53 * oracle.matmul(absx, absx) + 2.0 ** -52
+    assert np.all(np.abs(P - ref) <= bound)

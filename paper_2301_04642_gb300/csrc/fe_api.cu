@@ -617,7 +617,7 @@ void eng_steps(fe_ctx *ctx, Engine &e, int np, int count, const std::vector<cuda
     for (int it = 0; it < count; ++it) {
         if (pev) cudaEventRecord((*pev)[4 * it + 0], s);
         if (e.any_tc) {
-            k_sym_mma<<<grid_tc, kMmaThreads, smem, s>>>(e.d_probs, e.d_tiles, e.ntc, e.d_err);
+            k_sym_mma<<<grid_tc, kSymThreads, smem, s>>>(e.d_probs, e.d_tiles, e.ntc, e.d_err);
             ++ctx->launches;
         }
         if (pev) cudaEventRecord((*pev)[4 * it + 1], s);
@@ -955,6 +955,14 @@ extern "C" int fe_create(fe_ctx **out, const fe_config *cfg) {
                         cudaFuncSetAttribute(k_digit_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(digit_smem_bytes())) != cudaSuccess))
         rc = set_err(nullptr, FE_ECUDA, std::string("context setup: ") + cudaGetErrorString(cudaGetLastError()));
+    if (rc == FE_OK) {
+        // the register hand-off inside the split-FP16 kernel assumes this allocation
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k_sym_mma) != cudaSuccess || fa.numRegs != kSymLaunchRegs)
+            rc = set_err(nullptr, FE_ECUDA, "k_sym_mma was compiled with " + std::to_string(fa.numRegs) +
+                                                " registers per thread; the kernel needs " +
+                                                std::to_string(kSymLaunchRegs));
+    }
     if (rc != FE_OK) {
         const std::string why = g_err;
         fe_destroy(ctx);
@@ -1214,7 +1222,7 @@ extern "C" int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t l
     cudaMemcpyAsync(s->st, &st0, sizeof(SolveState), cudaMemcpyHostToDevice, q);
     cudaMemsetAsync(eg.d_err, 0, sizeof(int), q);
     const int nt = static_cast<int>(s->tiles.size());
-    k_sym_mma<<<std::min(nt, ctx->num_sms), kMmaThreads, mma_smem_bytes(), q>>>(
+    k_sym_mma<<<std::min(nt, ctx->num_sms), kSymThreads, mma_smem_bytes(), q>>>(
         eg.d_probs, eg.d_tiles, nt, eg.d_err);
     ctx->launches += 2;
     cudaMemcpy2DAsync(C, sizeof(float) * ldc, s->Y, sizeof(float) * s->ldy, sizeof(float) * n, n,

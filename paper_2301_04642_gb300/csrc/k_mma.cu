@@ -27,13 +27,15 @@
 // TMEM and sum the chunks in registers (round-to-nearest FP32) while the MMA
 // warp fills the other chunk buffer.
 //
-// Warp roles (320 threads):
+// Warp roles (384 threads; warpgroup 0 hands registers to warpgroups 1-2):
 //   warp 0      TMA producer: per K chunk one box per slice for the A panel
 //               (128 rows) and the B panel (256 rows).
 //   warp 1      TMEM owner and MMA issuer: per chunk 4 x (1 or 3) MMAs
 //               M128 N256 K16 into one of two chunk buffers (2 x 256 cols).
-//   warps 2-9   drain + epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
-//               and columns 128 ((w - 2) / 4) .. +127, i.e. one 128x128 block.
+//   warps 2-3   idle (give their registers away)
+//   warps 4-11  drain + epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
+//               and columns 128 ((w - 4) / 4) .. +127, i.e. one 128x128 block,
+//               two 64-column loads per chunk.
 // Every wait is bounded; on a timeout the kernel records an error code,
 // drains its own copies and MMAs, frees TMEM and returns.
 #include "fe_dev.cuh"
@@ -81,6 +83,23 @@ __device__ __forceinline__ void record_error(int *err, int code) { atomicCAS(err
 // named barrier of the 8 drain/epilogue warps
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+// hi/lo FP16 slices of s * v[0..7], packed for one 16-byte store each
+// (the same roundings as put_slices)
+__device__ __forceinline__ void split8(const float *v, float s, uint4 &hv, uint4 &lv) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const float y0 = v[2 * p] * s, y1 = v[2 * p + 1] * s;
+        const __half2 hh = __floats2half2_rn(y0, y1);
+        const float2 back = __half22float2(hh);
+        const __half2 ll = __floats2half2_rn(y0 - back.x, y1 - back.y);
+        h[p] = *reinterpret_cast<const uint32_t *>(&hh);
+        l[p] = *reinterpret_cast<const uint32_t *>(&ll);
+    }
+    hv = make_uint4(h[0], h[1], h[2], h[3]);
+    lv = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 __device__ __forceinline__ void put_slices(const MatSlot &m, size_t at, float ys) {
     const __half hh = __float2half_rn(ys);
     m.sl[0][at] = hh;
@@ -89,7 +108,7 @@ __device__ __forceinline__ void put_slices(const MatSlot &m, size_t at, float ys
 
 }  // namespace
 
-__global__ void __launch_bounds__(kMmaThreads, 1)
+__global__ void __launch_bounds__(kSymThreads, 1)
     k_sym_mma(const MmaProb *__restrict__ probs, const TileEnt *__restrict__ tiles, int ntiles,
               int *err) {
     extern __shared__ uint8_t smem_raw[];
@@ -119,6 +138,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
     tc_fence_after();
     const uint32_t tmem_base = tail->tmem_base;
 
+    if (warp < kSymEpiWarp0) setmaxnreg_dec<kSymRegsLow>();
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         uint32_t stage = 0, phase = 0;
@@ -244,9 +264,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             }
             __syncwarp();
         }
-    } else {
+    } else if (warp >= kSymEpiWarp0) {
         // ------------------------------------------------------------ drain + epilogue
-        const int ew = warp - 2;               // 0..7
+        setmaxnreg_inc<kSymRegsHigh>();
+        const int ew = warp - kSymEpiWarp0;    // 0..7
         const int q = warp & 3;                // TMEM lane quadrant (hardware rule: warp % 4)
         const int h = ew >> 2;                 // column half: 128-block 2Jp + h
         const int row_local = q * 32 + lane;
@@ -276,11 +297,11 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                 const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                                        buf * kTileN + static_cast<uint32_t>(h * 128);
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    float v[32];
-                    tmem_ld32(tbase + c4 * 32, v);
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    float v[64];
+                    tmem_ld64(tbase + c2 * 64, v);
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) acc[c4 * 32 + u] += v[u];
+                    for (int u = 0; u < 64; ++u) acc[c2 * 64 + u] += v[u];
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -324,18 +345,68 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             const int rsub = lane >> 3, csub = lane & 7;  // direct-write lane layout
             const bool lean = nout == 1 && pout == 0 && !E2 && op.out[0].flags == (kOutMaster | kOutSlices);
             if (lean && J >= te.I && J * kTileM < n && i0 < n) {
-                // the zero-temperature step: one output a v + b1 E1 + c [i == j]
+                // the zero-temperature step: one output a v + b1 E1 + c [i == j].
+                // An 8-column group wholly inside the matrix and above the
+                // diagonal (every element exists and counts twice) takes the
+                // vector path: each lane reads E1 and writes its own row's 8
+                // columns with 16-byte accesses, and the mirrored rows go
+                // through the staging buffer (layout [column][row], stride 33:
+                // conflict-free both ways) so that 4 lanes write 8 consecutive
+                // elements each of one row.  Other groups (the diagonal's, the
+                // matrix edge) take the element-wise path.
                 const bool diag = (J == te.I);
                 const OutSpec &os = op.out[0];
                 const MatSlot &m = pr.mats[os.mat];
                 const float oa = os.a, ob = os.b1, oc = static_cast<float>(os.c), osc = os.s;
                 float *Mo = m.master;
                 __half *S0 = m.sl[0], *S1 = m.sl[1];
+                const int mr = lane >> 2;        // mirrored row within the group
+                const int mc = (lane & 3) * 8;   // its first column within the strip
 #pragma unroll
                 for (int c8 = 0; c8 < kTileM / 8; ++c8) {
                     const int j0 = J * kTileM + c8 * 8;
                     if (j0 >= n) break;
                     if (diag && j0 + 7 < i0) continue;
+                    const bool full = i0 + 32 <= n && j0 + 8 <= n && (!diag || j0 >= i0 + 32);
+                    if (full) {
+                        const size_t ro = static_cast<size_t>(i) * ldy + j0;
+                        const float4 ea = *reinterpret_cast<const float4 *>(E1 + ro);
+                        const float4 eb = *reinterpret_cast<const float4 *>(E1 + ro + 4);
+                        const float e[8] = {ea.x, ea.y, ea.z, ea.w, eb.x, eb.y, eb.z, eb.w};
+                        float val[8];
+                        float csq = 0.0f, crr = 0.0f;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float v = acc[c8 * 8 + u] * inv;
+                            val[u] = fmaf(oa, v, ob * e[u]);
+                            const float r = fmaf(ra, v, rb * e[u]);
+                            csq = fmaf(val[u], val[u], csq);
+                            crr = fmaf(r, r, crr);
+                            stf[u * 33 + lane] = val[u];
+                        }
+                        sq += 2.0 * static_cast<double>(csq);
+                        rr += 2.0 * static_cast<double>(crr);
+                        *reinterpret_cast<float4 *>(Mo + ro) = make_float4(val[0], val[1], val[2], val[3]);
+                        *reinterpret_cast<float4 *>(Mo + ro + 4) = make_float4(val[4], val[5], val[6], val[7]);
+                        uint4 hv, lv;
+                        split8(val, osc, hv, lv);
+                        const size_t so = static_cast<size_t>(i) * lds + j0;
+                        *reinterpret_cast<uint4 *>(S0 + so) = hv;
+                        *reinterpret_cast<uint4 *>(S1 + so) = lv;
+                        __syncwarp();
+                        float w[8];
+#pragma unroll
+                        for (int t2 = 0; t2 < 8; ++t2) w[t2] = stf[mr * 33 + mc + t2];
+                        __syncwarp();
+                        const size_t mo = static_cast<size_t>(j0 + mr) * ldy + i0 + mc;
+                        *reinterpret_cast<float4 *>(Mo + mo) = make_float4(w[0], w[1], w[2], w[3]);
+                        *reinterpret_cast<float4 *>(Mo + mo + 4) = make_float4(w[4], w[5], w[6], w[7]);
+                        split8(w, osc, hv, lv);
+                        const size_t ms = static_cast<size_t>(j0 + mr) * lds + i0 + mc;
+                        *reinterpret_cast<uint4 *>(S0 + ms) = hv;
+                        *reinterpret_cast<uint4 *>(S1 + ms) = lv;
+                        continue;
+                    }
                     float csq = 0.0f, crr = 0.0f;
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {

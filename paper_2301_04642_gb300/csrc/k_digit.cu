@@ -73,6 +73,25 @@ __device__ __forceinline__ double x_at(const MmaProb &pr, const SolveState *st, 
     return static_cast<double>(pr.Y[static_cast<size_t>(i) * pr.ldy + j]) + (i == j ? st->c : 0.0);
 }
 
+// round(x 2^54) by integer operations on the FP64 encoding (GB300's FP64
+// conversions are slow), clamped to |x| <= 1.98 so that the top digit of the
+// balanced base-256 expansion stays in [-128, 127]
+__device__ __forceinline__ long long fixed54(double x) {
+    constexpr long long kLim = 35668509048774328LL;  // 1.98 * 2^54
+    const long long bits = __double_as_longlong(x);
+    const int e = static_cast<int>((bits >> 52) & 0x7FF);
+    const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);  // |x| = m 2^(e - 1075)
+    const int sh = e - 1021;                                       // |x| 2^54 = m 2^sh
+    long long v;
+    if (e == 0) v = 0;                  // zero or subnormal
+    else if (sh > 2) v = kLim;          // |x| >= 4, Inf, NaN
+    else if (sh >= 0) v = m << sh;
+    else if (sh > -63) v = (m + (1LL << (-sh - 1))) >> (-sh);  // round half away from zero
+    else v = 0;
+    v = v > kLim ? kLim : v;
+    return bits < 0 ? -v : v;
+}
+
 }  // namespace
 
 __global__ void k_digit_prep(const MmaProb *probs, int nprobs) {
@@ -83,9 +102,8 @@ __global__ void k_digit_prep(const MmaProb *probs, int nprobs) {
         const int n = pr.n;
         for (int i = blockIdx.x; i < n; i += gridDim.x) {
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                // V = round(X/4 * 2^56); |X| <= 1.98 keeps the top digit in [-128, 127]
-                const double x = fmin(fmax(x_at(pr, st, i, j), -1.98), 1.98);
-                long long V = __double2ll_rn(x * 18014398509481984.0);  // 2^54
+                // V = round(X/4 * 2^56)
+                long long V = fixed54(x_at(pr, st, i, j));
                 const size_t at = static_cast<size_t>(i) * pr.lds + j;
 #pragma unroll
                 for (int a = kDigits - 1; a >= 0; --a) {
@@ -179,7 +197,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
         uint32_t blk = 0;  // K blocks of this CTA: level-buffer phase = blk & 1
         bool ok = true;
         bool any_commit = false;
-        constexpr uint32_t idesc = idesc_f16(kTileM, kDigitN, 0);
+        constexpr uint32_t idesc = idesc_f16(kTileM, kDigitN, 0);       // one level
+        constexpr uint32_t idesc2 = idesc_f16(kTileM, 2 * kDigitN, 0);  // two adjacent levels
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const TileEnt te = tiles[t];
             const MmaProb &pr = probs[te.prob];
@@ -206,26 +225,37 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                         db[a] = smem_desc_sw64(stages[stage].b[a]);
                     }
 #pragma unroll
-                    for (int L = 0; L < kDigits; ++L) {
-                        if (first && got) {
-                            // the drain of this level's previous block must be done
-                            got = mbar_wait_bounded(&tail->lfree[L], (blk & 1u) ^ 1u);
-                            if (!got) record_error(err, kErrTimeoutTmem);
-                        }
-                        if (got) {
-                            const uint32_t tmem_d = tmem_base + static_cast<uint32_t>(L * kDigitN);
+                    // A digit a against B digits c0 and c0 + 1 in one N = 128 MMA:
+                    // the two B tiles are adjacent in shared memory and levels
+                    // a + c0 and a + c0 + 1 are adjacent 64-column buffers.
+                    // Digit a = 0 meets every level first, so its MMAs start
+                    // the block's sums (accumulate off at the first K step).
 #pragma unroll
-                            for (int a = 0; a <= L; ++a) {
+                    for (int a = 0; a < kDigits; ++a) {
+#pragma unroll
+                        for (int c0 = 0; c0 + a < kDigits; c0 += 2) {
+                            const int L = a + c0;
+                            const bool pair = (L + 1 < kDigits);
+                            if (first && a == 0 && got) {
+                                // the drain of these levels' previous block must be done
+                                got = mbar_wait_bounded(&tail->lfree[L], (blk & 1u) ^ 1u);
+                                if (got && pair) got = mbar_wait_bounded(&tail->lfree[L + 1], (blk & 1u) ^ 1u);
+                                if (!got) record_error(err, kErrTimeoutTmem);
+                            }
+                            if (got) {
+                                const uint32_t tmem_d = tmem_base + static_cast<uint32_t>(L * kDigitN);
 #pragma unroll
                                 for (int kk = 0; kk < kDigitK / 16; ++kk) {
                                     const uint64_t off = static_cast<uint64_t>(kk * 2);  // 32 B along K
                                     const uint32_t acc = (first && a == 0 && kk == 0) ? 0u : 1u;
-                                    tc_mma_f16(tmem_d, da[a] + off, db[L - a] + off, idesc, acc);
+                                    tc_mma_f16(tmem_d, da[a] + off, db[c0] + off, pair ? idesc2 : idesc,
+                                               acc);
                                 }
+                                any_commit = true;
                             }
-                            if (last) tc_commit(&tail->lfull[L]);
-                            any_commit = true;
                         }
+                        // digit a is the last to add to level a (c = 0)
+                        if (last && got) tc_commit(&tail->lfull[a]);
                     }
                     tc_commit(&tail->empty[stage]);
                 }

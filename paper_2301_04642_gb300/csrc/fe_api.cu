@@ -96,6 +96,13 @@ struct Engine {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int ntc = 0, n64 = 0, nD = 0;    // tile counts of the uploaded lists
     bool any_tc = false, any_fp64 = false, any_digit = false;
+    // the step loop as a CUDA graph: WHILE(any problem active) { IF(tc) k_sym_mma;
+    // IF(fp64) k_fp64_step; IF(digit) k_digit_prep, k_digit_mma; k_control }
+    StepFlags *d_flags = nullptr;
+    StepFlags h_flags{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<uintptr_t> gkey;     // what the instantiated graph was built for
 };
 
 // One fe_submit request.
@@ -505,6 +512,8 @@ int eng_init(fe_ctx *ctx, Engine &e, cudaStream_t user_stream) {
         e.own_stream = true;
     }
     FE_CUDA(ctx, cudaMalloc(&e.d_err, sizeof(int)));
+    FE_CUDA(ctx, cudaMalloc(&e.d_flags, sizeof(StepFlags)));
+    FE_CUDA(ctx, cudaMemset(e.d_flags, 0, sizeof(StepFlags)));
     FE_CUDA(ctx, cudaEventCreate(&e.ev0));
     FE_CUDA(ctx, cudaEventCreate(&e.ev1));
     return FE_OK;
@@ -512,6 +521,9 @@ int eng_init(fe_ctx *ctx, Engine &e, cudaStream_t user_stream) {
 
 void eng_free(Engine &e) {
     if (e.stream) cudaStreamSynchronize(e.stream);
+    if (e.gexec) cudaGraphExecDestroy(e.gexec);
+    if (e.graph) cudaGraphDestroy(e.graph);
+    if (e.d_flags) cudaFree(e.d_flags);
     if (e.d_err) cudaFree(e.d_err);
     if (e.d_probs) cudaFree(e.d_probs);
     if (e.d_tiles) cudaFree(e.d_tiles);
@@ -599,7 +611,7 @@ int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int 
         k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
         ctx->launches += 3;
     }
-    k_control<<<k1 - k0, 256, 0, s>>>(e.d_probs + k0, k1 - k0);
+    k_control<<<k1 - k0, 256, 0, s>>>(e.d_probs + k0, k1 - k0, nullptr, 0, 0, 0, 0, 0u);
     ++ctx->launches;
     // the state images must stay valid until their copies ran
     FE_CUDA(ctx, cudaStreamSynchronize(s));
@@ -633,7 +645,7 @@ void eng_steps(fe_ctx *ctx, Engine &e, int np, int count, const std::vector<cuda
             ctx->launches += 2;
         }
         if (pev) cudaEventRecord((*pev)[4 * it + 3], s);
-        k_control<<<np, 256, 0, s>>>(e.d_probs, np);
+        k_control<<<np, 256, 0, s>>>(e.d_probs, np, nullptr, 0, 0, 0, 0, 0u);
         ++ctx->launches;
     }
 }
@@ -681,6 +693,126 @@ void fill_result(const SolveState &st, int herr, double ms, fe_result &r) {
     r.ms = ms;
 }
 
+// The step loop of the uploaded table as an instantiated CUDA graph (built
+// once per table layout): the control kernel sets the loop condition and the
+// kernel switches of the next step on the device, so exactly the steps and
+// kernels that have work run, with no host round trip.
+int eng_graph(fe_ctx *ctx, Engine &e, int np) {
+    std::vector<uintptr_t> key = {reinterpret_cast<uintptr_t>(e.d_probs), reinterpret_cast<uintptr_t>(e.d_tiles),
+                                  reinterpret_cast<uintptr_t>(e.d_tiles64), reinterpret_cast<uintptr_t>(e.d_tilesD),
+                                  static_cast<uintptr_t>(np), static_cast<uintptr_t>(e.ntc),
+                                  static_cast<uintptr_t>(e.n64), static_cast<uintptr_t>(e.nD),
+                                  static_cast<uintptr_t>(e.any_tc), static_cast<uintptr_t>(e.any_fp64),
+                                  static_cast<uintptr_t>(e.any_digit)};
+    if (e.gexec && key == e.gkey) return FE_OK;
+    if (e.gexec) cudaGraphExecDestroy(e.gexec);
+    if (e.graph) cudaGraphDestroy(e.graph);
+    e.gexec = nullptr;
+    e.graph = nullptr;
+    e.gkey.clear();
+    cudaGraph_t g;
+    FE_CUDA(ctx, cudaGraphCreate(&g, 0));
+    e.graph = g;
+    cudaGraphConditionalHandle hl = 0, ht = 0, hf = 0, hd = 0;
+    // defaults: the first step runs every kernel family (each skips problems
+    // whose step is not its own); later steps follow the control kernel.
+    // A handle exists only for a family the graph contains.
+    unsigned hvalid = kStepActive;
+    FE_CUDA(ctx, cudaGraphConditionalHandleCreate(&hl, g, 1, cudaGraphCondAssignDefault));
+    if (e.any_tc) {
+        FE_CUDA(ctx, cudaGraphConditionalHandleCreate(&ht, g, 1, cudaGraphCondAssignDefault));
+        hvalid |= kStepTc;
+    }
+    if (e.any_fp64) {
+        FE_CUDA(ctx, cudaGraphConditionalHandleCreate(&hf, g, 1, cudaGraphCondAssignDefault));
+        hvalid |= kStepFp64;
+    }
+    if (e.any_digit) {
+        FE_CUDA(ctx, cudaGraphConditionalHandleCreate(&hd, g, 1, cudaGraphCondAssignDefault));
+        hvalid |= kStepDigit;
+    }
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hl;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    FE_CUDA(ctx, cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    cudaGraphNode_t prev = nullptr;
+    // an IF node in the loop body after `prev`; returns its body graph
+    auto add_if = [&](cudaGraphConditionalHandle h, cudaGraph_t *ib) -> cudaError_t {
+        cudaGraphNodeParams ip = {};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = h;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t in;
+        cudaError_t r = cudaGraphAddNode(&in, body, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &ip);
+        if (r == cudaSuccess) {
+            prev = in;
+            *ib = ip.conditional.phGraph_out[0];
+        }
+        return r;
+    };
+    auto add_kernel = [&](cudaGraph_t gr, const void *fn, int grid, int block, size_t smem, void **args,
+                          cudaGraphNode_t *dep, cudaGraphNode_t *out) -> cudaError_t {
+        cudaKernelNodeParams kp = {};
+        kp.func = const_cast<void *>(fn);
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(block);
+        kp.sharedMemBytes = static_cast<unsigned>(smem);
+        kp.kernelParams = args;
+        return cudaGraphAddKernelNode(out, gr, dep, dep ? 1 : 0, &kp);
+    };
+    const MmaProb *probs = e.d_probs;
+    int *err = e.d_err;
+    cudaGraphNode_t kn, kn2;
+    if (e.any_tc) {
+        cudaGraph_t ib;
+        FE_CUDA(ctx, add_if(ht, &ib));
+        const TileEnt *tl = e.d_tiles;
+        int nt = e.ntc;
+        void *args[] = {&probs, &tl, &nt, &err};
+        FE_CUDA(ctx, add_kernel(ib, reinterpret_cast<const void *>(k_sym_mma),
+                                std::max(1, std::min(e.ntc, ctx->num_sms)), kSymThreads, mma_smem_bytes(),
+                                args, nullptr, &kn));
+    }
+    if (e.any_fp64) {
+        cudaGraph_t ib;
+        FE_CUDA(ctx, add_if(hf, &ib));
+        const Tile64 *tl = e.d_tiles64;
+        int nt = e.n64;
+        void *args[] = {&probs, &tl, &nt};
+        FE_CUDA(ctx, add_kernel(ib, reinterpret_cast<const void *>(k_fp64_step),
+                                std::max(1, std::min(e.n64, 4 * ctx->num_sms)), 256, 0, args, nullptr, &kn));
+    }
+    if (e.any_digit) {
+        cudaGraph_t ib;
+        FE_CUDA(ctx, add_if(hd, &ib));
+        int npp = np;
+        void *pargs[] = {&probs, &npp};
+        FE_CUDA(ctx, add_kernel(ib, reinterpret_cast<const void *>(k_digit_prep), 2 * ctx->num_sms, 256, 0,
+                                pargs, nullptr, &kn));
+        const TileEnt *tl = e.d_tilesD;
+        int nt = e.nD;
+        void *args[] = {&probs, &tl, &nt, &err};
+        FE_CUDA(ctx, add_kernel(ib, reinterpret_cast<const void *>(k_digit_mma),
+                                std::max(1, std::min(e.nD, ctx->num_sms)), kMmaThreads, digit_smem_bytes(),
+                                args, &kn, &kn2));
+    }
+    {
+        int npp = np;
+        StepFlags *fl = e.d_flags;
+        void *args[] = {&probs, &npp, &fl, &hl, &ht, &hf, &hd, &hvalid};
+        FE_CUDA(ctx, add_kernel(body, reinterpret_cast<const void *>(k_control), np, 256, 0, args,
+                                prev ? &prev : nullptr, &kn));
+    }
+    FE_CUDA(ctx, cudaGraphInstantiate(&e.gexec, g, 0));
+    e.gkey = key;
+    return FE_OK;
+}
+
 // Run validated problems on acquired slots to completion (blocking calls).
 int run_problems(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) {
     Engine &e = ctx->eng;
@@ -703,7 +835,16 @@ int run_problems(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) {
             ctx->pev.push_back(ev);
         }
     }
-    eng_steps(ctx, e, np, nloop, ctx->prof ? &ctx->pev : nullptr);
+    const bool use_graph = !ctx->prof;  // per-launch events need plain launches
+    if (use_graph) {
+        rc = eng_graph(ctx, e, np);
+        if (rc != FE_OK) return rc;
+        FE_CUDA(ctx, cudaMemsetAsync(e.d_flags, 0, sizeof(StepFlags), s));
+        FE_CUDA(ctx, cudaGraphLaunch(e.gexec, s));
+        FE_CUDA(ctx, cudaMemcpyAsync(&e.h_flags, e.d_flags, sizeof(StepFlags), cudaMemcpyDeviceToHost, s));
+    } else {
+        eng_steps(ctx, e, np, nloop, ctx->prof ? &ctx->pev : nullptr);
+    }
     for (int k = 0; k < np; ++k) {
         rc = eng_finish(ctx, e, k, jobs[k]);
         if (rc != FE_OK) return rc;
@@ -715,6 +856,13 @@ int run_problems(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) {
     FE_CUDA(ctx, cudaStreamSynchronize(s));
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, e.ev0, e.ev1);
+    if (use_graph) {
+        // kernels the graph ran: a control per step, every family once in the
+        // first step, then the families the control kernel switched on
+        const StepFlags &fl = e.h_flags;
+        ctx->launches += fl.n_body + (e.any_tc ? 1 : 0) + (e.any_fp64 ? 1 : 0) + (e.any_digit ? 2 : 0) +
+                         fl.n_tc + fl.n_fp64 + 2ll * fl.n_digit;
+    }
     if (ctx->prof) {
         // launches that did work: the phases run in order (single FP16, split,
         // FP64), so the first it_phase[0] + it_phase[1] tensor-core launches

@@ -82,7 +82,18 @@ __global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *r
 // Zero temperature: X0 -> (c, Y0) and slices.  Finite temperature: z0.  Per-block partials.
 __global__ void k_init_x0(const MmaProb *probs, int prob);
 // Step control for every problem (one block per problem).
-__global__ void k_control(const MmaProb *probs, int nprobs);
+// Step bookkeeping of the graph-driven step loop (see k_control).
+enum StepBits : unsigned { kStepActive = 1u, kStepTc = 2u, kStepFp64 = 4u, kStepDigit = 8u };
+struct StepFlags {
+    unsigned mask, count;                  // per step: OR of the problems' needs; blocks done
+    unsigned n_body, n_tc, n_fp64, n_digit;  // steps run; steps that launched each family
+};
+// Control step: one block per problem.  With flags (inside the step graph)
+// the last block to finish also sets the graph's loop and kernel switches.
+__global__ void k_control(const MmaProb *probs, int nprobs, StepFlags *flags,
+                          cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_tc,
+                          cudaGraphConditionalHandle h_fp64, cudaGraphConditionalHandle h_digit,
+                          unsigned hvalid);
 // FP64-accurate product + SP2 update (upper tiles, mirrored), per-tile partials.
 __global__ void k_fp64_step(const MmaProb *probs, const Tile64 *tiles, int ntiles);
 // D = X -> out (FP64, ld), partials of tr(H D) and tr D.

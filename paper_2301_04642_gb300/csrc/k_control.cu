@@ -447,10 +447,9 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
 
 }  // namespace
 
-__global__ void k_control(const MmaProb *probs, int nprobs) {
-    const int p = blockIdx.x;
-    if (p >= nprobs) return;
-    const MmaProb &pr = probs[p];
+namespace {
+
+__device__ void control_one(const MmaProb &pr) {
     SolveState *st = pr.st;
     if (st->done) return;
 
@@ -491,6 +490,49 @@ __global__ void k_control(const MmaProb *probs, int nprobs) {
     }
     if (st->method == kMethodFermi) control_fermi(st, s_a[0], s_b[0], s_c[0]);
     else control_sp2(st, s_a[0], s_b[0], s_d[0]);
+}
+
+}  // namespace
+
+__global__ void k_control(const MmaProb *probs, int nprobs, StepFlags *flags,
+                          cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_tc,
+                          cudaGraphConditionalHandle h_fp64, cudaGraphConditionalHandle h_digit,
+                          unsigned hvalid) {
+    const int p = blockIdx.x;
+    if (p < nprobs) control_one(probs[p]);
+    if (!flags || threadIdx.x != 0) return;
+    // Inside the step graph: collect what the next step needs over all
+    // problems; the block that finishes last sets the graph's conditions
+    // (loop on while any problem is active; one switch per kernel family).
+    unsigned bits = 0;
+    if (p < nprobs) {
+        const SolveState *st = probs[p].st;
+        const int kind = *reinterpret_cast<const volatile int *>(&st->kind);
+        if (!*reinterpret_cast<const volatile int *>(&st->done)) {
+            bits |= kStepActive;
+            if (kind == kTcSingle || kind == kTcSplit || kind == kTcElem) bits |= kStepTc;
+            if (kind == kFp64 || kind == kDf) bits |= kStepFp64;
+            if (kind == kDigit) bits |= kStepDigit;
+        }
+    }
+    if (bits) atomicOr(&flags->mask, bits);
+    __threadfence();
+    if (atomicAdd(&flags->count, 1u) != static_cast<unsigned>(gridDim.x) - 1u) return;
+    __threadfence();
+    const unsigned m = atomicExch(&flags->mask, 0u);
+    atomicExch(&flags->count, 0u);
+    const bool on = (m & kStepActive) != 0;
+    // hvalid: which handles exist in this graph (bit = the family's StepBits)
+    if (hvalid & kStepActive) cudaGraphSetConditional(h_loop, on ? 1u : 0u);
+    if (hvalid & kStepTc) cudaGraphSetConditional(h_tc, (on && (m & kStepTc)) ? 1u : 0u);
+    if (hvalid & kStepFp64) cudaGraphSetConditional(h_fp64, (on && (m & kStepFp64)) ? 1u : 0u);
+    if (hvalid & kStepDigit) cudaGraphSetConditional(h_digit, (on && (m & kStepDigit)) ? 1u : 0u);
+    flags->n_body += 1;
+    if (on) {
+        flags->n_tc += (m & kStepTc) ? 1u : 0u;
+        flags->n_fp64 += (m & kStepFp64) ? 1u : 0u;
+        flags->n_digit += (m & kStepDigit) ? 1u : 0u;
+    }
 }
 
 }  // namespace fe

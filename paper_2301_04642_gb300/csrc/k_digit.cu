@@ -197,8 +197,6 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
         uint32_t blk = 0;  // K blocks of this CTA: level-buffer phase = blk & 1
         bool ok = true;
         bool any_commit = false;
-        constexpr uint32_t idesc = idesc_f16(kTileM, kDigitN, 0);       // one level
-        constexpr uint32_t idesc2 = idesc_f16(kTileM, 2 * kDigitN, 0);  // two adjacent levels
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const TileEnt te = tiles[t];
             const MmaProb &pr = probs[te.prob];
@@ -225,31 +223,32 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                         db[a] = smem_desc_sw64(stages[stage].b[a]);
                     }
 #pragma unroll
-                    // A digit a against B digits c0 and c0 + 1 in one N = 128 MMA:
-                    // the two B tiles are adjacent in shared memory and levels
-                    // a + c0 and a + c0 + 1 are adjacent 64-column buffers.
-                    // Digit a = 0 meets every level first, so its MMAs start
-                    // the block's sums (accumulate off at the first K step).
+                    // A digit a against up to four B digits c0 .. c0 + w - 1 in
+                    // one MMA of N = 64 w: those B tiles are adjacent in shared
+                    // memory and levels a + c0 .. a + c0 + w - 1 are adjacent
+                    // 64-column buffers.  Digit a = 0 meets every level first,
+                    // so its MMAs start the block's sums (accumulate off at
+                    // the first K step).
 #pragma unroll
                     for (int a = 0; a < kDigits; ++a) {
 #pragma unroll
-                        for (int c0 = 0; c0 + a < kDigits; c0 += 2) {
+                        for (int c0 = 0; c0 + a < kDigits; c0 += 4) {
                             const int L = a + c0;
-                            const bool pair = (L + 1 < kDigits);
+                            const int w = (kDigits - L < 4) ? (kDigits - L) : 4;  // levels in this MMA
                             if (first && a == 0 && got) {
                                 // the drain of these levels' previous block must be done
-                                got = mbar_wait_bounded(&tail->lfree[L], (blk & 1u) ^ 1u);
-                                if (got && pair) got = mbar_wait_bounded(&tail->lfree[L + 1], (blk & 1u) ^ 1u);
+                                for (int l = L; l < L + w && got; ++l)
+                                    got = mbar_wait_bounded(&tail->lfree[l], (blk & 1u) ^ 1u);
                                 if (!got) record_error(err, kErrTimeoutTmem);
                             }
                             if (got) {
                                 const uint32_t tmem_d = tmem_base + static_cast<uint32_t>(L * kDigitN);
+                                const uint32_t id = idesc_f16(kTileM, w * kDigitN, 0);
 #pragma unroll
                                 for (int kk = 0; kk < kDigitK / 16; ++kk) {
                                     const uint64_t off = static_cast<uint64_t>(kk * 2);  // 32 B along K
                                     const uint32_t acc = (first && a == 0 && kk == 0) ? 0u : 1u;
-                                    tc_mma_f16(tmem_d, da[a] + off, db[c0] + off, pair ? idesc2 : idesc,
-                                               acc);
+                                    tc_mma_f16(tmem_d, da[a] + off, db[c0] + off, id, acc);
                                 }
                                 any_commit = true;
                             }

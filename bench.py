@@ -49,6 +49,14 @@ def load_peaks():
 WORKLOADS = {
     "gapped_n4096": dict(make=lambda: hp_synth.workload_n4096(), precision="mixed"),
     "gapped_n256_fp64": dict(make=lambda: hp_synth.workload_n256(), precision="fp64"),
+    # larger single solves (generated on the GPU: the CPU QR would take minutes)
+    "gapped_n16384": dict(make=lambda: hp_synth.gapped(16384, 13926, (-3.0, -0.01), (0.01, 1.0), 1004,
+                                                         device="cuda", name="gapped_n16384"),
+                          precision="mixed"),
+    "fermi_n16384": dict(make=lambda: hp_synth.workload_n16384_ft(device="cuda"), precision="mixed"),
+    # many problems per step (see bench_batch / bench_serve)
+    "ragged_batch64": dict(make=None, precision="mixed"),
+    "serve_poisson": dict(make=None, precision="mixed"),
 }
 
 
@@ -201,11 +209,20 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        if wl["make"] is None or args.workload in ("gapped_n16384", "fermi_n16384"):
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm is timed on the "
+                              "single-solve workloads gapped_n4096 and gapped_n256_fp64"}), flush=True)
+            return
         reference_arm(args, wl["make"](), args.workload)
         return
 
     import torch
     import paper_2301_04642_gb300 as fe
+
+    if args.workload == "ragged_batch64":
+        return bench_batch(args, torch, fe)
+    if args.workload == "serve_poisson":
+        return bench_serve(args, torch, fe)
 
     dist = None
     if world > 1:
@@ -219,7 +236,8 @@ def main():
     p = wl["make"]()
     n = p.n
     prec = wl["precision"]
-    H = torch.from_numpy(p.H).to(dev)
+    kT = float(getattr(p, "kT", 0.0) or 0.0)
+    H = p.H.to(dev) if torch.is_tensor(p.H) else torch.from_numpy(p.H).to(dev)
     D = torch.empty_like(H)
     stream = torch.cuda.Stream(device=dev)
     ctx = fe.Context(device=local_rank, stream=stream.cuda_stream)
@@ -228,7 +246,7 @@ def main():
     def one():
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
-        return ctx.solve(H, p.ne, tol=p.tol, D=D, precision=prec)
+        return ctx.solve(H, p.ne, kT=kT, tol=p.tol, D=D, precision=prec)
 
     for _ in range(args.warmup):
         r = one()
@@ -260,17 +278,17 @@ def main():
     value = world * args.steps / (t_ms / 1e3)
 
     # ---- end to end through the C ABI with pinned host buffers
-    Hh = torch.from_numpy(p.H).pin_memory()
+    Hh = (p.H.cpu() if torch.is_tensor(p.H) else torch.from_numpy(p.H)).pin_memory()
     Dh = torch.empty_like(Hh).pin_memory()
     for _ in range(2):
-        ctx.solve(Hh.numpy(), p.ne, tol=p.tol, D=Dh.numpy(), precision=prec)
+        ctx.solve(Hh.numpy(), p.ne, kT=kT, tol=p.tol, D=Dh.numpy(), precision=prec)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(args.steps):
-        re = ctx.solve(Hh.numpy(), p.ne, tol=p.tol, D=Dh.numpy(), precision=prec)
+        re = ctx.solve(Hh.numpy(), p.ne, kT=kT, tol=p.tol, D=Dh.numpy(), precision=prec)
         _ = re["e_band"]
     f1.record(stream)
     torch.cuda.synchronize()
@@ -335,7 +353,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f16x2+f16digits" if prec == "mixed" else "f64",
            "data": "synthetic",
-           "config": {"workload": args.workload, "n": n, "n_e": p.ne, "kT": 0.0,
+           "config": {"workload": args.workload, "n": n, "n_e": p.ne, "kT": kT,
                       "precision": prec, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "256 MiB buffer written before every step; working set > 129 MB L2"},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
@@ -347,7 +365,8 @@ def main():
            "gpu_launches": launches, "roofline": roof, "kernels": kernels,
            "clocks": clk.summary()}
 
-    if rank == 0 and not args.no_baselines:
+    small_zero_t = n <= 4096 and kT == 0.0  # plain FP64 / syevd / CPU arms only where they finish
+    if rank == 0 and not args.no_baselines and small_zero_t:
         base = {}
         # the same expansion with every product in FP64 on this GPU
         t0 = time.perf_counter()
@@ -368,15 +387,131 @@ def main():
         out["baselines_same_gpu"] = base
         del Dsy, V
     if rank == 0:
-        import oracle
-        lo, hi = oracle.gershgorin(p.H)
-        prods = sp2_products_on_spectrum(p.lam, lo, hi, p.ne, 5e-8)
-        v, thr, sample = cpu_oracle_sample(p, prods)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample}
+        if small_zero_t:
+            import oracle
+            lo, hi = oracle.gershgorin(p.H)
+            prods = sp2_products_on_spectrum(p.lam, lo, hi, p.ne, 5e-8)
+            v, thr, sample = cpu_oracle_sample(p, prods)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample}
+        else:
+            out["cpu_baseline"] = None
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _kernel_times(ctx, n_list):
+    """Per-kernel CUDA-event times of the last profiled solve or batch."""
+    prof = ctx.profile_read()
+    return {"k_sym_mma_ms": prof["tc_ms"], "k_sym_mma_launches": prof["tc_launches"],
+            "fp64_accurate_ms": prof["fp64_ms"], "fp64_accurate_launches": prof["fp64_launches"],
+            "solve_ms": prof["solve_ms"]}
+
+
+def bench_batch(args, torch, fe):
+    """64 gapped problems, n log-uniform in [512, 6144], in one fe_solve_batch."""
+    dev = torch.device("cuda", 0)
+    sizes = hp_synth.ragged_batch_sizes()
+    probs = [hp_synth.ragged_member(i, device="cuda") for i in range(len(sizes))]
+    items = []
+    for p in probs:
+        H = p.H.to(dev) if torch.is_tensor(p.H) else torch.from_numpy(p.H).to(dev)
+        items.append(dict(H=H, ne=p.ne, tol=p.tol, D=torch.empty_like(H), precision="mixed"))
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fe.Context(device=0, stream=stream.cuda_stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def one():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        return ctx.solve_batch(items)
+
+    for _ in range(args.warmup):
+        rc, res = one()
+    l0 = ctx.launch_count()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            rc, res = one()
+            assert rc == 0
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    launches = ctx.launch_count() - l0
+    ctx.profile(True)
+    one()
+    kern = _kernel_times(ctx, sizes)
+    ctx.profile(False)
+    products = sum(float(n) ** 3 * r["iters"] * 2.0 for n, r in zip(sizes, res))
+    value = len(items) * args.steps / (t_ms / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f16x2+f16digits", "data": "synthetic",
+           "config": {"workload": "ragged_batch64", "problems": len(items), "n_min": min(sizes),
+                      "n_max": max(sizes), "n_e": "round(0.85 n)", "parallelism": "single",
+                      "l2": "256 MiB buffer written before every step"},
+           "effective_tflops": products * args.steps / (t_ms / 1e3) / 1e12,
+           "max_trace_err": max(abs(r["trace"] - p.ne) for r, p in zip(res, probs)),
+           "gpu_launches": launches, "kernels": kern, "clocks": clk.summary(), "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def bench_serve(args, torch, fe):
+    """Continuous batching: Poisson arrivals of mixed zero-T / finite-T requests
+    (n log-uniform in [1024, 8192]: the sub-capacity variant of the serving
+    configuration), submitted at their arrival times; latency = submit to done."""
+    dev = torch.device("cuda", 0)
+    rate = float(os.environ.get("FE_SERVE_RATE", "20"))
+    count = int(os.environ.get("FE_SERVE_COUNT", "40"))
+    u = hp_synth.uniform(3000, 4 * count)
+    reqs = []
+    for k in range(count):
+        n = int(round(math.exp(math.log(1024) + u[4 * k] * (math.log(8192) - math.log(1024)))))
+        n = max(64, n)
+        ne = round(0.85 * n)
+        if u[4 * k + 1] < 0.7:
+            gap = 0.01 + 0.09 * u[4 * k + 2]
+            p = hp_synth.gapped(n, ne, (-3.0, -gap / 2), (gap / 2, 1.0), 3100 + k, device="cuda")
+            kT = 0.0
+        else:
+            kT = 0.001 + 0.009 * u[4 * k + 2]
+            p = hp_synth.smeared(n, float(ne), kT, -2.0, 1.0, 3100 + k, device="cuda")
+        H = p.H.to(dev) if torch.is_tensor(p.H) else torch.from_numpy(p.H).to(dev)
+        reqs.append((n, ne, kT, p.tol, H, torch.empty_like(H)))
+    gaps = [-math.log(max(1e-12, 1.0 - x)) / rate for x in hp_synth.uniform(3001, count)]
+    ctx = fe.Context(device=0)
+    torch.cuda.synchronize()
+    # warm the kernels and slots on the first request
+    t = ctx.submit(reqs[0][4], reqs[0][1], kT=reqs[0][2], tol=reqs[0][3], D=reqs[0][5])
+    ctx.wait(t)
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        tickets = []
+        due = t0
+        for (n, ne, kT, tol, H, D), g in zip(reqs, gaps):
+            due += g
+            while time.perf_counter() < due:
+                time.sleep(0.0002)
+            tickets.append(ctx.submit(H, ne, kT=kT, tol=tol, D=D))
+        res = [ctx.wait(tk, timeout_s=1800) for tk in tickets]
+        t1 = time.perf_counter()
+    lat = [r["ms"] for r in res]
+    ok = sum(1 for r in res if r["status"] == 0)
+    value = ok / (t1 - t0)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": count, "warmup": 1,
+           "ms_per_step": (t1 - t0) * 1e3 / count, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f16x2+f16digits", "data": "synthetic",
+           "config": {"workload": "serve_poisson", "requests": count, "rate_per_s": rate,
+                      "n": "log-uniform [1024, 8192]", "mix": "70% gapped, 30% finite T",
+                      "parallelism": "single"},
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+           "completed_ok": ok, "clocks": clk.summary(), "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+    ctx.close()
 
 
 if __name__ == "__main__":

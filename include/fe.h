@@ -104,7 +104,8 @@ typedef struct {
     int iters_by_phase[4];  /* [0] single-FP16, [1] split-FP16, [2] FP64, [3] finite-T steps */
     double e_band;          /* tr(Hp D), FP64                                       */
     double trace;           /* tr D                                                 */
-    double idem_fro;        /* ||D^2 - D||_F measured on the last FP64 product (0 T) */
+    double idem_fro;        /* ||X^2 - X||_F of the last product's input, measured in its
+                               epilogue (0 T); D, its output, is closer to idempotent */
     double mu;              /* chemical potential (finite T), HOMO/LUMO midpoint estimate (0 T) */
     double eps_min;         /* Gershgorin lower bound of Hp                          */
     double eps_max;         /* Gershgorin upper bound of Hp                          */

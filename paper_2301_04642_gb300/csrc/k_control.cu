@@ -153,11 +153,17 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
             // deviations are about the square of fro_hist[0] = ||X^2 - X||_F of
             // the pair's second input.  The trace must also have landed: when
             // the correction was not admissible (deviations of both signs
-            // cancel in tr(X - X^2)), the next pair squares what is left.
+            // cancel in tr(X - X^2)), further products square what is left.
+            // After a pair every eigenvalue's x (1 - x) is >= 0 (squared
+            // deviations), so t1 - t2 = sum x (1 - x) bounds ||X^2 - X||_F;
+            // from then on a single product may end the phase (the SP2 rule
+            // picks the branch that squares the side holding the trace
+            // error, e.g. one slowly converging eigenvalue next to the gap).
             const double f0 = st->fro_hist[0];
-            if (nfp64 >= 2 && (nfp64 & 1) == 0 &&
-                ((f0 * f0 <= 5e-9 && fabs(idem) <= 1e-8 && fabs(t1 - ne) <= 2e-10) || nfp64 >= 6))
-                done = true;
+            const bool idem_small = idem >= -1e-12 && idem <= 5e-9;
+            const bool trace_ok = fabs(t1 - ne) <= 5e-10;
+            const bool pair_ok = (nfp64 & 1) == 0 ? f0 * f0 <= 5e-9 : true;
+            if (nfp64 >= 2 && ((idem_small && trace_ok && pair_ok) || nfp64 >= 6)) done = true;
         }
     }
     if (!done && st->iter >= st->max_iters) {

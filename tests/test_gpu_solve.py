@@ -148,3 +148,33 @@ def test_config_n4096_mixed():
     print(res, eps1, e_err, tr_err, idem)
     assert res["status"] == 0
     assert eps1 <= TOL_EPS1 and e_err <= TOL_E and tr_err <= TOL_TR and idem <= TOL_IDEM
+
+
+def test_config_n16384_mixed():
+    """The zero-temperature schedule at n = 16384 (gap 0.02 Ha in a Gershgorin
+    interval of ~225 Ha: a slowly converging eigenvalue next to the gap).
+    Checked by the exact trace, the band energy, sampled entries of the
+    constructed projector, and ||D - D_ref||_F and ||D^2 - D||_F estimated with
+    random probes (E ||A v||^2 = ||A||_F^2 for v ~ N(0, I))."""
+    n, ne = 16384, 13926
+    p = hp_synth.gapped(n, ne, (-3.0, -0.01), (0.01, 1.0), 1004, device="cuda")
+    D = torch.empty_like(p.H)
+    r = ctx().solve(p.H, ne, tol=p.tol, D=D)
+    assert r["status"] == 0
+    f = (np.arange(n) < ne).astype(float)
+    assert abs(r["trace"] - ne) <= TOL_TR
+    assert abs(r["e_band"] - float(np.sum(f * p.lam))) / ne <= TOL_E
+    Q = p.Q.cpu().numpy()
+    Dh = D.cpu().numpy()
+    assert abs(np.trace(Dh) - ne) <= TOL_TR
+    rng = np.random.default_rng(6)
+    rows, cols = rng.integers(0, n, 2000), rng.integers(0, n, 2000)
+    want = oracle.density_entries(Q, f, rows, cols)
+    assert np.abs(Dh[rows, cols] - want).max() <= 1e-6
+    V = rng.standard_normal((n, 4))
+    DV = Dh @ V
+    err = DV - Q @ (f[:, None] * (Q.T @ V))
+    eps1 = math.sqrt(np.sum(err ** 2) / 4) / math.sqrt(ne)
+    idem = math.sqrt(np.sum((Dh @ DV - DV) ** 2) / 4)
+    print(r, eps1, idem)
+    assert eps1 <= TOL_EPS1 and idem <= TOL_IDEM

@@ -106,10 +106,11 @@ typedef struct {
     double trace;           /* tr D                                                 */
     double idem_fro;        /* ||X^2 - X||_F of the last product's input, measured in its
                                epilogue (0 T); D, its output, is closer to idempotent */
-    double mu;              /* chemical potential (finite T), HOMO/LUMO midpoint estimate (0 T) */
+    double mu;              /* chemical potential (finite T); NaN at zero T          */
     double eps_min;         /* Gershgorin lower bound of Hp                          */
     double eps_max;         /* Gershgorin upper bound of Hp                          */
-    double ms;              /* device time of the solve (CUDA events), milliseconds */
+    double ms;              /* fe_solve / fe_solve_batch: device time of the solve
+                               (CUDA events); fe_poll: submit-to-done latency, ms   */
 } fe_result;
 
 typedef uint64_t fe_ticket;

@@ -453,12 +453,87 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                     __syncwarp();
                 }
             } else if (J >= te.I && J * kTileM < n && i0 < n) {
+                // any other step (1-3 outputs, E1/E2, FP64 outputs): groups
+                // wholly above the diagonal take the 16-byte path as in the
+                // zero-temperature step (one output after another; an output
+                // overwrites E1/E2 in place only when it is the single one)
                 const bool diag = (J == te.I);
+                bool has_f64 = false;
+                for (int o = 0; o < nout; ++o) has_f64 = has_f64 || (op.out[o].flags & (kOutF64a | kOutF64b));
+                const int mr = lane >> 2, mc = (lane & 3) * 8;
 #pragma unroll
                 for (int c8 = 0; c8 < kTileM / 8; ++c8) {
                     const int j0 = J * kTileM + c8 * 8;
                     if (j0 >= n) break;
                     if (diag && j0 + 7 < i0) continue;  // strictly below the diagonal
+                    if (!has_f64 && i0 + 32 <= n && j0 + 8 <= n && (!diag || j0 >= i0 + 32)) {
+                        const size_t ro = static_cast<size_t>(i) * ldy + j0;
+                        float e1[8], e2[8], v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) { e1[u] = 0.0f; e2[u] = 0.0f; }
+                        if (E1) {
+                            const float4 a4 = *reinterpret_cast<const float4 *>(E1 + ro);
+                            const float4 b4 = *reinterpret_cast<const float4 *>(E1 + ro + 4);
+                            e1[0] = a4.x; e1[1] = a4.y; e1[2] = a4.z; e1[3] = a4.w;
+                            e1[4] = b4.x; e1[5] = b4.y; e1[6] = b4.z; e1[7] = b4.w;
+                        }
+                        if (E2) {
+                            const float4 a4 = *reinterpret_cast<const float4 *>(E2 + ro);
+                            const float4 b4 = *reinterpret_cast<const float4 *>(E2 + ro + 4);
+                            e2[0] = a4.x; e2[1] = a4.y; e2[2] = a4.z; e2[3] = a4.w;
+                            e2[4] = b4.x; e2[5] = b4.y; e2[6] = b4.z; e2[7] = b4.w;
+                        }
+                        float crr = 0.0f;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            v[u] = acc[c8 * 8 + u] * inv;
+                            const float r = fmaf(ra, v[u], rb * e1[u]);
+                            crr = fmaf(r, r, crr);
+                        }
+                        rr += 2.0 * static_cast<double>(crr);
+                        const size_t so = static_cast<size_t>(i) * lds + j0;
+                        const size_t mo = static_cast<size_t>(j0 + mr) * ldy + i0 + mc;
+                        const size_t ms = static_cast<size_t>(j0 + mr) * lds + i0 + mc;
+                        for (int o = 0; o < nout; ++o) {
+                            const OutSpec &os = op.out[o];
+                            const int fl = os.flags;
+                            const MatSlot &m = pr.mats[os.mat];
+                            float val[8];
+                            float csq = 0.0f;
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                val[u] = fmaf(os.a, v[u], fmaf(os.b1, e1[u], os.b2 * e2[u]));
+                                csq = fmaf(val[u], val[u], csq);
+                                stf[u * 33 + lane] = val[u];
+                            }
+                            if (o == pout) sq += 2.0 * static_cast<double>(csq);
+                            uint4 hv, lv;
+                            if (fl & kOutMaster) {
+                                *reinterpret_cast<float4 *>(m.master + ro) = make_float4(val[0], val[1], val[2], val[3]);
+                                *reinterpret_cast<float4 *>(m.master + ro + 4) = make_float4(val[4], val[5], val[6], val[7]);
+                            }
+                            if (fl & kOutSlices) {
+                                split8(val, os.s, hv, lv);
+                                *reinterpret_cast<uint4 *>(m.sl[0] + so) = hv;
+                                *reinterpret_cast<uint4 *>(m.sl[1] + so) = lv;
+                            }
+                            __syncwarp();
+                            float w[8];
+#pragma unroll
+                            for (int t2 = 0; t2 < 8; ++t2) w[t2] = stf[mr * 33 + mc + t2];
+                            __syncwarp();
+                            if (fl & kOutMaster) {
+                                *reinterpret_cast<float4 *>(m.master + mo) = make_float4(w[0], w[1], w[2], w[3]);
+                                *reinterpret_cast<float4 *>(m.master + mo + 4) = make_float4(w[4], w[5], w[6], w[7]);
+                            }
+                            if (fl & kOutSlices) {
+                                split8(w, os.s, hv, lv);
+                                *reinterpret_cast<uint4 *>(m.sl[0] + ms) = hv;
+                                *reinterpret_cast<uint4 *>(m.sl[1] + ms) = lv;
+                            }
+                        }
+                        continue;
+                    }
                     // element (i, j0 + u) exists in this block's upper part
                     auto okf = [&](int u) { return i < n && j0 + u < n && (!diag || j0 + u >= i); };
                     auto e1f = [&](int u) { return E1 ? E1[static_cast<size_t>(j0 + u) * ldy + i] : 0.0f; };

@@ -24,7 +24,9 @@
 //   => z'' = N M^{-1},  N = 2 ((1 + t^2) z - t (I + z^2)),
 //                       M = (1 + t^2)(I + z^2) - 4 t z.
 // M^{-1} comes from Newton-Schulz, W <- W (2 I - M W), started at the
-// scalar w0 = 2 / (m_min + m_max) from the analytic bounds of M's spectrum.
+// scalar w0 = 2 / (m_min + m_max) from bounds of M's spectrum over
+// z in [-rho, rho], rho = tanh(beta_k R / 2) with R the Gershgorin radius
+// around mu: early stages (small z, M close to I) need few or no steps.
 // After the last stage up to three shift-only steps N = z - t I, M = I - t z
 // bring tr D near N_e, and a last product writes D0 = (I - z)/2 and
 // Q = (I - z^2)/4 = D0 - D0^2 in FP64; the output kernel forms
@@ -383,6 +385,12 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
         return;
     }
     const double beta_k = st->beta0 * ldexp(1.0, st->ft_stage);  // z = tanh(beta_k (H - mu)/2)
+    // spectral radius of z: |tanh(beta_k (lambda - mu)/2)| over the Gershgorin
+    // interval (z0 is linear in H, below tanh by < x^3/3 at |x| <= 1e-3; the
+    // margin also covers the expansion's rounding).  Early stages have small
+    // z, so M is close to I and Newton-Schulz needs few or no steps.
+    const double rad = fmax(fabs(st->emax - st->mu_t), fabs(st->emin - st->mu_t));
+    const double rho = fmin(1.0, tanh(0.5 * beta_k * rad) * (1.0 + 1e-6) + 1e-6);
     b = shift_only ? fmax(-1.0, fmin(1.0, b)) : fmax(-0.5, fmin(0.5, b));
     const double t = tanh(b);
     st->ft_t = t;
@@ -395,9 +403,13 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
         const double t2 = t * t;
         const double Mc = (1.0 + t2) * (1.0 + zc * zc) - 4.0 * t * zc;
         const double Nc = 2.0 * (1.0 + t2) * zc - 2.0 * t * (1.0 + zc * zc);
-        // spectrum of M = (1 - t z)^2 + (z - t)^2 for z in [-1, 1]
-        const double mmin = (1.0 - t2) * (1.0 - t2) / (1.0 + t2);
-        const double mmax = 2.0 * (1.0 + fabs(t)) * (1.0 + fabs(t));
+        // spectrum of M: m(x) = (1 + t^2)(1 + x^2) - 4 t x = (1 - t x)^2 + (x - t)^2
+        // over x in [-rho, rho]; a convex quadratic with its minimum at 2t/(1 + t^2)
+        const double m_p = (1.0 + t2) * (1.0 + rho * rho) - 4.0 * t * rho;
+        const double m_m = (1.0 + t2) * (1.0 + rho * rho) + 4.0 * t * rho;
+        const double mmax = fmax(m_p, m_m);
+        const double mmin = (fabs(2.0 * t / (1.0 + t2)) <= rho) ? (1.0 - t2) * (1.0 - t2) / (1.0 + t2)
+                                                                 : fmin(m_p, m_m);
         const double w0 = 2.0 / (mmin + mmax);
         st->w0 = w0;
         st->ft_nj = ns_steps(mmin, mmax);
@@ -423,10 +435,10 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
         st->ft_sub = kFtSquare;
         st->ft_last_mat = M;
     } else {
-        // ---- shift only: N = z - t I, M = I - t z, spectrum of M in [1 - |t|, 1 + |t|]
+        // ---- shift only: N = z - t I, M = I - t z, spectrum of M in [1 - |t| rho, 1 + |t| rho]
         const double Mc = 1.0 - t * zc;
         const double Nc = zc - t;
-        const double mmin = 1.0 - fabs(t), mmax = 1.0 + fabs(t);
+        const double mmin = 1.0 - fabs(t) * rho, mmax = 1.0 + fabs(t) * rho;
         const double w0 = 2.0 / (mmin + mmax);
         st->w0 = w0;
         st->ft_nj = ns_steps(mmin, mmax);

@@ -100,6 +100,9 @@ struct Engine {
     // IF(fp64) k_fp64_step; IF(digit) k_digit_prep, k_digit_mma; k_control }
     StepFlags *d_flags = nullptr;
     StepFlags h_flags{};
+    // Stream-K hand-off of split tiles in k_sym_mma: one slot and two counters per SM
+    float *d_skws = nullptr;
+    int *d_skcnt = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<uintptr_t> gkey;     // what the instantiated graph was built for
@@ -514,6 +517,9 @@ int eng_init(fe_ctx *ctx, Engine &e, cudaStream_t user_stream) {
     FE_CUDA(ctx, cudaMalloc(&e.d_err, sizeof(int)));
     FE_CUDA(ctx, cudaMalloc(&e.d_flags, sizeof(StepFlags)));
     FE_CUDA(ctx, cudaMemset(e.d_flags, 0, sizeof(StepFlags)));
+    FE_CUDA(ctx, cudaMalloc(&e.d_skws, sizeof(float) * kSkSlotFloats * ctx->num_sms));
+    FE_CUDA(ctx, cudaMalloc(&e.d_skcnt, sizeof(int) * 2 * ctx->num_sms));
+    FE_CUDA(ctx, cudaMemset(e.d_skcnt, 0, sizeof(int) * 2 * ctx->num_sms));
     FE_CUDA(ctx, cudaEventCreate(&e.ev0));
     FE_CUDA(ctx, cudaEventCreate(&e.ev1));
     return FE_OK;
@@ -524,6 +530,8 @@ void eng_free(Engine &e) {
     if (e.gexec) cudaGraphExecDestroy(e.gexec);
     if (e.graph) cudaGraphDestroy(e.graph);
     if (e.d_flags) cudaFree(e.d_flags);
+    if (e.d_skws) cudaFree(e.d_skws);
+    if (e.d_skcnt) cudaFree(e.d_skcnt);
     if (e.d_err) cudaFree(e.d_err);
     if (e.d_probs) cudaFree(e.d_probs);
     if (e.d_tiles) cudaFree(e.d_tiles);
@@ -551,9 +559,12 @@ int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
         hprobs[k].ldh = j.ldh;
         const bool fermi = method_of(j.p) == kMethodFermi;
         const uint32_t pr = prec_of(ctx, j.p);
+        hprobs[k].tc_tile0 = static_cast<int>(tiles.size());
+        hprobs[k].tc_ntiles = 0;
         if (pr != FE_PREC_FP64 || fermi) {
             e.any_tc = true;
             for (TileEnt t : j.slot->tiles) { t.prob = k; tiles.push_back(t); }
+            hprobs[k].tc_ntiles = static_cast<int>(j.slot->tiles.size());
         }
         if (pr == FE_PREC_FP64 && !fermi) {
             e.any_fp64 = true;
@@ -622,14 +633,15 @@ int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int 
 // tensor-core and FP64 launch is bracketed by events (4 per step).
 void eng_steps(fe_ctx *ctx, Engine &e, int np, int count, const std::vector<cudaEvent_t> *pev) {
     cudaStream_t s = e.stream;
-    const int grid_tc = std::max(1, std::min(e.ntc, ctx->num_sms));
+    const int grid_tc = ctx->num_sms;  // the kernel itself uses at most (work / largest tile) CTAs
     const int grid_64 = std::max(1, std::min(e.n64, 4 * ctx->num_sms));
     const size_t smem = mma_smem_bytes();
     const int grid_d = std::max(1, std::min(e.nD, ctx->num_sms));
     for (int it = 0; it < count; ++it) {
         if (pev) cudaEventRecord((*pev)[4 * it + 0], s);
         if (e.any_tc) {
-            k_sym_mma<<<grid_tc, kSymThreads, smem, s>>>(e.d_probs, e.d_tiles, e.ntc, e.d_err);
+            k_sym_mma<<<grid_tc, kSymThreads, smem, s>>>(e.d_probs, np, e.d_tiles, e.ntc, e.d_err, e.d_skws,
+                                                          e.d_skcnt);
             ++ctx->launches;
         }
         if (pev) cudaEventRecord((*pev)[4 * it + 1], s);
@@ -772,11 +784,12 @@ int eng_graph(fe_ctx *ctx, Engine &e, int np) {
         cudaGraph_t ib;
         FE_CUDA(ctx, add_if(ht, &ib));
         const TileEnt *tl = e.d_tiles;
-        int nt = e.ntc;
-        void *args[] = {&probs, &tl, &nt, &err};
-        FE_CUDA(ctx, add_kernel(ib, reinterpret_cast<const void *>(k_sym_mma),
-                                std::max(1, std::min(e.ntc, ctx->num_sms)), kSymThreads, mma_smem_bytes(),
-                                args, nullptr, &kn));
+        int nt = e.ntc, npp = np;
+        float *skws = e.d_skws;
+        int *skcnt = e.d_skcnt;
+        void *args[] = {&probs, &npp, &tl, &nt, &err, &skws, &skcnt};
+        FE_CUDA(ctx, add_kernel(ib, reinterpret_cast<const void *>(k_sym_mma), ctx->num_sms, kSymThreads,
+                                mma_smem_bytes(), args, nullptr, &kn));
     }
     if (e.any_fp64) {
         cudaGraph_t ib;
@@ -821,6 +834,7 @@ int run_problems(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) {
     int rc = eng_upload(ctx, e, jobs);
     if (rc != FE_OK) return rc;
     FE_CUDA(ctx, cudaMemsetAsync(e.d_err, 0, sizeof(int), s));
+    FE_CUDA(ctx, cudaMemsetAsync(e.d_skcnt, 0, sizeof(int) * 2 * ctx->num_sms, s));
     FE_CUDA(ctx, cudaEventRecord(e.ev0, s));
     rc = eng_setup(ctx, e, jobs, 0, np);
     if (rc != FE_OK) return rc;
@@ -1010,6 +1024,7 @@ void serve_loop(fe_ctx *ctx) {
         int herr = 0;
         if (rc == FE_OK) {
             cudaMemsetAsync(e.d_err, 0, sizeof(int), e.stream);
+            cudaMemsetAsync(e.d_skcnt, 0, sizeof(int) * 2 * ctx->num_sms, e.stream);
             eng_steps(ctx, e, np, kServeSteps, nullptr);
             for (int k = 0; k < np; ++k)
                 cudaMemcpyAsync(&e.h_done[k], &all[k]->slot->st->done, sizeof(int),
@@ -1364,14 +1379,17 @@ extern "C" int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t l
     if (rc == FE_OK) rc = ensure_dev(ctx, &eg.d_tiles, &eg.tiles_cap, s->tiles.size());
     if (rc != FE_OK) { release_slot(ctx, s); return rc; }
     MmaProb hp = s->hp;
+    hp.tc_tile0 = 0;
+    hp.tc_ntiles = static_cast<int>(s->tiles.size());
     cudaMemcpyAsync(eg.d_probs, &hp, sizeof(MmaProb), cudaMemcpyHostToDevice, q);
     cudaMemcpyAsync(eg.d_tiles, s->tiles.data(), sizeof(TileEnt) * s->tiles.size(),
                     cudaMemcpyHostToDevice, q);
+    cudaMemsetAsync(eg.d_skcnt, 0, sizeof(int) * 2 * ctx->num_sms, q);
     cudaMemcpyAsync(s->st, &st0, sizeof(SolveState), cudaMemcpyHostToDevice, q);
     cudaMemsetAsync(eg.d_err, 0, sizeof(int), q);
     const int nt = static_cast<int>(s->tiles.size());
-    k_sym_mma<<<std::min(nt, ctx->num_sms), kSymThreads, mma_smem_bytes(), q>>>(
-        eg.d_probs, eg.d_tiles, nt, eg.d_err);
+    k_sym_mma<<<ctx->num_sms, kSymThreads, mma_smem_bytes(), q>>>(eg.d_probs, 1, eg.d_tiles, nt, eg.d_err,
+                                                                   eg.d_skws, eg.d_skcnt);
     ctx->launches += 2;
     cudaMemcpy2DAsync(C, sizeof(float) * ldc, s->Y, sizeof(float) * s->ldy, sizeof(float) * n, n,
                       cudaMemcpyDeviceToDevice, q);

@@ -62,6 +62,7 @@ enum DevErr : int {
     kErrTimeoutEmpty = 2,   // smem stage never released
     kErrTimeoutTmem = 3,    // accumulator hand-off never happened
     kErrBadInput = 4,
+    kErrTimeoutPartner = 5, // the partial sums of a split tile never arrived
 };
 
 // bounded waits give up after this many nanoseconds of wall time

@@ -35,6 +35,7 @@ struct MmaProb {
     double *part;                    // per-tile partial slots (kPartStride doubles each)
     int n, ldy, lds, ntiles;
     int ntiles64, pad1;
+    int tc_tile0, tc_ntiles;         // this problem's range in the launch's tensor-core tile list
     float *Y;                        // FP32 master of the zero-temperature iterate
     double *Xd[2];                   // FP64 buffers (FP64 phase / finite-T output), ld ldx
     int ldx, pad0;
@@ -66,8 +67,12 @@ struct Tile64 {
     int slot;
 };
 
-__global__ void k_sym_mma(const MmaProb *__restrict__ probs, const TileEnt *__restrict__ tiles,
-                          int ntiles, int *err);
+// Split-FP16 symmetric products, Stream-K scheduled over the tiles of all
+// active problems.  ws: kSkSlotFloats floats per participating CTA (partial
+// sums of a split tile); cnt: 2 ints per CTA, zero between launches.
+__global__ void k_sym_mma(const MmaProb *__restrict__ probs, int nprobs,
+                          const TileEnt *__restrict__ tiles, int ntiles, int *err, float *ws, int *cnt);
+constexpr size_t kSkSlotFloats = static_cast<size_t>(kTileM) * kTileN;  // 128 KiB per slot
 size_t mma_smem_bytes();
 
 struct RowInfo {

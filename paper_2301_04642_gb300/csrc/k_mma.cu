@@ -59,6 +59,7 @@ struct MmaSmemTail {
     int abort_flag;
     double red[kEpiWarps][4];
     int vote[kEpiWarps];
+    int sk_ticket, sk_ok;             // split-tile hand-off (drain warp 0 writes, all read)
     double stage[kEpiWarps][32 * 9];  // per-warp staging of 32 rows x 8 columns (direct writes)
 };
 
@@ -106,11 +107,106 @@ __device__ __forceinline__ void put_slices(const MatSlot &m, size_t at, float ys
     m.sl[1][at] = __float2half_rn(ys - __half2float(hh));
 }
 
+// ---- Stream-K schedule.  The launch's work is the sequence, over the active
+// problems in table order, of their tiles, each worth `units` = its 64-wide K
+// chunks (1 for an epilogue-only step).  The participating CTAs take equal
+// contiguous ranges of it, so tile boundaries (and store phases) fall at
+// different times in different CTAs and the last wave is not left half
+// empty.  At most G = W / (largest tile) CTAs take part, so a tile spans at
+// most two ranges: a head segment at the end of one CTA's range and a tail
+// segment at the start of the next one's.  Every role of a CTA walks the same
+// segments.
+struct Seg {
+    int tile;   // index into the launch's tile list
+    int k0;     // first chunk
+    int nch;    // chunks (0 for an epilogue-only step)
+    bool split; // the tile is shared with a neighbouring CTA
+    bool head;  // this CTA has its first chunks (else its last)
+};
+
+__device__ __forceinline__ int tile_units(const MmaProb &pr) {
+    const int nk = step_chunks(pr.st, pr.n);
+    return nk > 0 ? nk : 1;
+}
+
+struct SegIter {
+    const MmaProb *probs;
+    int nprobs;
+    long long g, end;
+
+    __device__ void init(const MmaProb *p, int np) {
+        probs = p;
+        nprobs = np;
+        long long W = 0;
+        int wmax = 1;
+        for (int q = 0; q < np; ++q) {
+            const MmaProb &pr = p[q];
+            if (pr.tc_ntiles == 0 || !tile_active(pr.st)) continue;
+            const int w = tile_units(pr);
+            W += static_cast<long long>(pr.tc_ntiles) * w;
+            wmax = w > wmax ? w : wmax;
+        }
+        long long G = W / wmax;
+        if (G > static_cast<long long>(gridDim.x)) G = gridDim.x;
+        if (G < 1) G = 1;
+        const long long b = blockIdx.x;
+        if (W == 0 || b >= G) {
+            g = end = 0;
+        } else {
+            g = W * b / G;
+            end = W * (b + 1) / G;
+        }
+    }
+
+    __device__ bool next(Seg &sg) {
+        if (g >= end) return false;
+        long long r = g;
+        for (int q = 0; q < nprobs; ++q) {
+            const MmaProb &pr = probs[q];
+            if (pr.tc_ntiles == 0 || !tile_active(pr.st)) continue;
+            const int w = tile_units(pr);
+            const long long span = static_cast<long long>(pr.tc_ntiles) * w;
+            if (r < span) {
+                const int k = static_cast<int>(r % w);
+                const long long left = end - g;
+                const int k1 = (left < w - k) ? k + static_cast<int>(left) : w;
+                sg.tile = pr.tc_tile0 + static_cast<int>(r / w);
+                sg.k0 = k;
+                sg.nch = (step_chunks(pr.st, pr.n) > 0) ? k1 - k : 0;
+                sg.split = (k > 0) || (k1 < w);
+                sg.head = (k == 0);
+                g += k1 - k;
+                return true;
+            }
+            r -= span;
+        }
+        g = end;
+        return false;
+    }
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait for a flag that a running CTA sets; false after kWaitTimeoutNs.
+__device__ __forceinline__ bool flag_wait_bounded(const int *f) {
+    if (ld_acquire(f)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!ld_acquire(f)) {
+        if (globaltimer() - t0 > kWaitTimeoutNs) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(kSymThreads, 1)
-    k_sym_mma(const MmaProb *__restrict__ probs, const TileEnt *__restrict__ tiles, int ntiles,
-              int *err) {
+    k_sym_mma(const MmaProb *__restrict__ probs, int nprobs, const TileEnt *__restrict__ tiles,
+              int ntiles, int *err, float *ws, int *cnt) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t base_u32 = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
@@ -146,17 +242,19 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         uint32_t last_phase[kStages];
         bool issued[kStages];
         for (int s = 0; s < kStages; ++s) { issued[s] = false; last_phase[s] = 0; }
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const TileEnt te = tiles[t];
+        SegIter it;
+        it.init(probs, nprobs);
+        Seg sg;
+        while (ok && it.next(sg)) {
+            if (sg.tile >= ntiles) break;
+            const TileEnt te = tiles[sg.tile];
             const MmaProb &pr = probs[te.prob];
-            if (!tile_active(pr.st)) continue;
             const SolveState *st = pr.st;
             const int S = (step_kind(st) == kTcSplit) ? 2 : 1;
             const MatSlot &ma = pr.mats[st->op.A];
             const MatSlot &mb = pr.mats[st->op.B];
-            const int nk = step_chunks(st, pr.n);
             const uint32_t bytes = static_cast<uint32_t>(S * (kSliceABytes + kSliceBBytes));
-            for (int kc = 0; kc < nk; ++kc) {
+            for (int kc = sg.k0; kc < sg.k0 + sg.nch; ++kc) {
                 bool got = true;
                 if (lane == 0) got = mbar_wait_bounded(&tail->empty[stage], phase ^ 1u);
                 got = __shfl_sync(0xffffffffu, got, 0);
@@ -196,14 +294,16 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         bool ok = true;
         bool any_commit = false;
         constexpr uint32_t idesc = idesc_f16(kTileM, kTileN, 0);
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const TileEnt te = tiles[t];
+        SegIter it;
+        it.init(probs, nprobs);
+        Seg sg;
+        while (ok && it.next(sg)) {
+            if (sg.tile >= ntiles) break;
+            const TileEnt te = tiles[sg.tile];
             const MmaProb &pr = probs[te.prob];
-            if (!tile_active(pr.st)) continue;
             const SolveState *st = pr.st;
             const int S = (step_kind(st) == kTcSplit) ? 2 : 1;
-            const int nk = step_chunks(st, pr.n);
-            for (int kc = 0; kc < nk; ++kc) {
+            for (int kc = sg.k0; kc < sg.k0 + sg.nch; ++kc) {
                 const uint32_t buf = chunk & 1u;
                 const uint32_t cph = (chunk >> 1) & 1u;
                 bool got = true;
@@ -273,17 +373,19 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         const int row_local = q * 32 + lane;
         uint32_t chunk = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const TileEnt te = tiles[t];
+        SegIter it;
+        it.init(probs, nprobs);
+        Seg sg;
+        while (ok && it.next(sg)) {
+            if (sg.tile >= ntiles) break;
+            const TileEnt te = tiles[sg.tile];
             const MmaProb &pr = probs[te.prob];
-            if (!tile_active(pr.st)) continue;
             const SolveState *st = pr.st;
             const int n = pr.n;
-            const int nk = step_chunks(st, n);
             float acc[128];
 #pragma unroll
             for (int c = 0; c < 128; ++c) acc[c] = 0.0f;
-            for (int kc = 0; kc < nk; ++kc) {
+            for (int kc = sg.k0; kc < sg.k0 + sg.nch; ++kc) {
                 const uint32_t buf = chunk & 1u;
                 const uint32_t cph = (chunk >> 1) & 1u;
                 bool got = mbar_wait_bounded(&tail->cfull[buf], cph);
@@ -318,6 +420,53 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             if (!all_ok) {
                 ok = false;
                 break;
+            }
+
+            // ---- a tile shared with a neighbouring CTA: the first to arrive
+            // hands its partial sums over through global memory, the second
+            // adds them (one commutative addition: the same result whoever is
+            // second) and runs the epilogue.  The second waits only for a CTA
+            // that is already writing, so the wait is short and bounded.
+            if (sg.split) {
+                const int slot = sg.head ? static_cast<int>(blockIdx.x) : static_cast<int>(blockIdx.x) - 1;
+                float4 *wsp = reinterpret_cast<float4 *>(ws + static_cast<size_t>(slot) * kSkSlotFloats +
+                                                         (static_cast<size_t>(ew) * 32 + lane) * 128);
+                if (ew == 0 && lane == 0) tail->sk_ticket = atomicAdd(&cnt[2 * slot], 1);
+                epi_bar();
+                const int ticket = tail->sk_ticket;
+                epi_bar();
+                if (ticket == 0) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        wsp[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+                    __threadfence();
+                    epi_bar();
+                    if (ew == 0 && lane == 0) atomicExch(&cnt[2 * slot + 1], 1);
+                    continue;
+                }
+                if (ew == 0 && lane == 0) tail->sk_ok = flag_wait_bounded(&cnt[2 * slot + 1]) ? 1 : 0;
+                epi_bar();
+                const bool got = tail->sk_ok != 0;
+                epi_bar();
+                if (!got) {
+                    if (ew == 0 && lane == 0) record_error(err, kErrTimeoutPartner);
+                    ok = false;
+                    break;
+                }
+                __threadfence();
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const float4 p4 = __ldcg(wsp + c);
+                    acc[4 * c] += p4.x;
+                    acc[4 * c + 1] += p4.y;
+                    acc[4 * c + 2] += p4.z;
+                    acc[4 * c + 3] += p4.w;
+                }
+                epi_bar();
+                if (ew == 0 && lane == 0) {
+                    atomicExch(&cnt[2 * slot], 0);
+                    atomicExch(&cnt[2 * slot + 1], 0);
+                }
             }
 
             // ---- store phase for block J = 2 Jp + h

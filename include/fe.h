@@ -107,8 +107,9 @@ typedef struct {
     double idem_fro;        /* ||X^2 - X||_F of the last product's input, measured in its
                                epilogue (0 T); D, its output, is closer to idempotent */
     double mu;              /* chemical potential (finite T); NaN at zero T          */
-    double eps_min;         /* Gershgorin lower bound of Hp                          */
-    double eps_max;         /* Gershgorin upper bound of Hp                          */
+    double eps_min;         /* lower spectral bound the expansion used: a Lanczos
+                               estimate inside the Gershgorin interval (or Gershgorin) */
+    double eps_max;         /* upper spectral bound, likewise                        */
     double ms;              /* fe_solve / fe_solve_batch: device time of the solve
                                (CUDA events); fe_poll: submit-to-done latency, ms   */
 } fe_result;

@@ -64,6 +64,7 @@ struct Slot {
     float *Y = nullptr;
     double *Xd[2] = {};
     double *Dtmp = nullptr;
+    double *lzv = nullptr;  // Lanczos vectors (3 n doubles)
     double *part = nullptr;
     SolveState *st = nullptr;
     RowInfo *rowinfo = nullptr;
@@ -115,6 +116,7 @@ struct Req {
     std::vector<double> hbuf;       // host copy of Hp while no slot is free
     Slot *slot = nullptr;
     bool staged = false;            // Hp already copied into slot->Hcopy
+    bool gershgorin = false;        // the spectral-bound estimate proved too tight: use Gershgorin
     bool done = false;
     fe_result res{};
     std::chrono::steady_clock::time_point t_submit;
@@ -218,6 +220,7 @@ size_t slot_bytes(int n, int method, int *ldy, int *lds, int *ldx, size_t *npart
     add(8 * nn * (*ldx));                            // Xd[0]
     add(8 * nn * (*ldx));                            // Xd[1]
     add(8 * nn * nn);                                // Dtmp
+    add(8 * 3 * nn);                                 // Lanczos vectors
     if (method == kMethodSp2)
         for (int a = 0; a < kDigits; ++a) add(2 * nn * (*lds));  // digits of X/4
     add(8 * kPartStride * (*nparts));                // partials
@@ -311,6 +314,7 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
     s->Xd[0] = reinterpret_cast<double *>(take(8 * nn * ldx));
     s->Xd[1] = reinterpret_cast<double *>(take(8 * nn * ldx));
     s->Dtmp = reinterpret_cast<double *>(take(8 * nn * nn));
+    s->lzv = reinterpret_cast<double *>(take(8 * 3 * nn));
     __half *digs[kDigits] = {};
     if (method == kMethodSp2)
         for (int a = 0; a < kDigits; ++a) digs[a] = reinterpret_cast<__half *>(take(2 * nn * lds));
@@ -367,6 +371,7 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
     s->hp.ntiles = static_cast<int>(s->tiles.size());
     s->hp.ntiles64 = static_cast<int>(s->tiles64.size());
     s->hp.ntilesD = static_cast<int>(s->tilesD.size());
+    s->hp.lzv = s->lzv;
     s->hp.Xd[0] = s->Xd[0];
     s->hp.Xd[1] = s->Xd[1];
     s->hp.ldx = ldx;
@@ -477,6 +482,7 @@ struct Job {
     int64_t ldh = 0;
     const double *stage = nullptr;  // host Hp copied into slot->Hcopy at set-up, or null
     int64_t ldstage = 0;
+    bool lanczos = true;            // estimate the spectral bounds (else Gershgorin)
 };
 
 Job make_job(const fe_problem *p, Slot *s) {
@@ -614,13 +620,24 @@ int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int 
                                            sizeof(double) * j.ldstage, sizeof(double) * n, n,
                                            cudaMemcpyHostToDevice, s));
         init_state(ctx, j.p, &e.h_states[k]);
+        e.h_states[k].lz_on = j.lanczos ? 1 : 0;
         FE_CUDA(ctx, cudaMemcpyAsync(j.slot->st, &e.h_states[k], sizeof(SolveState),
                                      cudaMemcpyHostToDevice, s));
         FE_CUDA(ctx, cudaMemsetAsync(j.slot->bad, 0, sizeof(int), s));
         k_bounds_rows<<<ceil_div(n, 8), 256, 0, s>>>(e.d_probs, k, j.slot->rowinfo, j.slot->bad);
         k_bounds_reduce<<<1, 1024, 0, s>>>(e.d_probs, k, j.slot->rowinfo, j.slot->bad);
+        ctx->launches += 2;
+        if (j.lanczos) {
+            k_lanczos_start<<<1, 1024, 0, s>>>(e.d_probs, k);
+            for (int it = 0; it < kLanczosSteps; ++it) {
+                k_lanczos_matvec<<<kLzBlocks, 256, 0, s>>>(e.d_probs, k);
+                k_lanczos_update<<<1, 1024, 0, s>>>(e.d_probs, k, it);
+            }
+            k_bounds_finish<<<1, 32, 0, s>>>(e.d_probs, k);
+            ctx->launches += 2 + 2 * kLanczosSteps;
+        }
         k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
-        ctx->launches += 3;
+        ctx->launches += 1;
     }
     k_control<<<k1 - k0, 256, 0, s>>>(e.d_probs + k0, k1 - k0, nullptr, 0, 0, 0, 0, 0u);
     ++ctx->launches;
@@ -827,7 +844,7 @@ int eng_graph(fe_ctx *ctx, Engine &e, int np) {
 }
 
 // Run validated problems on acquired slots to completion (blocking calls).
-int run_problems(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) {
+int run_problems_once(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) {
     Engine &e = ctx->eng;
     const int np = static_cast<int>(jobs.size());
     cudaStream_t s = e.stream;
@@ -918,6 +935,33 @@ int run_problems(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) {
     return first_bad;
 }
 
+// As run_problems_once; a problem whose spectral-bound estimate proved too
+// tight (an eigenvalue of X left [0, 1]) is solved again from the Gershgorin
+// bounds, which always contain the spectrum.
+int run_problems(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) {
+    int rc = run_problems_once(ctx, jobs, rs);
+    std::vector<Job> again;
+    std::vector<int> where;
+    for (size_t k = 0; k < jobs.size(); ++k)
+        if (rs[k].status == kStatusEscaped) {
+            Job j = jobs[k];
+            j.lanczos = false;
+            again.push_back(j);
+            where.push_back(static_cast<int>(k));
+        }
+    if (again.empty()) return rc;
+    std::vector<fe_result> rr(again.size());
+    run_problems_once(ctx, again, rr.data());
+    rc = FE_OK;
+    for (size_t q = 0; q < again.size(); ++q) {
+        if (rr[q].status == kStatusEscaped) rr[q].status = FE_ENOTCONV;
+        rs[where[q]] = rr[q];
+    }
+    for (size_t k = 0; k < jobs.size(); ++k)
+        if (rs[k].status != FE_OK && rc == FE_OK) rc = rs[k].status;
+    return rc;
+}
+
 // ---------------------------------------------------------------- serving
 // Continuous batching behind fe_submit / fe_poll.  One worker thread owns a
 // second engine (its own stream).  Each tick it starts the waiting requests
@@ -963,6 +1007,7 @@ Job job_of(Req *r) {
         j.stage = r->hbuf.data();
         j.ldstage = r->p.n;
     }
+    j.lanczos = !r->gershgorin;
     return j;
 }
 
@@ -1054,14 +1099,27 @@ void serve_loop(fe_ctx *ctx) {
             const cudaError_t ce = cudaStreamSynchronize(e.stream);
             if (ce != cudaSuccess) rc = cuda_fail(ctx, ce, "serving finish");
         }
+        std::vector<Req *> redo;
         for (int k : fin) {
             Req *r = all[k];
             fe_result res;
             fill_result(e.h_states[k], 0, 0.0, res);
             if (rc != FE_OK) res.status = rc;
+            if (res.status == kStatusEscaped && !r->gershgorin) {
+                // start again from the Gershgorin bounds (Hp is in the slot)
+                r->gershgorin = true;
+                r->staged = true;
+                redo.push_back(r);
+                continue;
+            }
+            if (res.status == kStatusEscaped) res.status = FE_ENOTCONV;
             release_slot(ctx, r->slot);
             r->slot = nullptr;
             publish(ctx, r, res);
+        }
+        if (!redo.empty()) {
+            std::lock_guard<std::mutex> lk(ctx->qmu);
+            for (Req *r : redo) ctx->waiting.push_front(r);
         }
         running.swap(next);
         if (!fin.empty() && !running.empty()) {

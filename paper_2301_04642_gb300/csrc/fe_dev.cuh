@@ -69,6 +69,8 @@ enum DevErr : int {
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;
 
 constexpr int kHistRows = 160;  // per-step history kept in the solve state
+constexpr int kLanczosSteps = 16;   // Lanczos steps of the spectral-bound estimate
+constexpr int kStatusEscaped = -100;  // internal: an eigenvalue left [0, 1] (bounds too tight)
 constexpr int kHistCols = 6;
 
 // ---------------------------------------------------------------- state
@@ -121,9 +123,14 @@ struct SolveState {
     float scl[6];     // slice scale s of each slot's FP16 slices (slices hold s A~)
     double ft_t, w0;  // tanh of the current shift; Newton-Schulz start
     double tr_d0, tr_q;  // traces of D0 = (I - z)/2 and Q = (I - z^2)/4 at the end
-    // Gershgorin bounds and Hp statistics (written by the bounds kernel)
+    // spectral bounds used by the expansion (Lanczos estimate within the
+    // Gershgorin interval, or Gershgorin itself) and Hp statistics
     double emin, emax, trH, hmax;
     int bad_input;
+    int lz_on;            // 1: estimate the bounds with Lanczos (host sets it)
+    int lz_k, lz_pad;     // Lanczos steps taken
+    double gersh_lo, gersh_hi;
+    double lz_a[kLanczosSteps], lz_b[kLanczosSteps + 1];
     // iterate X = c I + Y, or X = Xd[xcur] (FP64) once in the FP64 phase
     double c;
     float s_cur;        // slice scale of the current slice set

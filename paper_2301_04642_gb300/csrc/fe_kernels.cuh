@@ -36,6 +36,7 @@ struct MmaProb {
     int n, ldy, lds, ntiles;
     int ntiles64, pad1;
     int tc_tile0, tc_ntiles;         // this problem's range in the launch's tensor-core tile list
+    double *lzv;                     // Lanczos vectors: v_prev, v, w (n doubles each)
     float *Y;                        // FP32 master of the zero-temperature iterate
     double *Xd[2];                   // FP64 buffers (FP64 phase / finite-T output), ld ldx
     int ldx, pad0;
@@ -81,9 +82,60 @@ struct RowInfo {
 
 // Gershgorin row pass: one warp per row.
 __global__ void k_bounds_rows(const MmaProb *probs, int prob, RowInfo *rowinfo, int *bad);
-// Deterministic reduction of the row info into the state (one block).
+// Deterministic reduction of the row info into the state (one block); with
+// the Lanczos estimate off it also prepares X0 from the Gershgorin bounds.
 __global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *rowinfo,
                                 const int *bad);
+// Spectral-bound estimate by kLanczosSteps Lanczos steps (FP64): start vector,
+// then per step w = H v (kLzBlocks blocks, partial dot products) and the
+// three-term update (one block); k_bounds_finish turns the tridiagonal into
+// bounds and prepares X0.
+constexpr int kLzBlocks = 304;
+__global__ void k_lanczos_start(const MmaProb *probs, int prob);
+__global__ void k_lanczos_matvec(const MmaProb *probs, int prob);
+__global__ void k_lanczos_update(const MmaProb *probs, int prob, int j);
+__global__ void k_bounds_finish(const MmaProb *probs, int prob);
+// X0 = (hi I - Hp)/(hi - lo) stored as c0 I + Y0 (its slice scale from a bound
+// on |Y0_ij|), or for finite temperature the parameters of z0.
+__device__ __forceinline__ void setup_from_bounds(const MmaProb &pr, SolveState *st, double lo, double hi) {
+    const int n = pr.n;
+    st->emin = lo;
+    st->emax = hi;
+    const double trH = st->trH;
+    double w = hi - lo;
+    if (!(w > 0.0)) w = 1.0;  // Hp = a I: X0 is constant; the expansion will stall
+    const double c0 = (hi - trH / n) / w;
+    // |Y0_ij| <= max|Hp_ij| / w + |eps_max / w - c0|
+    const double bound = st->hmax / w + fabs(hi / w - c0);
+    int e;
+    frexp(bound > 0.0 ? bound : 1.0, &e);  // bound < 2^e
+    st->c = c0;
+    st->s_cur = static_cast<float>(ldexp(1.0, 14 - e));
+    st->cur = 0;
+    st->xcur = 0;
+    st->x_fp64 = (st->prec == kPrecFp64) ? 1 : 0;
+    if (st->method == kMethodFermi) {
+        // z0 = (beta0 / 2)(H - mu0 I) with mu0 = tr H / n and the number of
+        // doublings m chosen so that |z0| <= t0 = 1e-3 on the bound interval:
+        // then z0 = tanh(beta0 (H - mu0)/2) to a relative 1e-7/3 in the
+        // logit, an error the doublings carry over unchanged.
+        const double mu0 = trH / n;
+        const double rad = fmax(fabs(lo - mu0), fabs(hi - mu0));
+        const double beta = 1.0 / st->kT;
+        const double t0 = 1e-3;
+        int m = 0;
+        if (beta * rad / 2.0 > t0) m = static_cast<int>(ceil(log2(beta * rad / (2.0 * t0))));
+        st->beta = beta;
+        st->ft_m = m;
+        st->beta0 = ldexp(beta, -m);
+        st->mu_t = mu0;
+        st->sc[kMatZ] = 0.0;
+        int ez;
+        frexp(fmax(st->beta0 * rad / 2.0, 1e-300) * 1.0001, &ez);
+        st->scl[kMatZ] = static_cast<float>(ldexp(1.0, 14 - ez));
+    }
+}
+
 // Zero temperature: X0 -> (c, Y0) and slices.  Finite temperature: z0.  Per-block partials.
 __global__ void k_init_x0(const MmaProb *probs, int prob);
 // Step control for every problem (one block per problem).

@@ -129,6 +129,14 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
     // ---- precision schedule and stopping rules
     bool done = false;
     int phase = st->phase;
+    // With every eigenvalue of X in [0, 1], t2 <= t1 and 0 <= t1 <= n.  An
+    // eigenvalue outside the spectral-bound estimate can end on the wrong side
+    // only after leaving [-0.37, 1.37], where x (x - 1) > 0.5: stop, and the
+    // host solves again from the Gershgorin bounds.
+    if (!(t2 <= t1 + 0.5) || t1 < -0.5 || t1 > nn + 0.5) {
+        st->status = st->lz_on ? kStatusEscaped : -3;  // -3: FE_ENOTCONV
+        done = true;
+    }
     if (phase == kPhaseSingle && reltr < 5e-4) phase = kPhaseSplit;  // the paper's switch point
     if (phase == kPhaseSplit && prev_kind == kTcSplit) {
         // The split products carry ~22 bits and the FP32 master 24, so the
@@ -188,16 +196,19 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
         sq = !st->sq;
         // Exact trace: the branch output F(X) has trace t2 (X^2) or 2 t1 - t2
         // (2X - X^2); adding gamma (X - X^2), of trace t1 - t2, lands tr X' on
-        // N_e.  gamma moves eigenvalue x by gamma x (1 - x), at most ~2
-        // ||X_prev^2 - X_prev||_F |gamma|; it is applied only when a trace
-        // error remains and that move stays within a few times the error.
+        // N_e.  gamma moves eigenvalue x by gamma x (1 - x); this input's
+        // deviations are first order (one side of the pair is not squared
+        // yet), so the move is at most |gamma| 2 ||X_prev^2 - X_prev||_F in
+        // Frobenius norm.  It is applied only while that stays within the
+        // idempotency budget (2e-9); otherwise the next product's branch
+        // squares what is left and takes the trace with it.
         const double trF = sq ? t2 : 2.0 * t1 - t2;
         const double dtr = ne - trF;
         const double dev = t1 - t2;
         if (fabs(dtr) > 5e-11 && fabs(dev) > 1e-14 * nes) {
             const double g = dtr / dev;
             const double max_move = fabs(g) * 2.0 * st->fro_hist[0];
-            if (fabs(g) <= 0.5 && max_move <= fmax(4.0 * fabs(dtr), 1e-10)) st->gamma = g;
+            if (fabs(g) <= 0.5 && max_move <= 2e-9) st->gamma = g;
         }
     }
     st->sq = sq;

@@ -1,0 +1,217 @@
+// Spectral-bound estimates for the expansion (Sec. II-C: the polynomial
+// expansions need estimates eps_1, eps_N of the spectral bounds, and the
+// number of products grows with the width they span).
+//
+// Gershgorin discs always contain the spectrum but, for a dense rotated Hp,
+// span ~20-50x its true width, which costs SP2 about 2 log2 of that ratio in
+// extra products (and the finite-temperature recursion extra doublings).
+// Here kLanczosSteps steps of the Lanczos recurrence in FP64, from a fixed
+// pseudo-random unit vector, give Ritz values theta_min, theta_max inside the
+// spectrum; the bounds are
+//     theta -/+ (2 |beta_k s_k| + 0.05 (theta_max - theta_min)),
+// where |beta_k s_k| is the residual of the extreme Ritz pair (s the unit
+// eigenvector of the tridiagonal T), clipped to the Gershgorin interval.
+// They are estimates, not guarantees: the zero-temperature control kernel
+// watches sum x^2 - sum x, which turns positive by more than 0.5 only if an
+// eigenvalue has left [-0.37, 1.37] (the only way one can end on the wrong
+// side), and the host then re-runs that problem from the Gershgorin bounds.
+//
+// No reorthogonalisation: loss of orthogonality only repeats converged Ritz
+// values, which cannot move the extreme ones outward.
+#include <cfloat>
+
+#include "fe_dev.cuh"
+#include "fe_kernels.cuh"
+
+namespace fe {
+
+namespace {
+
+// SplitMix64 finaliser: a fixed, well-mixed 64-bit value per index
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double block_sum_1024(double v, double *sh) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) sh[t] += sh[t + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// number of eigenvalues of the tridiagonal (a, b) below x (Sturm sequence)
+__device__ int sturm_count(const double *a, const double *b, int k, double x) {
+    int c = 0;
+    double q = a[0] - x;
+    if (q < 0.0) ++c;
+    for (int i = 1; i < k; ++i) {
+        if (q == 0.0) q = 1e-300;
+        q = a[i] - x - b[i] * b[i] / q;
+        if (q < 0.0) ++c;
+    }
+    return c;
+}
+
+// eigenvalue number `idx` (0-based, ascending) of T by bisection in [lo, hi]
+__device__ double tri_eig(const double *a, const double *b, int k, int idx, double lo, double hi) {
+    for (int it = 0; it < 200 && hi - lo > 1e-13 * fmax(1.0, fabs(lo) + fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(a, b, k, mid) > idx) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// |last component| of the unit eigenvector of T for eigenvalue th (forward
+// three-term recurrence, rescaled to stay finite)
+__device__ double tri_last_comp(const double *a, const double *b, int k, double th) {
+    double s_prev = 0.0, s = 1.0, norm2 = 1.0;
+    for (int i = 0; i + 1 < k; ++i) {
+        // (a_i - th) s_i + b_i s_{i-1} + b_{i+1} s_{i+1} = 0
+        const double bn = b[i + 1];
+        const double s_next = (bn != 0.0) ? -((a[i] - th) * s + b[i] * s_prev) / bn : 0.0;
+        s_prev = s;
+        s = s_next;
+        norm2 += s * s;
+        if (norm2 > 1e200) {
+            const double r = 1e-100;
+            s *= r;
+            s_prev *= r;
+            norm2 *= r * r;
+        }
+    }
+    return fabs(s) / sqrt(norm2);
+}
+
+}  // namespace
+
+// v = fixed pseudo-random unit vector, v_prev = 0 (one block of 1024 threads)
+__global__ void k_lanczos_start(const MmaProb *probs, int prob) {
+    const MmaProb &pr = probs[prob];
+    SolveState *st = pr.st;
+    const int n = pr.n;
+    double *vp = pr.lzv, *v = pr.lzv + n;
+    __shared__ double sh[1024];
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = static_cast<double>(mix64(0xF00Dull + static_cast<uint64_t>(i)) >> 11) *
+                             (2.0 / 9007199254740992.0) - 1.0;  // uniform in [-1, 1)
+        v[i] = x;
+        vp[i] = 0.0;
+        ss += x * x;
+    }
+    const double nrm = sqrt(block_sum_1024(ss, sh));
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] *= inv;
+    if (threadIdx.x == 0) {
+        st->lz_k = 0;
+        st->lz_b[0] = 0.0;
+    }
+}
+
+// w = H v, one warp per row; per-block partial of w . v in the partial slots
+__global__ void k_lanczos_matvec(const MmaProb *probs, int prob) {
+    const MmaProb &pr = probs[prob];
+    const SolveState *st = pr.st;
+    const int n = pr.n;
+    if (st->lz_k < 0) return;  // the recurrence stopped early
+    const double *v = pr.lzv + n;
+    double *w = pr.lzv + 2 * static_cast<size_t>(n);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double part = 0.0;
+    for (int row = blockIdx.x * 8 + wid; row < n; row += gridDim.x * 8) {
+        const double *h = pr.H + static_cast<size_t>(row) * pr.ldh;
+        // four independent partial sums keep four row loads in flight per lane
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int j = lane;
+        for (; j + 96 < n; j += 128) {
+            s0 = fma(h[j], v[j], s0);
+            s1 = fma(h[j + 32], v[j + 32], s1);
+            s2 = fma(h[j + 64], v[j + 64], s2);
+            s3 = fma(h[j + 96], v[j + 96], s3);
+        }
+        for (; j < n; j += 32) s0 = fma(h[j], v[j], s0);
+        double s = warp_sum((s0 + s1) + (s2 + s3));
+        if (lane == 0) {
+            w[row] = s;
+            part = fma(s, v[row], part);
+        }
+    }
+    __shared__ double red[8];
+    if (lane == 0) red[wid] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int k = 0; k < 8; ++k) a += red[k];
+        pr.part[static_cast<size_t>(blockIdx.x) * kPartStride] = a;
+    }
+}
+
+// alpha_j = w . v; w' = w - alpha_j v - beta_j v_prev; beta_{j+1} = ||w'||;
+// v_prev <- v, v <- w' / beta_{j+1} (one block of 1024 threads)
+__global__ void k_lanczos_update(const MmaProb *probs, int prob, int j) {
+    const MmaProb &pr = probs[prob];
+    SolveState *st = pr.st;
+    const int n = pr.n;
+    if (st->lz_k < 0) return;
+    double *vp = pr.lzv, *v = pr.lzv + n, *w = pr.lzv + 2 * static_cast<size_t>(n);
+    __shared__ double sh[1024];
+    double a = 0.0;
+    for (int b = threadIdx.x; b < kLzBlocks; b += blockDim.x) a += pr.part[static_cast<size_t>(b) * kPartStride];
+    const double alpha = block_sum_1024(a, sh);
+    const double beta = st->lz_b[j];
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = w[i] - alpha * v[i] - beta * vp[i];
+        w[i] = x;
+        ss += x * x;
+    }
+    const double bn = sqrt(block_sum_1024(ss, sh));
+    const bool stop = !(bn > 1e-12 * fmax(fabs(alpha), 1e-300));  // invariant subspace found
+    const double inv = stop ? 0.0 : 1.0 / bn;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        vp[i] = v[i];
+        v[i] = w[i] * inv;
+    }
+    if (threadIdx.x == 0) {
+        st->lz_a[j] = alpha;
+        st->lz_b[j + 1] = stop ? 0.0 : bn;
+        st->lz_k = stop ? -(j + 1) : j + 1;  // negative: stopped after |lz_k| steps
+    }
+}
+
+// bounds from the tridiagonal, then the X0 preparation (one thread)
+__global__ void k_bounds_finish(const MmaProb *probs, int prob) {
+    const MmaProb &pr = probs[prob];
+    SolveState *st = pr.st;
+    if (threadIdx.x != 0) return;
+    const int k = st->lz_k < 0 ? -st->lz_k : st->lz_k;
+    const double glo = st->gersh_lo, ghi = st->gersh_hi;
+    double lo = glo, hi = ghi;
+    if (k >= 2) {
+        const double *a = st->lz_a, *b = st->lz_b;  // b[i] couples i-1 and i, b[k] the residual
+        const double tmin = tri_eig(a, b, k, 0, glo, ghi);
+        const double tmax = tri_eig(a, b, k, k - 1, glo, ghi);
+        const double rmin = b[k] * tri_last_comp(a, b, k, tmin);
+        const double rmax = b[k] * tri_last_comp(a, b, k, tmax);
+        const double margin = 0.05 * (tmax - tmin);
+        lo = fmax(glo, tmin - 2.0 * rmin - margin);
+        hi = fmin(ghi, tmax + 2.0 * rmax + margin);
+        if (!(hi > lo)) {
+            lo = glo;
+            hi = ghi;
+        }
+    }
+    setup_from_bounds(pr, st, lo, hi);
+}
+
+}  // namespace fe

@@ -67,44 +67,12 @@ __global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *r
         __syncthreads();
     }
     if (t == 0) {
-        const int n = pr.n;
-        st->emin = s_lo[0];
-        st->emax = s_hi[0];
+        st->gersh_lo = s_lo[0];
+        st->gersh_hi = s_hi[0];
         st->trH = s_tr[0];
         st->hmax = s_mx[0];
         st->bad_input = *bad;
-        double w = s_hi[0] - s_lo[0];
-        if (!(w > 0.0)) w = 1.0;  // Hp = a I: X0 is constant; the expansion will stall
-        const double c0 = (s_hi[0] - s_tr[0] / n) / w;
-        // |Y0_ij| <= max|Hp_ij| / w + |eps_max / w - c0|
-        const double bound = s_mx[0] / w + fabs(s_hi[0] / w - c0);
-        int e;
-        frexp(bound > 0.0 ? bound : 1.0, &e);  // bound < 2^e
-        st->c = c0;
-        st->s_cur = static_cast<float>(ldexp(1.0, 14 - e));
-        st->cur = 0;
-        st->xcur = 0;
-        st->x_fp64 = (st->prec == kPrecFp64) ? 1 : 0;
-        if (st->method == kMethodFermi) {
-            // z0 = (beta0 / 2)(H - mu0 I) with mu0 = tr H / n and the number of
-            // doublings m chosen so that |z0| <= t0 = 1e-3 on the Gershgorin
-            // interval: then z0 = tanh(beta0 (H - mu0)/2) to a relative 1e-7/3
-            // in the logit, an error the doublings carry over unchanged.
-            const double mu0 = s_tr[0] / n;
-            const double rad = fmax(fabs(s_lo[0] - mu0), fabs(s_hi[0] - mu0));
-            const double beta = 1.0 / st->kT;
-            const double t0 = 1e-3;
-            int m = 0;
-            if (beta * rad / 2.0 > t0) m = static_cast<int>(ceil(log2(beta * rad / (2.0 * t0))));
-            st->beta = beta;
-            st->ft_m = m;
-            st->beta0 = ldexp(beta, -m);
-            st->mu_t = mu0;
-            st->sc[kMatZ] = 0.0;
-            int ez;
-            frexp(fmax(st->beta0 * rad / 2.0, 1e-300) * 1.0001, &ez);
-            st->scl[kMatZ] = static_cast<float>(ldexp(1.0, 14 - ez));
-        }
+        if (!st->lz_on) setup_from_bounds(pr, st, s_lo[0], s_hi[0]);
     }
 }
 

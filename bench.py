@@ -270,6 +270,7 @@ def main():
         if dist:
             dist.barrier()
     launches = ctx.launch_count() - l0
+    phases = ctx.phase_ms()  # the last timed solve: set-up, step loop, output
     t_ms = e0.elapsed_time(e1)
     if dist:
         tt = torch.tensor([t_ms], device=dev)
@@ -357,6 +358,7 @@ def main():
                       "precision": prec, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "256 MiB buffer written before every step; working set > 129 MB L2"},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+           "phases_ms": phases,
            "effective_tflops": iters * 2.0 * n ** 3 * value / 1e12,
            "products_per_solve": iters, "iters_by_phase": r["iters_by_phase"],
            "accuracy": {"trace_err": abs(r["trace"] - p.ne)},

@@ -10,7 +10,9 @@
  *   - Sec. II-B1, Eq. (1): zero temperature by SP2, X_{k+1} = X_k^2 or
  *     2 X_k - X_k^2, the branch chosen from tr X and tr X^2 = ||X||_F^2
  *     (Sec. III-B) so that tr X -> N_e.  X_0 is Hp scaled into [0, 1] with
- *     Gershgorin bounds (Sec. II-C).
+ *     spectral bounds (Sec. II-C): a Lanczos estimate, certified to contain
+ *     the spectrum by three logistic steps (a Chebyshev T_8 filter), within
+ *     the Gershgorin interval.
  *   - Sec. III-A: relative trace change RelTr as the convergence measure and a
  *     mixed-precision schedule (cheap products far from convergence, FP64-
  *     accurate products at the end).
@@ -108,7 +110,8 @@ typedef struct {
                                epilogue (0 T); D, its output, is closer to idempotent */
     double mu;              /* chemical potential (finite T); NaN at zero T          */
     double eps_min;         /* lower spectral bound the expansion used: a Lanczos
-                               estimate inside the Gershgorin interval (or Gershgorin) */
+                               estimate widened by its certificate so that it
+                               contains the spectrum, within the Gershgorin interval */
     double eps_max;         /* upper spectral bound, likewise                        */
     double ms;              /* fe_solve / fe_solve_batch: device time of the solve
                                (CUDA events); fe_poll: submit-to-done latency, ms   */

@@ -73,6 +73,24 @@ FE_API int fe_k_digit_square(fe_ctx *ctx, const double *X, int64_t n, int64_t ld
 FE_API int fe_k_profile(fe_ctx *ctx, int enable);
 FE_API int fe_k_profile_read(fe_ctx *ctx, double *out8);
 
+/* Test hook (no counterpart in the paper): every following solve on ctx,
+ * blocking or submitted, shrinks its Lanczos estimate of the spectral bounds
+ * about the interval's centre by `factor` (1 = off, the default) before the
+ * estimate is certified.  A factor below 1 leaves eigenvalues of Hp outside
+ * the estimate; the certificate (three logistic steps X <- 4 X (I - X) from X0
+ * on the estimate, i.e. the Chebyshev polynomial T_8) must widen the bounds
+ * until they contain the spectrum again (fe_result's eps_min / eps_max are the
+ * bounds used).  Call it while no submitted solve is running.
+ * Errors: FE_EINVAL (ctx NULL, factor outside (0, 1]). */
+FE_API int fe_k_narrow_bounds(fe_ctx *ctx, double factor);
+
+/* Where the last blocking solve or batch on ctx spent its device time
+ * (measurement hook, no counterpart in the paper; CUDA events, always on).
+ * out4 (HOST): [0] ms of set-up (Hp staging, bounds, X0, first control step),
+ * [1] ms of the step loop, [2] ms of the output kernels, [3] steps the loop
+ * ran.  Zeros before the first solve. */
+FE_API int fe_k_phase_ms(fe_ctx *ctx, double *out4);
+
 /* Number of kernels this context has launched since fe_create (HOST out). */
 FE_API int fe_k_launch_count(fe_ctx *ctx, int64_t *out);
 

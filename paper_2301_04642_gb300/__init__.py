@@ -76,13 +76,15 @@ def load(build=True):
     L.fe_k_gershgorin_noalloc.argtypes = [P, i64, i64, P, P]
     L.fe_k_digit_square.argtypes = [P, P, i64, i64, P, i64]
     L.fe_k_profile.argtypes = [P, ctypes.c_int]
+    L.fe_k_narrow_bounds.argtypes = [P, dbl]
+    L.fe_k_phase_ms.argtypes = [P, ctypes.POINTER(dbl)]
     L.fe_k_profile_read.argtypes = [P, ctypes.POINTER(dbl)]
     L.fe_k_launch_count.argtypes = [P, ctypes.POINTER(i64)]
     L.fe_k_history.argtypes = [P, ctypes.c_int, ctypes.POINTER(dbl), ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int)]
     for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
                  "fe_k_gershgorin", "fe_k_gershgorin_noalloc", "fe_k_sym_square", "fe_k_digit_square",
-                 "fe_k_profile", "fe_k_profile_read",
+                 "fe_k_profile", "fe_k_profile_read", "fe_k_narrow_bounds", "fe_k_phase_ms",
                  "fe_k_launch_count", "fe_k_history"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -300,6 +302,19 @@ class Context:
         keys = ("tc_ms", "tc_launches", "fp64_ms", "fp64_launches", "solve_ms", "launches_total",
                 "tc_ms_all", "tc_launches_all")
         return dict(zip(keys, list(out)))
+
+    def narrow_bounds(self, factor):
+        """Test hook: shrink the estimated spectral bounds of later solves
+        about their centre by `factor` (1 = off)."""
+        rc = self.L.fe_k_narrow_bounds(self.h, float(factor))
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+
+    def phase_ms(self):
+        """Device time of the last blocking solve by phase (CUDA events)."""
+        out = (ctypes.c_double * 4)()
+        self.L.fe_k_phase_ms(self.h, out)
+        return dict(zip(("setup_ms", "loop_ms", "output_ms", "steps"), list(out)))
 
     def launch_count(self):
         v = ctypes.c_int64()

@@ -89,12 +89,14 @@ struct Engine {
     Tile64 *d_tiles64 = nullptr;
     size_t tiles64_cap = 0;
     TileEnt *d_tilesD = nullptr;
+    std::vector<int> off64, cnt64;  // each problem's range in the FP64 tile list
     size_t tilesD_cap = 0;
     SolveState *h_states = nullptr;  // pinned
     size_t h_states_cap = 0;
     int *h_done = nullptr;           // pinned copies of the done flags (serving)
     size_t h_done_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev_setup = nullptr, ev_loop = nullptr;  // end of set-up, end of the step loop
     int ntc = 0, n64 = 0, nD = 0;    // tile counts of the uploaded lists
     bool any_tc = false, any_fp64 = false, any_digit = false;
     // the step loop as a CUDA graph: WHILE(any problem active) { IF(tc) k_sym_mma;
@@ -138,6 +140,8 @@ struct fe_ctx {
     std::vector<cudaEvent_t> pev;
     double prof_out[8] = {};
     std::atomic<long long> launches{0};  // kernels launched by this context
+    std::atomic<double> lz_narrow{1.0};  // test hook: scale of the estimated bound interval
+    double phase_ms[4] = {};             // last blocking solve: set-up, step loop, output; steps
     std::recursive_mutex mu;  // eng, profiling state (blocking calls)
     // continuous batching (fe_submit / fe_poll): a worker thread with its own engine
     Engine seng;
@@ -171,24 +175,45 @@ int cuda_fail(fe_ctx *ctx, cudaError_t e, const char *what) {
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// Upper-triangle tiles (row panel I < nI, column panel jmin(I) <= J < nJ,
+// jmin nondecreasing) in bands of `band` row panels, column by column within
+// a band.  The product kernels hand out consecutive tiles to CTAs that run at
+// the same time, so a wave then touches about `band` row panels and
+// wave / band column panels instead of one or two rows of the triangle and
+// every column.  `slot` stays the row-major index: per-tile partial sums land
+// in the same places, and are reduced in the same order, whatever the order.
+template <class Jmin>
+void push_banded(std::vector<TileEnt> &out, int nI, int nJ, int band, Jmin jmin) {
+    out.clear();
+    std::vector<int> row0(nI + 1, 0);
+    for (int I = 0; I < nI; ++I) row0[I + 1] = row0[I] + std::max(0, nJ - jmin(I));
+    for (int b0 = 0; b0 < nI; b0 += band) {
+        const int b1 = std::min(nI, b0 + band);
+        for (int J = jmin(b0); J < nJ; ++J)
+            for (int I = b0; I < b1; ++I)
+                if (J >= jmin(I)) out.push_back(TileEnt{0, I, J, row0[I] + J - jmin(I)});
+    }
+}
+
+// 128-row panels per band: the tensor-core tiles read 128 x K and 256 x K
+// panels (two FP16 slices each), the digit tiles 128 x K and 64 x K panels of
+// seven digits; the bands balance row-panel and column-panel bytes over a
+// wave of about 150 tiles.
+constexpr int kBandTc = 16, kBandDigit = 8;
+
 void build_tiles(Slot *s) {
-    s->tiles.clear();
     const int T = ceil_div(s->n, kTileM);
     const int TP = ceil_div(T, 2);
-    int slot = 0;
-    for (int I = 0; I < T; ++I)
-        for (int Jp = I / 2; Jp < TP; ++Jp) s->tiles.push_back(TileEnt{0, I, Jp, slot++});
+    push_banded(s->tiles, T, TP, kBandTc, [](int I) { return I / 2; });
     s->tiles64.clear();
     const int T64 = ceil_div(s->n, kTile64);
-    slot = 0;
+    int slot = 0;
     for (int I = 0; I < T64; ++I)
         for (int J = I; J < T64; ++J) s->tiles64.push_back(Tile64{0, I, J, slot++});
     s->tilesD.clear();
     if (s->method == kMethodSp2) {
         const int TD = ceil_div(s->n, kDigitN);
-        slot = 0;
-        for (int I = 0; I < T; ++I)
-            for (int J = 2 * I; J < TD; ++J) s->tilesD.push_back(TileEnt{0, I, J, slot++});
+        push_banded(s->tilesD, T, TD, kBandDigit, [](int I) { return 2 * I; });
     }
 }
 
@@ -528,6 +553,8 @@ int eng_init(fe_ctx *ctx, Engine &e, cudaStream_t user_stream) {
     FE_CUDA(ctx, cudaMemset(e.d_skcnt, 0, sizeof(int) * 2 * ctx->num_sms));
     FE_CUDA(ctx, cudaEventCreate(&e.ev0));
     FE_CUDA(ctx, cudaEventCreate(&e.ev1));
+    FE_CUDA(ctx, cudaEventCreate(&e.ev_setup));
+    FE_CUDA(ctx, cudaEventCreate(&e.ev_loop));
     return FE_OK;
 }
 
@@ -547,6 +574,8 @@ void eng_free(Engine &e) {
     if (e.h_done) cudaFreeHost(e.h_done);
     if (e.ev0) cudaEventDestroy(e.ev0);
     if (e.ev1) cudaEventDestroy(e.ev1);
+    if (e.ev_setup) cudaEventDestroy(e.ev_setup);
+    if (e.ev_loop) cudaEventDestroy(e.ev_loop);
     if (e.own_stream && e.stream) cudaStreamDestroy(e.stream);
     e = Engine();
 }
@@ -558,6 +587,8 @@ int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
     std::vector<Tile64> tiles64;
     std::vector<TileEnt> tilesD;
     e.any_tc = e.any_fp64 = e.any_digit = false;
+    e.off64.assign(np, 0);
+    e.cnt64.assign(np, 0);
     for (int k = 0; k < np; ++k) {
         const Job &j = jobs[k];
         hprobs[k] = j.slot->hp;
@@ -572,9 +603,12 @@ int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
             for (TileEnt t : j.slot->tiles) { t.prob = k; tiles.push_back(t); }
             hprobs[k].tc_ntiles = static_cast<int>(j.slot->tiles.size());
         }
+        e.off64[k] = static_cast<int>(tiles64.size());
+        e.cnt64[k] = 0;
         if (pr == FE_PREC_FP64 && !fermi) {
             e.any_fp64 = true;
             for (Tile64 t : j.slot->tiles64) { t.prob = k; tiles64.push_back(t); }
+            e.cnt64[k] = static_cast<int>(j.slot->tiles64.size());
         }
         if ((pr == FE_PREC_MIXED || pr == FE_PREC_TRY_FP16) && !fermi) {
             e.any_digit = true;
@@ -633,11 +667,30 @@ int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int 
                 k_lanczos_matvec<<<kLzBlocks, 256, 0, s>>>(e.d_probs, k);
                 k_lanczos_update<<<1, 1024, 0, s>>>(e.d_probs, k, it);
             }
-            k_bounds_finish<<<1, 32, 0, s>>>(e.d_probs, k);
+            k_bounds_finish<<<1, 32, 0, s>>>(e.d_probs, k, ctx->lz_narrow.load(std::memory_order_relaxed));
             ctx->launches += 2 + 2 * kLanczosSteps;
         }
         k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
         ctx->launches += 1;
+        if (j.lanczos) {
+            // certify the estimate: kCheckSteps products of this problem
+            // alone (a one-entry table), then X0 again on the certified bounds
+            const MmaProb *one = e.d_probs + k;
+            const bool fp64_only = (e.cnt64[k] > 0);
+            k_control<<<1, 256, 0, s>>>(one, 1, nullptr, 0, 0, 0, 0, 0u);
+            for (int c = 0; c < kCheckSteps; ++c) {
+                if (fp64_only)
+                    k_fp64_step<<<std::max(1, std::min(e.cnt64[k], 4 * ctx->num_sms)), 256, 0, s>>>(
+                        e.d_probs, e.d_tiles64 + e.off64[k], e.cnt64[k]);
+                else
+                    k_sym_mma<<<ctx->num_sms, kSymThreads, mma_smem_bytes(), s>>>(
+                        one, 1, e.d_tiles, e.ntc, e.d_err, e.d_skws, e.d_skcnt);
+                k_control<<<1, 256, 0, s>>>(one, 1, nullptr, 0, 0, 0, 0, 0u);
+            }
+            k_check_bounds<<<1, 32, 0, s>>>(e.d_probs, k);
+            k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
+            ctx->launches += 3 + 2 * kCheckSteps;
+        }
     }
     k_control<<<k1 - k0, 256, 0, s>>>(e.d_probs + k0, k1 - k0, nullptr, 0, 0, 0, 0, 0u);
     ++ctx->launches;
@@ -855,6 +908,7 @@ int run_problems_once(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) 
     FE_CUDA(ctx, cudaEventRecord(e.ev0, s));
     rc = eng_setup(ctx, e, jobs, 0, np);
     if (rc != FE_OK) return rc;
+    FE_CUDA(ctx, cudaEventRecord(e.ev_setup, s));
     int total_iters = 0;
     for (int k = 0; k < np; ++k) total_iters = std::max(total_iters, e.h_states[k].max_iters);
     // one step = product + control; +8 covers the phase hand-offs
@@ -876,6 +930,7 @@ int run_problems_once(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) 
     } else {
         eng_steps(ctx, e, np, nloop, ctx->prof ? &ctx->pev : nullptr);
     }
+    FE_CUDA(ctx, cudaEventRecord(e.ev_loop, s));
     for (int k = 0; k < np; ++k) {
         rc = eng_finish(ctx, e, k, jobs[k]);
         if (rc != FE_OK) return rc;
@@ -885,8 +940,15 @@ int run_problems_once(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) 
     int herr = 0;
     FE_CUDA(ctx, cudaMemcpyAsync(&herr, e.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     FE_CUDA(ctx, cudaStreamSynchronize(s));
-    float ms = 0.0f;
+    float ms = 0.0f, ms_setup = 0.0f, ms_loop = 0.0f, ms_fin = 0.0f;
     cudaEventElapsedTime(&ms, e.ev0, e.ev1);
+    cudaEventElapsedTime(&ms_setup, e.ev0, e.ev_setup);
+    cudaEventElapsedTime(&ms_loop, e.ev_setup, e.ev_loop);
+    cudaEventElapsedTime(&ms_fin, e.ev_loop, e.ev1);
+    ctx->phase_ms[0] = ms_setup;
+    ctx->phase_ms[1] = ms_loop;
+    ctx->phase_ms[2] = ms_fin;
+    ctx->phase_ms[3] = use_graph ? static_cast<double>(e.h_flags.n_body) : static_cast<double>(nloop);
     if (use_graph) {
         // kernels the graph ran: a control per step, every family once in the
         // first step, then the families the control kernel switched on
@@ -1511,6 +1573,20 @@ extern "C" int fe_k_profile(fe_ctx *ctx, int enable) {
     if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     ctx->prof = enable != 0;
+    return FE_OK;
+}
+
+extern "C" int fe_k_narrow_bounds(fe_ctx *ctx, double factor) {
+    if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
+    if (!(factor > 0.0 && factor <= 1.0)) return set_err(ctx, FE_EINVAL, "factor must be in (0, 1]");
+    ctx->lz_narrow.store(factor, std::memory_order_relaxed);
+    return FE_OK;
+}
+
+extern "C" int fe_k_phase_ms(fe_ctx *ctx, double *out4) {
+    if (!ctx || !out4) return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    for (int i = 0; i < 4; ++i) out4[i] = ctx->phase_ms[i];
     return FE_OK;
 }
 

@@ -70,6 +70,7 @@ constexpr uint64_t kWaitTimeoutNs = 2000000000ull;
 
 constexpr int kHistRows = 160;  // per-step history kept in the solve state
 constexpr int kLanczosSteps = 16;   // Lanczos steps of the spectral-bound estimate
+constexpr int kCheckSteps = 3;      // logistic steps certifying the estimate (T_8)
 constexpr int kStatusEscaped = -100;  // internal: an eigenvalue left [0, 1] (bounds too tight)
 constexpr int kHistCols = 6;
 
@@ -131,6 +132,12 @@ struct SolveState {
     int lz_k, lz_pad;     // Lanczos steps taken
     double gersh_lo, gersh_hi;
     double lz_a[kLanczosSteps], lz_b[kLanczosSteps + 1];
+    // certificate of the estimate [lz_lo, lz_hi]: kCheckSteps logistic steps
+    // X <- 4 X (I - X) from X0 on that interval; ||X||_F^2 after them (chk_F)
+    // bounds how far the spectrum reaches beyond it (chk_amax, in half-widths)
+    int chk_left;         // check products still to issue
+    int chk;              // 1: the product issued is a check step
+    double lz_lo, lz_hi, chk_F, chk_amax;
     // iterate X = c I + Y, or X = Xd[xcur] (FP64) once in the FP64 phase
     double c;
     float s_cur;        // slice scale of the current slice set

@@ -89,12 +89,16 @@ __global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *r
 // Spectral-bound estimate by kLanczosSteps Lanczos steps (FP64): start vector,
 // then per step w = H v (kLzBlocks blocks, partial dot products) and the
 // three-term update (one block); k_bounds_finish turns the tridiagonal into
-// bounds and prepares X0.
+// bounds and prepares X0.  narrow < 1 shrinks the estimated interval about its
+// centre by that factor (a test hook that forces the too-tight case).
 constexpr int kLzBlocks = 304;
 __global__ void k_lanczos_start(const MmaProb *probs, int prob);
 __global__ void k_lanczos_matvec(const MmaProb *probs, int prob);
 __global__ void k_lanczos_update(const MmaProb *probs, int prob, int j);
-__global__ void k_bounds_finish(const MmaProb *probs, int prob);
+__global__ void k_bounds_finish(const MmaProb *probs, int prob, double narrow);
+// Certified bounds from the certificate steps (kCheckSteps products issued by
+// k_control after k_bounds_finish), then the X0 preparation.
+__global__ void k_check_bounds(const MmaProb *probs, int prob);
 // X0 = (hi I - Hp)/(hi - lo) stored as c0 I + Y0 (its slice scale from a bound
 // on |Y0_ij|), or for finite temperature the parameters of z0.
 __device__ __forceinline__ void setup_from_bounds(const MmaProb &pr, SolveState *st, double lo, double hi) {

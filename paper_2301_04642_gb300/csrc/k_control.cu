@@ -73,6 +73,60 @@ __device__ void begin_op(ProdOp &op, int A, int B, int E1, int E2, double inv) {
     op.ra = op.rb = op.rc = 0.0f;
 }
 
+// ------------------------------------------------------ bound certificate
+// The kCheckSteps logistic steps X <- 4 X (I - X) that certify the spectral-
+// bound estimate (the derivation is with k_check_bounds).  X0 was prepared on
+// the estimate in the zero-temperature form for either method; the products
+// use the split-FP16 kernel (the FP64 kernel for FP64-only problems).  After
+// the last one, chk_amax bounds |a| over the spectrum, a in half-widths of
+// the estimate about its centre.
+__device__ void control_check(SolveState *st, double trV, double sumsq) {
+    const int n = st->n;
+    const int prev = st->kind;
+    if (prev == kTcSplit) {
+        st->c = st->c_next;
+        st->s_cur = st->s_next;
+        st->cur ^= 1;
+    } else if (prev == kFp64) {
+        st->xcur ^= 1;
+    }
+    const double cc = st->c;
+    const double f2 = st->x_fp64 ? sumsq : n * cc * cc + 2.0 * cc * trV + sumsq;  // ||X||_F^2
+    if (st->chk_left == 0) {
+        // |T_8(a)| = |1 - 2 x_3| <= 1 + 2 ||X_3||_F for every eigenvalue; the
+        // allowance (a quarter of ||X_3||_F, plus 1) covers the products'
+        // rounding: FP16 slices of ~22 bits and FP32 sums, a relative error of
+        // order 1e-5 after three products even where the rounding is one-sided
+        const double f = sqrt(fmax(f2, 0.0));
+        const double t = 1.0 + 2.0 * (1.25 * f + 1.0);
+        st->chk_F = f2;
+        st->chk_amax = cosh(acosh(t) / static_cast<double>(1 << kCheckSteps));
+        st->chk = 0;
+        st->kind = kNone;
+        return;
+    }
+    st->chk = 1;
+    st->chk_left -= 1;
+    if (st->x_fp64) {
+        st->kind = kFp64;
+        return;
+    }
+    // X = c I + Y:  4X - 4X^2 -> c' = 4c - 4c^2, Y' = (4 - 8c) Y - 4 Y^2, with
+    // ||Y'||_F <= |4 - 8c| ||Y||_F + 4 ||Y||_F^2 (no [0, 1] assumption here)
+    const double alpha = 4.0 - 8.0 * cc;
+    const double fro = sqrt(fmax(sumsq, 0.0));
+    const double bound = fabs(alpha) * fro + 4.0 * fro * fro;
+    st->kind = kTcSplit;
+    st->c_next = 4.0 * cc - 4.0 * cc * cc;
+    ProdOp &op = st->op;
+    const int cur = st->cur;
+    const double s = st->s_cur;
+    begin_op(op, cur, cur, cur, -1, 1.0 / (s * s));
+    op.nout = 1;
+    set_out(op.out[0], cur ^ 1, kOutMaster | kOutSlices, -4.0, alpha, 0.0, 0.0, bound);
+    st->s_next = op.out[0].s;
+}
+
 // ------------------------------------------------------------------ SP2 step
 __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq) {
     const int n = st->n;
@@ -517,7 +571,8 @@ __device__ void control_one(const MmaProb &pr) {
         st->kind = kNone;
         return;
     }
-    if (st->method == kMethodFermi) control_fermi(st, s_a[0], s_b[0], s_c[0]);
+    if (st->chk_left > 0 || st->chk) control_check(st, s_a[0], s_b[0]);
+    else if (st->method == kMethodFermi) control_fermi(st, s_a[0], s_b[0], s_c[0]);
     else control_sp2(st, s_a[0], s_b[0], s_d[0]);
 }
 

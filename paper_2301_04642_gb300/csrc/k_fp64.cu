@@ -57,6 +57,7 @@ __device__ __forceinline__ void step_epilogue(const MmaProb &pr, const SolveStat
                                               const double (&P)[4][4], Partials &pa) {
     double *Xo = pr.Xd[st->xcur ^ 1];  // the control kernel flips xcur afterwards
     const int sq = st->sq;
+    const int chk = st->chk;  // bound-certificate step: X' = 4 X (I - X)
     const double gamma = st->gamma;
     const int n = src.n;
 #pragma unroll
@@ -69,7 +70,8 @@ __device__ __forceinline__ void step_epilogue(const MmaProb &pr, const SolveStat
             const double xo = src.at(i, j);
             // SP2 branch plus the trace correction gamma (X - X^2), which
             // commutes with Hp and moves each eigenvalue by gamma x (1 - x)
-            const double xn = (sq ? P[r][q] : 2.0 * xo - P[r][q]) + gamma * (xo - P[r][q]);
+            const double xn = chk ? 4.0 * (xo - P[r][q])
+                                  : (sq ? P[r][q] : 2.0 * xo - P[r][q]) + gamma * (xo - P[r][q]);
             Xo[static_cast<long long>(i) * pr.ldx + j] = xn;
             const double dd = P[r][q] - xo;
             if (j != i) {

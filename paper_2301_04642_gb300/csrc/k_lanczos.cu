@@ -7,14 +7,22 @@
 // extra products (and the finite-temperature recursion extra doublings).
 // Here kLanczosSteps steps of the Lanczos recurrence in FP64, from a fixed
 // pseudo-random unit vector, give Ritz values theta_min, theta_max inside the
-// spectrum; the bounds are
-//     theta -/+ (2 |beta_k s_k| + 0.05 (theta_max - theta_min)),
-// where |beta_k s_k| is the residual of the extreme Ritz pair (s the unit
-// eigenvector of the tridiagonal T), clipped to the Gershgorin interval.
-// They are estimates, not guarantees: the zero-temperature control kernel
-// watches sum x^2 - sum x, which turns positive by more than 0.5 only if an
-// eigenvalue has left [-0.37, 1.37] (the only way one can end on the wrong
-// side), and the host then re-runs that problem from the Gershgorin bounds.
+// spectrum; the estimate is
+//     [theta_min - |beta_k s_min|, theta_max + |beta_k s_max|],
+// widened by the residuals of the extreme Ritz pairs (s the unit eigenvector
+// of the tridiagonal T) and clipped to the Gershgorin interval.
+//
+// An estimate is not a bound, so it is certified before use (k_check_bounds):
+// with X0 = (hi I - Hp)/(hi - lo), kCheckSteps logistic steps
+// X <- 4 X (I - X) give X_3 = (I - T_8(A))/2, T_8 the Chebyshev polynomial and
+// A = (2 Hp - (hi + lo) I)/(hi - lo).  |T_8| <= 1 on [-1, 1] and
+// T_8(a) = cosh(8 arccosh |a|) outside, so every eigenvalue a of A satisfies
+// (cosh(8 arccosh |a|) - 1)/2 <= ||X_3||_F, i.e.
+//     |a| <= cosh(arccosh(1 + 2 ||X_3||_F) / 8),
+// and the interval widened by that factor contains the spectrum.  Eigenvalues
+// inside the estimate keep X_3 in [0, 1] (||X_3||_F <= sqrt(n): at most a
+// ~25% widening); one that the estimate missed grows X_3 and widens the
+// bound just enough to take it in.
 //
 // No reorthogonalisation: loss of orthogonality only repeats converged Ritz
 // values, which cannot move the extreme ones outward.
@@ -190,7 +198,7 @@ __global__ void k_lanczos_update(const MmaProb *probs, int prob, int j) {
 }
 
 // bounds from the tridiagonal, then the X0 preparation (one thread)
-__global__ void k_bounds_finish(const MmaProb *probs, int prob) {
+__global__ void k_bounds_finish(const MmaProb *probs, int prob, double narrow) {
     const MmaProb &pr = probs[prob];
     SolveState *st = pr.st;
     if (threadIdx.x != 0) return;
@@ -203,14 +211,40 @@ __global__ void k_bounds_finish(const MmaProb *probs, int prob) {
         const double tmax = tri_eig(a, b, k, k - 1, glo, ghi);
         const double rmin = b[k] * tri_last_comp(a, b, k, tmin);
         const double rmax = b[k] * tri_last_comp(a, b, k, tmax);
-        const double margin = 0.05 * (tmax - tmin);
-        lo = fmax(glo, tmin - 2.0 * rmin - margin);
-        hi = fmin(ghi, tmax + 2.0 * rmax + margin);
+        lo = fmax(glo, tmin - rmin);
+        hi = fmin(ghi, tmax + rmax);
         if (!(hi > lo)) {
             lo = glo;
             hi = ghi;
         }
     }
+    if (narrow < 1.0) {
+        const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo) * narrow;
+        lo = mid - half;
+        hi = mid + half;
+    }
+    // X0 on the estimate, for the certificate steps (k_control issues them)
+    st->lz_lo = lo;
+    st->lz_hi = hi;
+    st->chk_left = kCheckSteps;
+    setup_from_bounds(pr, st, lo, hi);
+}
+
+// Certified bounds from the check steps, then the X0 preparation (one thread)
+__global__ void k_check_bounds(const MmaProb *probs, int prob) {
+    const MmaProb &pr = probs[prob];
+    SolveState *st = pr.st;
+    if (threadIdx.x != 0) return;
+    const double mid = 0.5 * (st->lz_lo + st->lz_hi), half = 0.5 * (st->lz_hi - st->lz_lo);
+    const double a = st->chk_amax;
+    double lo = st->gersh_lo, hi = st->gersh_hi;
+    if (a < 1e300 && half > 0.0) {  // NaN and overflow keep the Gershgorin interval
+        lo = fmax(lo, mid - half * a);
+        hi = fmin(hi, mid + half * a);
+    }
+    st->chk = 0;
+    st->chk_left = 0;
+    st->kind = kNone;
     setup_from_bounds(pr, st, lo, hi);
 }
 

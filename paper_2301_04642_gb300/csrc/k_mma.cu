@@ -107,17 +107,24 @@ __device__ __forceinline__ void put_slices(const MatSlot &m, size_t at, float ys
     m.sl[1][at] = __float2half_rn(ys - __half2float(hh));
 }
 
-// ---- Stream-K schedule.  The launch's work is the sequence, over the active
-// problems in table order, of their tiles, each worth `units` = its 64-wide K
-// chunks (1 for an epilogue-only step).  The participating CTAs take equal
-// contiguous ranges of it, so tile boundaries (and store phases) fall at
-// different times in different CTAs and the last wave is not left half
-// empty.  At most G = W / (largest tile) CTAs take part, so a tile spans at
-// most two ranges: a head segment at the end of one CTA's range and a tail
-// segment at the start of the next one's.  Every role of a CTA walks the same
-// segments.
+// ---- Schedule: data-parallel waves, then Stream-K.  The launch's work is the
+// sequence, over the active problems in table order, of their tiles, each
+// worth `units` = its 64-wide K chunks (1 for an epilogue-only step).
+// When every tile is worth the same and there are at least two waves, whole
+// waves go first, tile t to CTA t mod grid: all CTAs then step through K
+// together on tiles that are neighbours in the list (the host orders tiles in
+// bands so that these share row and column panels), and each panel chunk is
+// read from HBM about once per wave while the rest hit L2.  The remaining one
+// to two waves of tiles (all of them otherwise) are cut into equal contiguous
+// ranges, one per participating CTA (Stream-K), so tile boundaries (and store
+// phases) fall at different times in different CTAs and the last wave is not
+// left half empty.  At most G = W / (largest tile) CTAs take part, so a tile
+// spans at most two ranges: a head segment at the end of one CTA's range and
+// a tail segment at the start of the next one's.  Every role of a CTA walks
+// the same segments.
 struct Seg {
     int tile;   // index into the launch's tile list
+    int prob;   // index of its problem in the launch's table
     int k0;     // first chunk
     int nch;    // chunks (0 for an epilogue-only step)
     bool split; // the tile is shared with a neighbouring CTA
@@ -132,33 +139,61 @@ __device__ __forceinline__ int tile_units(const MmaProb &pr) {
 struct SegIter {
     const MmaProb *probs;
     int nprobs;
-    long long g, end;
+    long long dp, dp_end;  // data-parallel part: next tile index (over active tiles), end
+    long long g, end;      // Stream-K part: this CTA's range of work units
 
     __device__ void init(const MmaProb *p, int np) {
         probs = p;
         nprobs = np;
-        long long W = 0;
-        int wmax = 1;
+        long long W = 0, T = 0;
+        int wmax = 1, wmin = 0x7fffffff;
         for (int q = 0; q < np; ++q) {
             const MmaProb &pr = p[q];
             if (pr.tc_ntiles == 0 || !tile_active(pr.st)) continue;
             const int w = tile_units(pr);
             W += static_cast<long long>(pr.tc_ntiles) * w;
+            T += pr.tc_ntiles;
             wmax = w > wmax ? w : wmax;
+            wmin = w < wmin ? w : wmin;
         }
-        long long G = W / wmax;
-        if (G > static_cast<long long>(gridDim.x)) G = gridDim.x;
-        if (G < 1) G = 1;
+        const long long grid = gridDim.x;
         const long long b = blockIdx.x;
-        if (W == 0 || b >= G) {
+        long long D = 0;  // tiles in whole data-parallel waves
+        if (T > 0 && wmin == wmax && T >= 2 * grid) D = (T % grid == 0) ? T : (T / grid - 1) * grid;
+        dp = b;
+        dp_end = D;
+        const long long Wsk = W - D * wmax;
+        long long G = Wsk / wmax;
+        if (G > grid) G = grid;
+        if (G < 1) G = 1;
+        if (Wsk <= 0 || b >= G) {
             g = end = 0;
         } else {
-            g = W * b / G;
-            end = W * (b + 1) / G;
+            g = D * wmax + Wsk * b / G;
+            end = D * wmax + Wsk * (b + 1) / G;
         }
     }
 
     __device__ bool next(Seg &sg) {
+        if (dp < dp_end) {
+            long long r = dp;
+            dp += gridDim.x;
+            for (int q = 0; q < nprobs; ++q) {
+                const MmaProb &pr = probs[q];
+                if (pr.tc_ntiles == 0 || !tile_active(pr.st)) continue;
+                if (r < pr.tc_ntiles) {
+                    sg.tile = pr.tc_tile0 + static_cast<int>(r);
+                    sg.prob = q;
+                    sg.k0 = 0;
+                    sg.nch = (step_chunks(pr.st, pr.n) > 0) ? tile_units(pr) : 0;
+                    sg.split = false;
+                    sg.head = true;
+                    return true;
+                }
+                r -= pr.tc_ntiles;
+            }
+            dp = dp_end;
+        }
         if (g >= end) return false;
         long long r = g;
         for (int q = 0; q < nprobs; ++q) {
@@ -171,6 +206,7 @@ struct SegIter {
                 const long long left = end - g;
                 const int k1 = (left < w - k) ? k + static_cast<int>(left) : w;
                 sg.tile = pr.tc_tile0 + static_cast<int>(r / w);
+                sg.prob = q;
                 sg.k0 = k;
                 sg.nch = (step_chunks(pr.st, pr.n) > 0) ? k1 - k : 0;
                 sg.split = (k > 0) || (k1 < w);
@@ -248,7 +284,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         while (ok && it.next(sg)) {
             if (sg.tile >= ntiles) break;
             const TileEnt te = tiles[sg.tile];
-            const MmaProb &pr = probs[te.prob];
+            const MmaProb &pr = probs[sg.prob];
             const SolveState *st = pr.st;
             const int S = (step_kind(st) == kTcSplit) ? 2 : 1;
             const MatSlot &ma = pr.mats[st->op.A];
@@ -300,7 +336,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         while (ok && it.next(sg)) {
             if (sg.tile >= ntiles) break;
             const TileEnt te = tiles[sg.tile];
-            const MmaProb &pr = probs[te.prob];
+            const MmaProb &pr = probs[sg.prob];
             const SolveState *st = pr.st;
             const int S = (step_kind(st) == kTcSplit) ? 2 : 1;
             for (int kc = sg.k0; kc < sg.k0 + sg.nch; ++kc) {
@@ -379,7 +415,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         while (ok && it.next(sg)) {
             if (sg.tile >= ntiles) break;
             const TileEnt te = tiles[sg.tile];
-            const MmaProb &pr = probs[te.prob];
+            const MmaProb &pr = probs[sg.prob];
             const SolveState *st = pr.st;
             const int n = pr.n;
             float acc[128];

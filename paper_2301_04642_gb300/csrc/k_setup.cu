@@ -88,7 +88,8 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
     const double dshift = st->emax * inv_w - st->c;  // diagonal of Y0 gets +dshift
     const float s0 = st->s_cur;
     const bool fp64 = (st->prec == kPrecFp64);
-    const bool fermi = (st->method == kMethodFermi);
+    // the certificate steps start from X0 in the zero-temperature form
+    const bool fermi = (st->method == kMethodFermi) && st->chk_left == 0;
     const double hb0 = 0.5 * st->beta0, mu0 = st->mu_t;
     const float sz = st->scl[kMatZ];
     double tr = 0.0, sq = 0.0, mx = 0.0;

@@ -50,6 +50,9 @@ WORKLOADS = {
     "gapped_n4096": dict(make=lambda: hp_synth.workload_n4096(), precision="mixed"),
     "gapped_n256_fp64": dict(make=lambda: hp_synth.workload_n256(), precision="fp64"),
     # larger single solves (generated on the GPU: the CPU QR would take minutes)
+    "gapped_n8192": dict(make=lambda: hp_synth.gapped(8192, 6963, (-3.0, -0.01), (0.01, 1.0), 1005,
+                                                        device="cuda", name="gapped_n8192"),
+                         precision="mixed"),
     "gapped_n16384": dict(make=lambda: hp_synth.gapped(16384, 13926, (-3.0, -0.01), (0.01, 1.0), 1004,
                                                          device="cuda", name="gapped_n16384"),
                           precision="mixed"),
@@ -209,7 +212,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        if wl["make"] is None or args.workload in ("gapped_n16384", "fermi_n16384"):
+        if wl["make"] is None or args.workload in ("gapped_n8192", "gapped_n16384", "fermi_n16384"):
             print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm is timed on the "
                               "single-solve workloads gapped_n4096 and gapped_n256_fp64"}), flush=True)
             return

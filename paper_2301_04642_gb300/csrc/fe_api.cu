@@ -90,6 +90,8 @@ struct Engine {
     size_t tiles64_cap = 0;
     TileEnt *d_tilesD = nullptr;
     std::vector<int> off64, cnt64;  // each problem's range in the FP64 tile list
+    MmaProb *d_chk = nullptr;       // table of the problems certifying their bounds together
+    size_t chk_cap = 0;
     size_t tilesD_cap = 0;
     SolveState *h_states = nullptr;  // pinned
     size_t h_states_cap = 0;
@@ -364,11 +366,10 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
     }
     if (method == kMethodSp2) {
         for (int a = 0; a < kDigits; ++a) {
-            int rc = encode_map(ctx, &s->hp.dA[a], digs[a], n, lds, kTileM, kDigitK,
-                                CU_TENSOR_MAP_SWIZZLE_64B);
+            const CUtensorMapSwizzle dswz = (kDigitK == 16) ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B;
+            int rc = encode_map(ctx, &s->hp.dA[a], digs[a], n, lds, kTileM, kDigitK, dswz);
             if (rc == FE_OK)
-                rc = encode_map(ctx, &s->hp.dB[a], digs[a], n, lds, kDigitN, kDigitK,
-                                CU_TENSOR_MAP_SWIZZLE_64B);
+                rc = encode_map(ctx, &s->hp.dB[a], digs[a], n, lds, kDigitN, kDigitK, dswz);
             if (rc != FE_OK) {
                 free_slot(ctx, s);
                 return rc;
@@ -570,6 +571,7 @@ void eng_free(Engine &e) {
     if (e.d_tiles) cudaFree(e.d_tiles);
     if (e.d_tiles64) cudaFree(e.d_tiles64);
     if (e.d_tilesD) cudaFree(e.d_tilesD);
+    if (e.d_chk) cudaFree(e.d_chk);
     if (e.h_states) cudaFreeHost(e.h_states);
     if (e.h_done) cudaFreeHost(e.h_done);
     if (e.ev0) cudaEventDestroy(e.ev0);
@@ -646,6 +648,8 @@ int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
 int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int k1) {
     if (k1 <= k0) return FE_OK;
     cudaStream_t s = e.stream;
+    const int m = k1 - k0;
+    std::vector<int> tc_chk, f64_chk;  // problems certifying with the split-FP16 / FP64 kernel
     for (int k = k0; k < k1; ++k) {
         const Job &j = jobs[k];
         const int n = static_cast<int>(j.p->n);
@@ -661,38 +665,63 @@ int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int 
         k_bounds_rows<<<ceil_div(n, 8), 256, 0, s>>>(e.d_probs, k, j.slot->rowinfo, j.slot->bad);
         k_bounds_reduce<<<1, 1024, 0, s>>>(e.d_probs, k, j.slot->rowinfo, j.slot->bad);
         ctx->launches += 2;
-        if (j.lanczos) {
-            k_lanczos_start<<<1, 1024, 0, s>>>(e.d_probs, k);
-            for (int it = 0; it < kLanczosSteps; ++it) {
-                k_lanczos_matvec<<<kLzBlocks, 256, 0, s>>>(e.d_probs, k);
-                k_lanczos_update<<<1, 1024, 0, s>>>(e.d_probs, k, it);
-            }
-            k_bounds_finish<<<1, 32, 0, s>>>(e.d_probs, k, ctx->lz_narrow.load(std::memory_order_relaxed));
-            ctx->launches += 2 + 2 * kLanczosSteps;
+        if (j.lanczos) (e.cnt64[k] > 0 ? f64_chk : tc_chk).push_back(k);
+    }
+    const bool any_lz = !tc_chk.empty() || !f64_chk.empty();
+    if (any_lz) {
+        // the estimate of every problem that takes one, all at once (the
+        // kernels skip problems without lz_on)
+        k_lanczos_start<<<m, 1024, 0, s>>>(e.d_probs, k0);
+        for (int it = 0; it < kLanczosSteps; ++it) {
+            k_lanczos_matvec<<<dim3(kLzBlocks, m), kLzThreads, 0, s>>>(e.d_probs, k0);
+            k_lanczos_update<<<m, 1024, 0, s>>>(e.d_probs, k0, it);
         }
-        k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
-        ctx->launches += 1;
-        if (j.lanczos) {
-            // certify the estimate: kCheckSteps products of this problem
-            // alone (a one-entry table), then X0 again on the certified bounds
+        k_bounds_finish<<<m, 32, 0, s>>>(e.d_probs, k0, ctx->lz_narrow.load(std::memory_order_relaxed));
+        ctx->launches += 2 + 2 * kLanczosSteps;
+    }
+    for (int k = k0; k < k1; ++k) k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
+    ctx->launches += m;
+    if (any_lz) {
+        // certify the estimates: kCheckSteps products over a table of just
+        // those problems (the split-FP16 kernel takes them all in one launch,
+        // the FP64 kernel one problem at a time), then X0 again on the
+        // certified bounds
+        if (!tc_chk.empty()) {
+            const int nt = static_cast<int>(tc_chk.size());
+            const MmaProb *tab = e.d_probs + tc_chk[0];
+            if (tc_chk.back() - tc_chk[0] + 1 != nt) {  // not contiguous: gather the entries
+                int rc = ensure_dev(ctx, &e.d_chk, &e.chk_cap, static_cast<size_t>(nt));
+                if (rc != FE_OK) return rc;
+                for (int q = 0; q < nt; ++q)
+                    FE_CUDA(ctx, cudaMemcpyAsync(e.d_chk + q, e.d_probs + tc_chk[q], sizeof(MmaProb),
+                                                 cudaMemcpyDeviceToDevice, s));
+                tab = e.d_chk;
+            }
+            k_control<<<nt, 256, 0, s>>>(tab, nt, nullptr, 0, 0, 0, 0, 0u);
+            for (int c = 0; c < kCheckSteps; ++c) {
+                k_sym_mma<<<ctx->num_sms, kSymThreads, mma_smem_bytes(), s>>>(tab, nt, e.d_tiles, e.ntc, e.d_err,
+                                                                           e.d_skws, e.d_skcnt);
+                k_control<<<nt, 256, 0, s>>>(tab, nt, nullptr, 0, 0, 0, 0, 0u);
+            }
+            ctx->launches += 1 + 2 * kCheckSteps;
+        }
+        for (int k : f64_chk) {
             const MmaProb *one = e.d_probs + k;
-            const bool fp64_only = (e.cnt64[k] > 0);
             k_control<<<1, 256, 0, s>>>(one, 1, nullptr, 0, 0, 0, 0, 0u);
             for (int c = 0; c < kCheckSteps; ++c) {
-                if (fp64_only)
-                    k_fp64_step<<<std::max(1, std::min(e.cnt64[k], 4 * ctx->num_sms)), 256, 0, s>>>(
-                        e.d_probs, e.d_tiles64 + e.off64[k], e.cnt64[k]);
-                else
-                    k_sym_mma<<<ctx->num_sms, kSymThreads, mma_smem_bytes(), s>>>(
-                        one, 1, e.d_tiles, e.ntc, e.d_err, e.d_skws, e.d_skcnt);
+                k_fp64_step<<<std::max(1, std::min(e.cnt64[k], 4 * ctx->num_sms)), 256, 0, s>>>(
+                    e.d_probs, e.d_tiles64 + e.off64[k], e.cnt64[k]);
                 k_control<<<1, 256, 0, s>>>(one, 1, nullptr, 0, 0, 0, 0, 0u);
             }
-            k_check_bounds<<<1, 32, 0, s>>>(e.d_probs, k);
-            k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
-            ctx->launches += 3 + 2 * kCheckSteps;
+            ctx->launches += 1 + 2 * kCheckSteps;
         }
+        k_check_bounds<<<m, 32, 0, s>>>(e.d_probs, k0);
+        ++ctx->launches;
+        for (int k : tc_chk) k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
+        for (int k : f64_chk) k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
+        ctx->launches += static_cast<long long>(tc_chk.size() + f64_chk.size());
     }
-    k_control<<<k1 - k0, 256, 0, s>>>(e.d_probs + k0, k1 - k0, nullptr, 0, 0, 0, 0, 0u);
+    k_control<<<m, 256, 0, s>>>(e.d_probs + k0, m, nullptr, 0, 0, 0, 0, 0u);
     ++ctx->launches;
     // the state images must stay valid until their copies ran
     FE_CUDA(ctx, cudaStreamSynchronize(s));

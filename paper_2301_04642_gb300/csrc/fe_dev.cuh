@@ -52,7 +52,7 @@ constexpr float kSliceTop = 16384.0f;  // slices are scaled so |s Y| <= 2^14 < f
 constexpr int kDigits = 7;
 constexpr int kDigitN = 64;       // tile columns (7 level buffers x 64 TMEM columns)
 constexpr int kDigitK = 32;       // K per pipeline stage (one 64-byte swizzle row of FP16)
-constexpr int kDigitStages = 2;
+constexpr int kDigitStages = 2;   // 2 x 84 KiB (4 x 42 KiB stages of K = 16 measured slower)
 constexpr int kDigitKBlock = 128; // K per drain of the level buffers
 
 // error codes written by kernels into the context's device error word
@@ -345,6 +345,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(const void *tile) {
     d |= static_cast<uint64_t>((512u >> 4) & 0x3FFFu) << 32;
     d |= static_cast<uint64_t>(1u) << 46;
     d |= static_cast<uint64_t>(4u) << 61;                        // swizzle mode: 64 B
+    return d;
+}
+
+// The same for 32-byte swizzling: rows of 32 bytes, 8-row atoms 256 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw32(const void *tile) {
+    const uint32_t addr = smem_u32(tile);
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>(1u) << 16;
+    d |= static_cast<uint64_t>((256u >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;
+    d |= static_cast<uint64_t>(6u) << 61;                        // swizzle mode: 32 B
     return d;
 }
 

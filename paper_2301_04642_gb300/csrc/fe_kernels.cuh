@@ -86,19 +86,23 @@ __global__ void k_bounds_rows(const MmaProb *probs, int prob, RowInfo *rowinfo, 
 // the Lanczos estimate off it also prepares X0 from the Gershgorin bounds.
 __global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *rowinfo,
                                 const int *bad);
-// Spectral-bound estimate by kLanczosSteps Lanczos steps (FP64): start vector,
-// then per step w = H v (kLzBlocks blocks, partial dot products) and the
-// three-term update (one block); k_bounds_finish turns the tridiagonal into
-// bounds and prepares X0.  narrow < 1 shrinks the estimated interval about its
-// centre by that factor (a test hook that forces the too-tight case).
+// Spectral-bound estimate by kLanczosSteps Lanczos steps (FP64) for the
+// problems k0 .. k0 + (blocks or grid rows) - 1 that have lz_on: start
+// vector, then per step w = H v (kLzBlocks blocks of kLzThreads per problem,
+// partial dot products) and the three-term update (one block per problem);
+// k_bounds_finish turns the tridiagonal into the estimate and prepares X0 on
+// it.  narrow < 1 shrinks the estimate about its centre by that factor (a test
+// hook that forces the too-tight case).
 constexpr int kLzBlocks = 304;
-__global__ void k_lanczos_start(const MmaProb *probs, int prob);
-__global__ void k_lanczos_matvec(const MmaProb *probs, int prob);
-__global__ void k_lanczos_update(const MmaProb *probs, int prob, int j);
-__global__ void k_bounds_finish(const MmaProb *probs, int prob, double narrow);
+constexpr int kLzThreads = 512;
+__global__ void k_lanczos_start(const MmaProb *probs, int k0);
+__global__ void k_lanczos_matvec(const MmaProb *probs, int k0);
+__global__ void k_lanczos_update(const MmaProb *probs, int k0, int j);
+__global__ void k_bounds_finish(const MmaProb *probs, int k0, double narrow);
 // Certified bounds from the certificate steps (kCheckSteps products issued by
-// k_control after k_bounds_finish), then the X0 preparation.
-__global__ void k_check_bounds(const MmaProb *probs, int prob);
+// k_control after k_bounds_finish), then the X0 preparation; one block per
+// problem from k0.
+__global__ void k_check_bounds(const MmaProb *probs, int k0);
 // X0 = (hi I - Hp)/(hi - lo) stored as c0 I + Y0 (its slice scale from a bound
 // on |Y0_ij|), or for finite temperature the parameters of z0.
 __device__ __forceinline__ void setup_from_bounds(const MmaProb &pr, SolveState *st, double lo, double hi) {

@@ -23,7 +23,8 @@
 //
 // Tiles: 128 rows (block I) x 64 columns (block J), J >= 2I, one persistent
 // CTA per SM.  Warp roles as in the split-FP16 kernel: warp 0 TMA (per K
-// stage of 32 one box per digit for A and for B), warp 1 TMEM owner and MMA
+// stage of kDigitK one box per digit for A and for B; kDigitStages stages),
+// warp 1 TMEM owner and MMA
 // issuer (7 level buffers of 64 columns), warps 2-9 drain + epilogue (warp w:
 // TMEM lanes 32 (w % 4) .., columns 32 ((w - 2) / 4) .. of each level).
 // Every wait is bounded; on a timeout the kernel records an error code,
@@ -35,8 +36,16 @@ namespace fe {
 
 namespace {
 
-constexpr int kDA = kTileM * kDigitK * 2;   // 8 KiB: one digit, 128 rows x 32 K
-constexpr int kDB = kDigitN * kDigitK * 2;  // 4 KiB: one digit, 64 rows x 32 K
+constexpr int kDA = kTileM * kDigitK * 2;   // one digit, 128 rows x kDigitK
+constexpr int kDB = kDigitN * kDigitK * 2;  // one digit, 64 rows x kDigitK
+static_assert(kDigitK == 16 || kDigitK == 32, "a stage is one 32- or 64-byte swizzle row");
+
+// shared-memory descriptor of one digit block of a stage (K-major, swizzled
+// rows of kDigitK FP16)
+__device__ __forceinline__ uint64_t digit_desc(const void *tile) {
+    if constexpr (kDigitK == 16) return smem_desc_sw32(tile);
+    else return smem_desc_sw64(tile);
+}
 constexpr int kStagesPerBlock = kDigitKBlock / kDigitK;
 
 struct alignas(1024) DigitStage {
@@ -219,8 +228,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                     uint64_t da[kDigits], db[kDigits];
 #pragma unroll
                     for (int a = 0; a < kDigits; ++a) {
-                        da[a] = smem_desc_sw64(stages[stage].a[a]);
-                        db[a] = smem_desc_sw64(stages[stage].b[a]);
+                        da[a] = digit_desc(stages[stage].a[a]);
+                        db[a] = digit_desc(stages[stage].b[a]);
                     }
 #pragma unroll
                     // A digit a against up to four B digits c0 .. c0 + w - 1 in

@@ -69,12 +69,22 @@ __device__ int sturm_count(const double *a, const double *b, int k, double x) {
     return c;
 }
 
-// eigenvalue number `idx` (0-based, ascending) of T by bisection in [lo, hi]
+// eigenvalue number `idx` (0-based, ascending) of T in [lo, hi] by 32-point
+// multisection over the warp (every lane calls it): each round lane l counts
+// the eigenvalues below lo + (hi - lo)(l + 1)/33, and the interval shrinks to
+// the two neighbouring points that bracket eigenvalue idx (33x per round).
 __device__ double tri_eig(const double *a, const double *b, int k, int idx, double lo, double hi) {
-    for (int it = 0; it < 200 && hi - lo > 1e-13 * fmax(1.0, fabs(lo) + fabs(hi)); ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (sturm_count(a, b, k, mid) > idx) hi = mid;
-        else lo = mid;
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < 12; ++r) {
+        const double w = hi - lo;
+        if (!(w > 1e-13 * fmax(1.0, fabs(lo) + fabs(hi)))) break;
+        const double x = lo + w * static_cast<double>(lane + 1) / 33.0;
+        const unsigned above = __ballot_sync(0xffffffffu, sturm_count(a, b, k, x) > idx);
+        const int f = above ? __ffs(above) - 1 : 32;  // first point above the eigenvalue
+        const double nlo = lo + w * static_cast<double>(f) / 33.0;
+        const double nhi = (f < 32) ? lo + w * static_cast<double>(f + 1) / 33.0 : hi;
+        lo = nlo;
+        hi = nhi;
     }
     return 0.5 * (lo + hi);
 }
@@ -102,10 +112,15 @@ __device__ double tri_last_comp(const double *a, const double *b, int k, double 
 
 }  // namespace
 
-// v = fixed pseudo-random unit vector, v_prev = 0 (one block of 1024 threads)
-__global__ void k_lanczos_start(const MmaProb *probs, int prob) {
-    const MmaProb &pr = probs[prob];
+// Every kernel below serves the problems k0 + b of the table (b = the block
+// index named in each) that estimate their bounds (lz_on); the others return.
+
+// v = fixed pseudo-random unit vector, v_prev = 0 (one block of 1024 threads
+// per problem, blockIdx.x)
+__global__ void k_lanczos_start(const MmaProb *probs, int k0) {
+    const MmaProb &pr = probs[k0 + blockIdx.x];
     SolveState *st = pr.st;
+    if (!st->lz_on) return;
     const int n = pr.n;
     double *vp = pr.lzv, *v = pr.lzv + n;
     __shared__ double sh[1024];
@@ -126,51 +141,69 @@ __global__ void k_lanczos_start(const MmaProb *probs, int prob) {
     }
 }
 
-// w = H v, one warp per row; per-block partial of w . v in the partial slots
-__global__ void k_lanczos_matvec(const MmaProb *probs, int prob) {
-    const MmaProb &pr = probs[prob];
+// w = H v, one warp per row (kLzThreads / 32 rows per block, kLzBlocks blocks
+// per problem, blockIdx.y); per-block partial of w . v in the partial slots.
+// The row is read as 16-byte pairs (after one peeled element when the row
+// starts off a 16-byte boundary), four pairs per lane in flight, so that the
+// 128 to 2048 rows an SM holds keep enough loads outstanding to stream H at
+// HBM speed; v is read through L1.
+__global__ void __launch_bounds__(kLzThreads) k_lanczos_matvec(const MmaProb *probs, int k0) {
+    const MmaProb &pr = probs[k0 + blockIdx.y];
     const SolveState *st = pr.st;
+    if (!st->lz_on || st->lz_k < 0) return;  // no estimate, or the recurrence stopped early
     const int n = pr.n;
-    if (st->lz_k < 0) return;  // the recurrence stopped early
     const double *v = pr.lzv + n;
     double *w = pr.lzv + 2 * static_cast<size_t>(n);
+    constexpr int kWarps = kLzThreads / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double part = 0.0;
-    for (int row = blockIdx.x * 8 + wid; row < n; row += gridDim.x * 8) {
+    for (int row = blockIdx.x * kWarps + wid; row < n; row += gridDim.x * kWarps) {
         const double *h = pr.H + static_cast<size_t>(row) * pr.ldh;
-        // four independent partial sums keep four row loads in flight per lane
+        const int j0 = (reinterpret_cast<uintptr_t>(h) & 15u) ? 1 : 0;
+        const int m = (n - j0) >> 1;  // 16-byte pairs
+        const double2 *h2 = reinterpret_cast<const double2 *>(h + j0);
+        const double *vj = v + j0;
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int j = lane;
-        for (; j + 96 < n; j += 128) {
-            s0 = fma(h[j], v[j], s0);
-            s1 = fma(h[j + 32], v[j + 32], s1);
-            s2 = fma(h[j + 64], v[j + 64], s2);
-            s3 = fma(h[j + 96], v[j + 96], s3);
+        int k = lane;
+        for (; k + 96 < m; k += 128) {
+            const double2 a0 = h2[k], a1 = h2[k + 32], a2 = h2[k + 64], a3 = h2[k + 96];
+            s0 = fma(a0.x, vj[2 * k], fma(a0.y, vj[2 * k + 1], s0));
+            s1 = fma(a1.x, vj[2 * k + 64], fma(a1.y, vj[2 * k + 65], s1));
+            s2 = fma(a2.x, vj[2 * k + 128], fma(a2.y, vj[2 * k + 129], s2));
+            s3 = fma(a3.x, vj[2 * k + 192], fma(a3.y, vj[2 * k + 193], s3));
         }
-        for (; j < n; j += 32) s0 = fma(h[j], v[j], s0);
-        double s = warp_sum((s0 + s1) + (s2 + s3));
+        for (; k < m; k += 32) {
+            const double2 a0 = h2[k];
+            s0 = fma(a0.x, vj[2 * k], fma(a0.y, vj[2 * k + 1], s0));
+        }
+        if (lane == 0) {
+            if (j0) s1 = fma(h[0], v[0], s1);
+            if ((n - j0) & 1) s2 = fma(h[n - 1], v[n - 1], s2);
+        }
+        const double s = warp_sum((s0 + s1) + (s2 + s3));
         if (lane == 0) {
             w[row] = s;
             part = fma(s, v[row], part);
         }
     }
-    __shared__ double red[8];
+    __shared__ double red[kWarps];
     if (lane == 0) red[wid] = part;
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0;
-        for (int k = 0; k < 8; ++k) a += red[k];
+        for (int q = 0; q < kWarps; ++q) a += red[q];
         pr.part[static_cast<size_t>(blockIdx.x) * kPartStride] = a;
     }
 }
 
 // alpha_j = w . v; w' = w - alpha_j v - beta_j v_prev; beta_{j+1} = ||w'||;
-// v_prev <- v, v <- w' / beta_{j+1} (one block of 1024 threads)
-__global__ void k_lanczos_update(const MmaProb *probs, int prob, int j) {
-    const MmaProb &pr = probs[prob];
+// v_prev <- v, v <- w' / beta_{j+1} (one block of 1024 threads per problem,
+// blockIdx.x)
+__global__ void k_lanczos_update(const MmaProb *probs, int k0, int j) {
+    const MmaProb &pr = probs[k0 + blockIdx.x];
     SolveState *st = pr.st;
+    if (!st->lz_on || st->lz_k < 0) return;
     const int n = pr.n;
-    if (st->lz_k < 0) return;
     double *vp = pr.lzv, *v = pr.lzv + n, *w = pr.lzv + 2 * static_cast<size_t>(n);
     __shared__ double sh[1024];
     double a = 0.0;
@@ -197,16 +230,21 @@ __global__ void k_lanczos_update(const MmaProb *probs, int prob, int j) {
     }
 }
 
-// bounds from the tridiagonal, then the X0 preparation (one thread)
-__global__ void k_bounds_finish(const MmaProb *probs, int prob, double narrow) {
-    const MmaProb &pr = probs[prob];
+// bounds from the tridiagonal, then the X0 preparation (one thread per
+// problem, blockIdx.x)
+__global__ void k_bounds_finish(const MmaProb *probs, int k0, double narrow) {
+    const MmaProb &pr = probs[k0 + blockIdx.x];
     SolveState *st = pr.st;
-    if (threadIdx.x != 0) return;
+    if (!st->lz_on) return;
+    const int lane = threadIdx.x & 31;
     const int k = st->lz_k < 0 ? -st->lz_k : st->lz_k;
     const double glo = st->gersh_lo, ghi = st->gersh_hi;
+    __shared__ double a[kLanczosSteps], b[kLanczosSteps + 1];  // b[i] couples i-1 and i, b[k] the residual
+    if (lane < kLanczosSteps) a[lane] = st->lz_a[lane];
+    if (lane <= kLanczosSteps) b[lane] = st->lz_b[lane];
+    __syncwarp();
     double lo = glo, hi = ghi;
     if (k >= 2) {
-        const double *a = st->lz_a, *b = st->lz_b;  // b[i] couples i-1 and i, b[k] the residual
         const double tmin = tri_eig(a, b, k, 0, glo, ghi);
         const double tmax = tri_eig(a, b, k, k - 1, glo, ghi);
         const double rmin = b[k] * tri_last_comp(a, b, k, tmin);
@@ -218,6 +256,7 @@ __global__ void k_bounds_finish(const MmaProb *probs, int prob, double narrow) {
             hi = ghi;
         }
     }
+    if (lane != 0) return;
     if (narrow < 1.0) {
         const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo) * narrow;
         lo = mid - half;
@@ -230,11 +269,12 @@ __global__ void k_bounds_finish(const MmaProb *probs, int prob, double narrow) {
     setup_from_bounds(pr, st, lo, hi);
 }
 
-// Certified bounds from the check steps, then the X0 preparation (one thread)
-__global__ void k_check_bounds(const MmaProb *probs, int prob) {
-    const MmaProb &pr = probs[prob];
+// Certified bounds from the check steps, then the X0 preparation (one thread
+// per problem, blockIdx.x)
+__global__ void k_check_bounds(const MmaProb *probs, int k0) {
+    const MmaProb &pr = probs[k0 + blockIdx.x];
     SolveState *st = pr.st;
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0 || !st->lz_on) return;
     const double mid = 0.5 * (st->lz_lo + st->lz_hi), half = 0.5 * (st->lz_hi - st->lz_lo);
     const double a = st->chk_amax;
     double lo = st->gersh_lo, hi = st->gersh_hi;

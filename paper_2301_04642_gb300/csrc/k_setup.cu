@@ -23,14 +23,26 @@ __global__ void k_bounds_rows(const MmaProb *probs, int prob, RowInfo *rowinfo, 
     const double *h = pr.H + static_cast<long long>(row) * pr.ldh;
     double s = 0.0, mx = 0.0;
     int nonfinite = 0;
-    for (int j = lane; j < pr.n; j += 32) {
+    // four loads per lane in flight: the 128 to 2048 rows an SM holds must
+    // keep enough bytes outstanding to stream Hp at HBM speed
+    int j = lane;
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (; j + 96 < pr.n; j += 128) {
+        const double v0 = h[j], v1 = h[j + 32], v2 = h[j + 64], v3 = h[j + 96];
+        if (!(isfinite(v0) && isfinite(v1) && isfinite(v2) && isfinite(v3))) nonfinite = 1;
+        s += fabs(v0);
+        s1 += fabs(v1);
+        s2 += fabs(v2);
+        s3 += fabs(v3);
+        mx = fmax(fmax(mx, fabs(v0)), fmax(fabs(v1), fmax(fabs(v2), fabs(v3))));
+    }
+    for (; j < pr.n; j += 32) {
         const double v = h[j];
         if (!isfinite(v)) nonfinite = 1;
-        const double a = fabs(v);
-        s += a;
-        mx = fmax(mx, a);
+        s += fabs(v);
+        mx = fmax(mx, fabs(v));
     }
-    s = warp_sum(s);
+    s = warp_sum((s + s1) + (s2 + s3));
     mx = warp_max(mx);
     nonfinite = __any_sync(0xffffffffu, nonfinite);
     if (lane == 0) {
@@ -93,11 +105,10 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
     const double hb0 = 0.5 * st->beta0, mu0 = st->mu_t;
     const float sz = st->scl[kMatZ];
     double tr = 0.0, sq = 0.0, mx = 0.0;
-    const long long total = static_cast<long long>(n) * n;
-    for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(e / n);
-        const int j = static_cast<int>(e - static_cast<long long>(i) * n);
+    // block b takes rows b, b + grid, ...; thread t columns t, t + blockDim, ...
+    for (int i = blockIdx.x; i < n; i += gridDim.x)
+#pragma unroll 4
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const double h = pr.H[static_cast<long long>(i) * pr.ldh + j];
         if (fermi) {
             // z0~ = (beta0 / 2)(H - mu0 I); its identity part is 0
@@ -167,11 +178,10 @@ __global__ void k_finalize(const MmaProb *probs, int prob, double *D, long long 
     // tr D = N_e.  It is the first-order change of D for mu -> mu + gamma/beta.
     const double gamma = (fermi && st->tr_q > 0.0) ? (st->ne - st->tr_d0) / st->tr_q : 0.0;
     double tr = 0.0, eb = 0.0;
-    const long long total = static_cast<long long>(n) * n;
-    for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(e / n);
-        const int j = static_cast<int>(e - static_cast<long long>(i) * n);
+    // block b takes rows b, b + grid, ...; thread t columns t, t + blockDim, ...
+    for (int i = blockIdx.x; i < n; i += gridDim.x)
+#pragma unroll 4
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
         double d;
         if (fermi) {
             const long long at = static_cast<long long>(i) * pr.ldx + j;

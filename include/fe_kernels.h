@@ -72,6 +72,11 @@ FE_API int fe_k_digit_square(fe_ctx *ctx, const double *X, int64_t n, int64_t ld
  * [6] ms in all tensor-core step launches, [7] their count. */
 FE_API int fe_k_profile(fe_ctx *ctx, int enable);
 FE_API int fe_k_profile_read(fe_ctx *ctx, double *out8);
+/* Per step of the last profiled solve: ms of its tensor-core step launch
+ * (out, HOST, up to max_steps values; *count = values written).  Steps run in
+ * phase order, so with fe_result's iters_by_phase the first iters_by_phase[0]
+ * values are single-FP16 products and the next iters_by_phase[1] split ones. */
+FE_API int fe_k_profile_steps(fe_ctx *ctx, double *out, int max_steps, int *count);
 
 /* Test hook (no counterpart in the paper): every following solve on ctx,
  * blocking or submitted, shrinks its Lanczos estimate of the spectral bounds

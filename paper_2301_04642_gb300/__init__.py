@@ -78,13 +78,14 @@ def load(build=True):
     L.fe_k_profile.argtypes = [P, ctypes.c_int]
     L.fe_k_narrow_bounds.argtypes = [P, dbl]
     L.fe_k_phase_ms.argtypes = [P, ctypes.POINTER(dbl)]
+    L.fe_k_profile_steps.argtypes = [P, ctypes.POINTER(dbl), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.fe_k_profile_read.argtypes = [P, ctypes.POINTER(dbl)]
     L.fe_k_launch_count.argtypes = [P, ctypes.POINTER(i64)]
     L.fe_k_history.argtypes = [P, ctypes.c_int, ctypes.POINTER(dbl), ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int)]
     for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
                  "fe_k_gershgorin", "fe_k_gershgorin_noalloc", "fe_k_sym_square", "fe_k_digit_square",
-                 "fe_k_profile", "fe_k_profile_read", "fe_k_narrow_bounds", "fe_k_phase_ms",
+                 "fe_k_profile", "fe_k_profile_read", "fe_k_narrow_bounds", "fe_k_phase_ms", "fe_k_profile_steps",
                  "fe_k_launch_count", "fe_k_history"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -309,6 +310,13 @@ class Context:
         rc = self.L.fe_k_narrow_bounds(self.h, float(factor))
         if rc != FE_OK:
             raise FeError(rc, self.last_error())
+
+    def profile_steps(self, max_steps=400):
+        """ms of each step's tensor-core launch in the last profiled solve."""
+        out = (ctypes.c_double * max_steps)()
+        cnt = ctypes.c_int()
+        self.L.fe_k_profile_steps(self.h, out, int(max_steps), ctypes.byref(cnt))
+        return list(out[: cnt.value])
 
     def phase_ms(self):
         """Device time of the last blocking solve by phase (CUDA events)."""

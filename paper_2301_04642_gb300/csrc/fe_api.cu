@@ -141,6 +141,7 @@ struct fe_ctx {
     bool prof = false;
     std::vector<cudaEvent_t> pev;
     double prof_out[8] = {};
+    std::vector<double> prof_steps;  // tensor-core launch ms of each step of the last profiled solve
     std::atomic<long long> launches{0};  // kernels launched by this context
     std::atomic<double> lz_narrow{1.0};  // test hook: scale of the estimated bound interval
     double phase_ms[4] = {};             // last blocking solve: set-up, step loop, output; steps
@@ -998,10 +999,12 @@ int run_problems_once(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) 
             fp_active = std::max(fp_active, st.method == kMethodFermi ? 0 : st.it_phase[2]);
         }
         double tc_ms = 0, fp_ms = 0, tc_all = 0;
+        ctx->prof_steps.assign(nloop, 0.0);
         for (int it = 0; it < nloop; ++it) {
             float a = 0, b = 0;
             cudaEventElapsedTime(&a, ctx->pev[4 * it + 0], ctx->pev[4 * it + 1]);
             cudaEventElapsedTime(&b, ctx->pev[4 * it + 2], ctx->pev[4 * it + 3]);
+            ctx->prof_steps[it] = a;
             tc_all += a;
             if (it < tc_active) tc_ms += a;
             if (it >= tc_active && it < tc_active + fp_active) fp_ms += b;
@@ -1609,6 +1612,15 @@ extern "C" int fe_k_narrow_bounds(fe_ctx *ctx, double factor) {
     if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
     if (!(factor > 0.0 && factor <= 1.0)) return set_err(ctx, FE_EINVAL, "factor must be in (0, 1]");
     ctx->lz_narrow.store(factor, std::memory_order_relaxed);
+    return FE_OK;
+}
+
+extern "C" int fe_k_profile_steps(fe_ctx *ctx, double *out, int max_steps, int *count) {
+    if (!ctx || !out || !count || max_steps < 0) return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    const int m = std::min(max_steps, static_cast<int>(ctx->prof_steps.size()));
+    for (int i = 0; i < m; ++i) out[i] = ctx->prof_steps[i];
+    *count = m;
     return FE_OK;
 }
 

@@ -69,7 +69,7 @@ enum DevErr : int {
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;
 
 constexpr int kHistRows = 160;  // per-step history kept in the solve state
-constexpr int kLanczosSteps = 16;   // Lanczos steps of the spectral-bound estimate
+constexpr int kLanczosSteps = 12;   // Lanczos steps of the spectral-bound estimate
 constexpr int kCheckSteps = 3;      // logistic steps certifying the estimate (T_8)
 constexpr int kStatusEscaped = -100;  // internal: an eigenvalue left [0, 1] (bounds too tight)
 constexpr int kHistCols = 6;

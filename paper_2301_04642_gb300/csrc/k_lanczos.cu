@@ -56,15 +56,18 @@ __device__ __forceinline__ double block_sum_1024(double v, double *sh) {
     return r;
 }
 
-// number of eigenvalues of the tridiagonal (a, b) below x (Sturm sequence)
-__device__ int sturm_count(const double *a, const double *b, int k, double x) {
+// number of eigenvalues of the tridiagonal (a, b) below x (Sturm sequence),
+// in FP32 with the squared couplings b2[i] = b[i]^2 (GB300 runs FP64 at 1/64
+// of the FP32 rate; the estimate needs no more than FP32 precision, since the
+// certificate that follows decides the bounds)
+__device__ int sturm_count_f(const float *a, const float *b2, int k, float x) {
     int c = 0;
-    double q = a[0] - x;
-    if (q < 0.0) ++c;
+    float q = a[0] - x;
+    if (q < 0.0f) ++c;
     for (int i = 1; i < k; ++i) {
-        if (q == 0.0) q = 1e-300;
-        q = a[i] - x - b[i] * b[i] / q;
-        if (q < 0.0) ++c;
+        if (q == 0.0f) q = 1e-30f;
+        q = a[i] - x - b2[i] / q;
+        if (q < 0.0f) ++c;
     }
     return c;
 }
@@ -72,14 +75,15 @@ __device__ int sturm_count(const double *a, const double *b, int k, double x) {
 // eigenvalue number `idx` (0-based, ascending) of T in [lo, hi] by 32-point
 // multisection over the warp (every lane calls it): each round lane l counts
 // the eigenvalues below lo + (hi - lo)(l + 1)/33, and the interval shrinks to
-// the two neighbouring points that bracket eigenvalue idx (33x per round).
-__device__ double tri_eig(const double *a, const double *b, int k, int idx, double lo, double hi) {
+// the two neighbouring points that bracket eigenvalue idx (33x per round),
+// down to FP32 resolution.
+__device__ double tri_eig(const float *a, const float *b2, int k, int idx, double lo, double hi) {
     const int lane = threadIdx.x & 31;
-    for (int r = 0; r < 12; ++r) {
+    for (int r = 0; r < 8; ++r) {
         const double w = hi - lo;
-        if (!(w > 1e-13 * fmax(1.0, fabs(lo) + fabs(hi)))) break;
+        if (!(w > 3e-7 * fmax(fabs(lo), fabs(hi)))) break;
         const double x = lo + w * static_cast<double>(lane + 1) / 33.0;
-        const unsigned above = __ballot_sync(0xffffffffu, sturm_count(a, b, k, x) > idx);
+        const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f(a, b2, k, static_cast<float>(x)) > idx);
         const int f = above ? __ffs(above) - 1 : 32;  // first point above the eigenvalue
         const double nlo = lo + w * static_cast<double>(f) / 33.0;
         const double nhi = (f < 32) ? lo + w * static_cast<double>(f + 1) / 33.0 : hi;
@@ -240,13 +244,20 @@ __global__ void k_bounds_finish(const MmaProb *probs, int k0, double narrow) {
     const int k = st->lz_k < 0 ? -st->lz_k : st->lz_k;
     const double glo = st->gersh_lo, ghi = st->gersh_hi;
     __shared__ double a[kLanczosSteps], b[kLanczosSteps + 1];  // b[i] couples i-1 and i, b[k] the residual
-    if (lane < kLanczosSteps) a[lane] = st->lz_a[lane];
-    if (lane <= kLanczosSteps) b[lane] = st->lz_b[lane];
+    __shared__ float af[kLanczosSteps], b2f[kLanczosSteps + 1];
+    if (lane < kLanczosSteps) {
+        a[lane] = st->lz_a[lane];
+        af[lane] = static_cast<float>(a[lane]);
+    }
+    if (lane <= kLanczosSteps) {
+        b[lane] = st->lz_b[lane];
+        b2f[lane] = static_cast<float>(b[lane] * b[lane]);
+    }
     __syncwarp();
     double lo = glo, hi = ghi;
     if (k >= 2) {
-        const double tmin = tri_eig(a, b, k, 0, glo, ghi);
-        const double tmax = tri_eig(a, b, k, k - 1, glo, ghi);
+        const double tmin = tri_eig(af, b2f, k, 0, glo, ghi);
+        const double tmax = tri_eig(af, b2f, k, k - 1, glo, ghi);
         const double rmin = b[k] * tri_last_comp(a, b, k, tmin);
         const double rmax = b[k] * tri_last_comp(a, b, k, tmax);
         lo = fmax(glo, tmin - rmin);

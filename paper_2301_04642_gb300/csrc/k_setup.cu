@@ -21,29 +21,39 @@ __global__ void k_bounds_rows(const MmaProb *probs, int prob, RowInfo *rowinfo, 
     const int lane = threadIdx.x & 31;
     if (row >= pr.n) return;
     const double *h = pr.H + static_cast<long long>(row) * pr.ldh;
-    double s = 0.0, mx = 0.0;
-    int nonfinite = 0;
+    // |h| and the NaN/Inf test work on the bit patterns (for non-negative
+    // doubles their order as integers is their order as values): the one
+    // FP64 operation per element is the row sum (GB300 runs FP64 at 1/64 of
+    // the FP32 rate)
+    constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull, kExp = 0x7FF0000000000000ull;
+    double s = 0.0;
+    unsigned long long mxb = 0, nonfin = 0;
     // four loads per lane in flight: the 128 to 2048 rows an SM holds must
     // keep enough bytes outstanding to stream Hp at HBM speed
     int j = lane;
     double s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (; j + 96 < pr.n; j += 128) {
-        const double v0 = h[j], v1 = h[j + 32], v2 = h[j + 64], v3 = h[j + 96];
-        if (!(isfinite(v0) && isfinite(v1) && isfinite(v2) && isfinite(v3))) nonfinite = 1;
-        s += fabs(v0);
-        s1 += fabs(v1);
-        s2 += fabs(v2);
-        s3 += fabs(v3);
-        mx = fmax(fmax(mx, fabs(v0)), fmax(fabs(v1), fmax(fabs(v2), fabs(v3))));
+        const unsigned long long b0 = static_cast<unsigned long long>(__double_as_longlong(h[j])) & kAbs;
+        const unsigned long long b1 = static_cast<unsigned long long>(__double_as_longlong(h[j + 32])) & kAbs;
+        const unsigned long long b2 = static_cast<unsigned long long>(__double_as_longlong(h[j + 64])) & kAbs;
+        const unsigned long long b3 = static_cast<unsigned long long>(__double_as_longlong(h[j + 96])) & kAbs;
+        nonfin |= ((b0 & kExp) == kExp) | ((b1 & kExp) == kExp) | ((b2 & kExp) == kExp) | ((b3 & kExp) == kExp);
+        s += __longlong_as_double(static_cast<long long>(b0));
+        s1 += __longlong_as_double(static_cast<long long>(b1));
+        s2 += __longlong_as_double(static_cast<long long>(b2));
+        s3 += __longlong_as_double(static_cast<long long>(b3));
+        mxb = max(max(mxb, b0), max(b1, max(b2, b3)));
     }
     for (; j < pr.n; j += 32) {
-        const double v = h[j];
-        if (!isfinite(v)) nonfinite = 1;
-        s += fabs(v);
-        mx = fmax(mx, fabs(v));
+        const unsigned long long b0 = static_cast<unsigned long long>(__double_as_longlong(h[j])) & kAbs;
+        nonfin |= ((b0 & kExp) == kExp);
+        s += __longlong_as_double(static_cast<long long>(b0));
+        mxb = max(mxb, b0);
     }
     s = warp_sum((s + s1) + (s2 + s3));
-    mx = warp_max(mx);
+    for (int o = 16; o > 0; o >>= 1) mxb = max(mxb, __shfl_xor_sync(0xffffffffu, mxb, o));
+    const double mx = __longlong_as_double(static_cast<long long>(mxb));
+    int nonfinite = nonfin ? 1 : 0;
     nonfinite = __any_sync(0xffffffffu, nonfinite);
     if (lane == 0) {
         const double d = h[row];
@@ -104,63 +114,66 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
     const bool fermi = (st->method == kMethodFermi) && st->chk_left == 0;
     const double hb0 = 0.5 * st->beta0, mu0 = st->mu_t;
     const float sz = st->scl[kMatZ];
-    double tr = 0.0, sq = 0.0, mx = 0.0;
+    // FP32 arithmetic off the diagonal (GB300 runs FP64 at 1/64 of the FP32
+    // rate, and the FP32 result is what is stored); each thread's squares are
+    // summed in FP32 over its columns of one row (at most n / blockDim terms),
+    // then in FP64 across rows
+    const float inv_wf = static_cast<float>(inv_w), hb0f = static_cast<float>(hb0);
+    double tr = 0.0, sq = 0.0;
     // block b takes rows b, b + grid, ...; thread t columns t, t + blockDim, ...
-    for (int i = blockIdx.x; i < n; i += gridDim.x)
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        float sqr = 0.0f;
+        double sqd = 0.0;
 #pragma unroll 4
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double h = pr.H[static_cast<long long>(i) * pr.ldh + j];
-        if (fermi) {
-            // z0~ = (beta0 / 2)(H - mu0 I); its identity part is 0
-            const float zf = static_cast<float>(hb0 * (h - ((i == j) ? mu0 : 0.0)));
-            const MatSlot &mz = pr.mats[kMatZ];
-            mz.master[static_cast<long long>(i) * pr.ldy + j] = zf;
-            const float zs = zf * sz;
-            const __half hh = __float2half_rn(zs);
-            mz.sl[0][static_cast<long long>(i) * pr.lds + j] = hh;
-            mz.sl[1][static_cast<long long>(i) * pr.lds + j] = __float2half_rn(zs - __half2float(hh));
-            if (i == j) tr += zf;
-            sq += static_cast<double>(zf) * zf;
-        } else if (fp64) {
-            const double x = ((i == j) ? st->emax - h : -h) * inv_w;
-            pr.Xd[0][static_cast<long long>(i) * pr.ldx + j] = x;
-            if (i == j) tr += x;
-            sq += x * x;
-            mx = fmax(mx, fabs(x));
-        } else {
-            const double y = -h * inv_w + ((i == j) ? dshift : 0.0);
-            const float yf = static_cast<float>(y);
-            pr.Y[static_cast<long long>(i) * pr.ldy + j] = yf;
-            const float ys = yf * s0;
-            const __half hh = __float2half_rn(ys);
-            const MatSlot &my = pr.mats[kMatY0];
-            my.sl[0][static_cast<long long>(i) * pr.lds + j] = hh;
-            my.sl[1][static_cast<long long>(i) * pr.lds + j] = __float2half_rn(ys - __half2float(hh));
-            if (i == j) tr += yf;
-            sq += static_cast<double>(yf) * yf;
-            mx = fmax(mx, fabs(static_cast<double>(yf)));
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const double h = pr.H[static_cast<long long>(i) * pr.ldh + j];
+            if (fermi) {
+                // z0~ = (beta0 / 2)(H - mu0 I); its identity part is 0
+                const float zf = (i == j) ? static_cast<float>(hb0 * (h - mu0)) : hb0f * static_cast<float>(h);
+                const MatSlot &mz = pr.mats[kMatZ];
+                mz.master[static_cast<long long>(i) * pr.ldy + j] = zf;
+                const float zs = zf * sz;
+                const __half hh = __float2half_rn(zs);
+                mz.sl[0][static_cast<long long>(i) * pr.lds + j] = hh;
+                mz.sl[1][static_cast<long long>(i) * pr.lds + j] = __float2half_rn(zs - __half2float(hh));
+                if (i == j) tr += zf;
+                sqr = fmaf(zf, zf, sqr);
+            } else if (fp64) {
+                const double x = ((i == j) ? st->emax - h : -h) * inv_w;
+                pr.Xd[0][static_cast<long long>(i) * pr.ldx + j] = x;
+                if (i == j) tr += x;
+                sqd += x * x;
+            } else {
+                const float yf = (i == j) ? static_cast<float>(-h * inv_w + dshift) : -inv_wf * static_cast<float>(h);
+                pr.Y[static_cast<long long>(i) * pr.ldy + j] = yf;
+                const float ys = yf * s0;
+                const __half hh = __float2half_rn(ys);
+                const MatSlot &my = pr.mats[kMatY0];
+                my.sl[0][static_cast<long long>(i) * pr.lds + j] = hh;
+                my.sl[1][static_cast<long long>(i) * pr.lds + j] = __float2half_rn(ys - __half2float(hh));
+                if (i == j) tr += yf;
+                sqr = fmaf(yf, yf, sqr);
+            }
         }
+        sq += static_cast<double>(sqr) + sqd;
     }
-    __shared__ double red[3][32];
+    __shared__ double red[2][32];
     tr = warp_sum(tr);
     sq = warp_sum(sq);
-    mx = warp_max(mx);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { red[0][wid] = tr; red[1][wid] = sq; red[2][wid] = mx; }
+    if (lane == 0) { red[0][wid] = tr; red[1][wid] = sq; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0, b = 0, c = 0;
+        double a = 0, b = 0;
         for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
             a += red[0][w2];
             b += red[1][w2];
-            c = fmax(c, red[2][w2]);
         }
         double *slot = pr.part + static_cast<size_t>(blockIdx.x) * kPartStride;
         slot[0] = a;
         slot[1] = b;
         slot[2] = 0.0;
         slot[3] = 0.0;
-        (void)c;
     }
 }
 

@@ -128,7 +128,9 @@ FE_API int fe_destroy(fe_ctx *ctx);
 
 /* Blocking solve of one problem.  Hp is read (copied into the pool first when
  * it is a host pointer, or when its ld is not the pool's layout); D (if not
- * NULL) is written on success.  r receives the result even on failure.
+ * NULL) is written on success: a page-locked host D (cudaHostAlloc,
+ * cudaHostRegister) by the output kernel directly, other host memory through a
+ * staging copy.  r receives the result even on failure.
  * Errors: FE_EINVAL (n < 1, ld < n, N_e out of [0, n], kT < 0, non-integral
  * N_e at kT == 0, tol < 0, NaN/Inf in Hp), FE_ENOMEM, FE_ENOTCONV,
  * FE_ETIMEOUT, FE_ECUDA. */

@@ -769,18 +769,31 @@ int eng_finish(fe_ctx *ctx, Engine &e, int k, const Job &j) {
     const fe_problem *p = j.p;
     double *dout = nullptr;
     long long ldd = p->n;
+    bool staged = false;
     if (p->D) {
         if (p->flags & FE_PTR_DEVICE) {
             dout = p->D;
             ldd = p->ld;
         } else {
-            dout = j.slot->Dtmp;
+            // page-locked host memory that the device can address: the output
+            // kernel writes D there directly (one pass over the host link, no
+            // staging buffer or separate copy); other host memory is staged
+            cudaPointerAttributes a;
+            if (cudaPointerGetAttributes(&a, p->D) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+                a.devicePointer != nullptr) {
+                dout = static_cast<double *>(a.devicePointer);
+                ldd = p->ld;
+            } else {
+                cudaGetLastError();  // a pointer CUDA does not know is not an error here
+                dout = j.slot->Dtmp;
+                staged = true;
+            }
         }
     }
     k_finalize<<<kFinBlocks, 256, 0, s>>>(e.d_probs, k, dout, ldd);
     k_finalize_reduce<<<1, 512, 0, s>>>(e.d_probs, k);
     ctx->launches += 2;
-    if (p->D && !(p->flags & FE_PTR_DEVICE))
+    if (staged)
         FE_CUDA(ctx, cudaMemcpy2DAsync(p->D, sizeof(double) * p->ld, j.slot->Dtmp,
                                        sizeof(double) * p->n, sizeof(double) * p->n, p->n,
                                        cudaMemcpyDeviceToHost, s));

@@ -547,16 +547,33 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 __half *S0 = m.sl[0], *S1 = m.sl[1];
                 const int mr = lane >> 2;        // mirrored row within the group
                 const int mc = (lane & 3) * 8;   // its first column within the strip
+                // a group takes the vector path when all of it exists and lies
+                // above the diagonal; its E1 row segment is loaded one group
+                // ahead, so the load's latency overlaps the previous group
+                auto vec_group = [&](int c) {
+                    const int jc = J * kTileM + c * 8;
+                    return i0 + 32 <= n && jc + 8 <= n && (!diag || jc >= i0 + 32);
+                };
+                float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
+                if (vec_group(0)) {
+                    const size_t r0 = static_cast<size_t>(i) * ldy + J * kTileM;
+                    pa = *reinterpret_cast<const float4 *>(E1 + r0);
+                    pb = *reinterpret_cast<const float4 *>(E1 + r0 + 4);
+                }
 #pragma unroll
                 for (int c8 = 0; c8 < kTileM / 8; ++c8) {
                     const int j0 = J * kTileM + c8 * 8;
                     if (j0 >= n) break;
+                    const float4 ea = pa, eb = pb;  // this group's E1 (when it is a vector group)
+                    if (c8 + 1 < kTileM / 8 && vec_group(c8 + 1)) {
+                        const size_t rn = static_cast<size_t>(i) * ldy + j0 + 8;
+                        pa = *reinterpret_cast<const float4 *>(E1 + rn);
+                        pb = *reinterpret_cast<const float4 *>(E1 + rn + 4);
+                    }
                     if (diag && j0 + 7 < i0) continue;
-                    const bool full = i0 + 32 <= n && j0 + 8 <= n && (!diag || j0 >= i0 + 32);
+                    const bool full = vec_group(c8);
                     if (full) {
                         const size_t ro = static_cast<size_t>(i) * ldy + j0;
-                        const float4 ea = *reinterpret_cast<const float4 *>(E1 + ro);
-                        const float4 eb = *reinterpret_cast<const float4 *>(E1 + ro + 4);
                         const float e[8] = {ea.x, ea.y, ea.z, ea.w, eb.x, eb.y, eb.z, eb.w};
                         float val[8];
                         float csq = 0.0f, crr = 0.0f;

@@ -199,3 +199,26 @@ def test_config_n16384_mixed():
     idem = math.sqrt(np.sum((Dh @ DV - DV) ** 2) / 4)
     print(r, eps1, idem)
     assert eps1 <= TOL_EPS1 and idem <= TOL_IDEM
+
+
+def test_pinned_host_output_matches_staged():
+    """A page-locked host D is written by the output kernel directly; the
+    result is the one the staged copy of a pageable D receives, bit for bit."""
+    p = hp_synth.gapped(700, 500, (-3.0, -0.01), (0.01, 1.0), 4700)
+    Dpin = torch.empty(p.n, p.n, dtype=torch.float64).pin_memory()
+    Dpin.fill_(np.nan)
+    r1 = ctx().solve(p.H, p.ne, tol=p.tol, D=Dpin.numpy())
+    D2 = np.zeros_like(p.H)
+    r2 = ctx().solve(p.H, p.ne, tol=p.tol, D=D2)
+    assert r1["status"] == 0 and r2["status"] == 0
+    assert np.array_equal(Dpin.numpy(), D2)
+    m = check_zero_t(p, D2, r2)
+    assert m["eps1"] <= TOL_EPS1 and m["tr_err"] <= TOL_TR and m["idem"] <= TOL_IDEM
+    # a row stride wider than n: only the n x n block is written
+    big = torch.full((p.n, p.n + 5), -7.0, dtype=torch.float64).pin_memory()
+    Hw = np.zeros((p.n, p.n + 5))
+    Hw[:, :p.n] = p.H
+    r3 = ctx().solve(Hw[:, :p.n], p.ne, tol=p.tol, D=big.numpy()[:, :p.n])
+    assert r3["status"] == 0
+    assert np.array_equal(big.numpy()[:, :p.n], D2)
+    assert np.all(big.numpy()[:, p.n:] == -7.0)

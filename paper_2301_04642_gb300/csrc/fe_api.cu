@@ -64,7 +64,7 @@ struct Slot {
     float *Y = nullptr;
     double *Xd[2] = {};
     double *Dtmp = nullptr;
-    double *lzv = nullptr;  // Lanczos vectors (3 n doubles)
+    float *lzv = nullptr;   // Lanczos vectors (3 n FP32)
     double *part = nullptr;
     SolveState *st = nullptr;
     RowInfo *rowinfo = nullptr;
@@ -342,7 +342,7 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
     s->Xd[0] = reinterpret_cast<double *>(take(8 * nn * ldx));
     s->Xd[1] = reinterpret_cast<double *>(take(8 * nn * ldx));
     s->Dtmp = reinterpret_cast<double *>(take(8 * nn * nn));
-    s->lzv = reinterpret_cast<double *>(take(8 * 3 * nn));
+    s->lzv = reinterpret_cast<float *>(take(4 * 3 * nn));
     __half *digs[kDigits] = {};
     if (method == kMethodSp2)
         for (int a = 0; a < kDigits; ++a) digs[a] = reinterpret_cast<__half *>(take(2 * nn * lds));

@@ -36,7 +36,7 @@ struct MmaProb {
     int n, ldy, lds, ntiles;
     int ntiles64, pad1;
     int tc_tile0, tc_ntiles;         // this problem's range in the launch's tensor-core tile list
-    double *lzv;                     // Lanczos vectors: v_prev, v, w (n doubles each)
+    float *lzv;                      // Lanczos vectors: v_prev, v, w (n FP32 each)
     float *Y;                        // FP32 master of the zero-temperature iterate
     double *Xd[2];                   // FP64 buffers (FP64 phase / finite-T output), ld ldx
     int ldx, pad0;

@@ -5,7 +5,8 @@
 // Gershgorin discs always contain the spectrum but, for a dense rotated Hp,
 // span ~20-50x its true width, which costs SP2 about 2 log2 of that ratio in
 // extra products (and the finite-temperature recursion extra doublings).
-// Here kLanczosSteps steps of the Lanczos recurrence in FP64, from a fixed
+// Here kLanczosSteps steps of the Lanczos recurrence (FP32 vectors and
+// products, FP64 sums), from a fixed
 // pseudo-random unit vector, give Ritz values theta_min, theta_max inside the
 // spectrum; the estimate is
 //     [theta_min - |beta_k s_min|, theta_max + |beta_k s_max|],
@@ -119,6 +120,25 @@ __device__ double tri_last_comp(const double *a, const double *b, int k, double 
 // Every kernel below serves the problems k0 + b of the table (b = the block
 // index named in each) that estimate their bounds (lz_on); the others return.
 
+// The recurrence runs in FP32 (vectors, H entries, products) with FP64 sums:
+// the estimate needs no more (the certificate decides the bounds), and GB300
+// runs FP64 arithmetic at 1/64 of the FP32 rate.
+
+// H_ij to FP32, rounded toward zero, by integer operations on the FP64
+// encoding (no FP64 instruction); values below FP32's normal range become 0,
+// values above it infinity (Hp was checked for NaN/Inf beforehand)
+__device__ __forceinline__ float h_to_f32(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+    const int fe = static_cast<int>((hi >> 20) & 0x7FFu) - 896;  // FP32 exponent field
+    const unsigned sign = hi & 0x80000000u;
+    unsigned r;
+    if (fe <= 0) r = sign;
+    else if (fe >= 255) r = sign | 0x7F800000u;
+    else r = sign | (static_cast<unsigned>(fe) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    return __uint_as_float(r);
+}
+
 // v = fixed pseudo-random unit vector, v_prev = 0 (one block of 1024 threads
 // per problem, blockIdx.x)
 __global__ void k_lanczos_start(const MmaProb *probs, int k0) {
@@ -126,18 +146,18 @@ __global__ void k_lanczos_start(const MmaProb *probs, int k0) {
     SolveState *st = pr.st;
     if (!st->lz_on) return;
     const int n = pr.n;
-    double *vp = pr.lzv, *v = pr.lzv + n;
+    float *vp = pr.lzv, *v = pr.lzv + n;
     __shared__ double sh[1024];
     double ss = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double x = static_cast<double>(mix64(0xF00Dull + static_cast<uint64_t>(i)) >> 11) *
-                             (2.0 / 9007199254740992.0) - 1.0;  // uniform in [-1, 1)
+        const float x = static_cast<float>(static_cast<double>(mix64(0xF00Dull + static_cast<uint64_t>(i)) >> 11) *
+                                           (2.0 / 9007199254740992.0) - 1.0);  // uniform in [-1, 1)
         v[i] = x;
-        vp[i] = 0.0;
-        ss += x * x;
+        vp[i] = 0.0f;
+        ss += static_cast<double>(x) * x;
     }
     const double nrm = sqrt(block_sum_1024(ss, sh));
-    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    const float inv = nrm > 0.0 ? static_cast<float>(1.0 / nrm) : 0.0f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] *= inv;
     if (threadIdx.x == 0) {
         st->lz_k = 0;
@@ -149,15 +169,15 @@ __global__ void k_lanczos_start(const MmaProb *probs, int k0) {
 // per problem, blockIdx.y); per-block partial of w . v in the partial slots.
 // The row is read as 16-byte pairs (after one peeled element when the row
 // starts off a 16-byte boundary), four pairs per lane in flight, so that the
-// 128 to 2048 rows an SM holds keep enough loads outstanding to stream H at
-// HBM speed; v is read through L1.
+// rows an SM holds keep enough loads outstanding to stream H at HBM speed;
+// v is read through L1.
 __global__ void __launch_bounds__(kLzThreads) k_lanczos_matvec(const MmaProb *probs, int k0) {
     const MmaProb &pr = probs[k0 + blockIdx.y];
     const SolveState *st = pr.st;
     if (!st->lz_on || st->lz_k < 0) return;  // no estimate, or the recurrence stopped early
     const int n = pr.n;
-    const double *v = pr.lzv + n;
-    double *w = pr.lzv + 2 * static_cast<size_t>(n);
+    const float *v = pr.lzv + n;
+    float *w = pr.lzv + 2 * static_cast<size_t>(n);
     constexpr int kWarps = kLzThreads / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double part = 0.0;
@@ -166,28 +186,28 @@ __global__ void __launch_bounds__(kLzThreads) k_lanczos_matvec(const MmaProb *pr
         const int j0 = (reinterpret_cast<uintptr_t>(h) & 15u) ? 1 : 0;
         const int m = (n - j0) >> 1;  // 16-byte pairs
         const double2 *h2 = reinterpret_cast<const double2 *>(h + j0);
-        const double *vj = v + j0;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        const float *vj = v + j0;
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
         int k = lane;
         for (; k + 96 < m; k += 128) {
             const double2 a0 = h2[k], a1 = h2[k + 32], a2 = h2[k + 64], a3 = h2[k + 96];
-            s0 = fma(a0.x, vj[2 * k], fma(a0.y, vj[2 * k + 1], s0));
-            s1 = fma(a1.x, vj[2 * k + 64], fma(a1.y, vj[2 * k + 65], s1));
-            s2 = fma(a2.x, vj[2 * k + 128], fma(a2.y, vj[2 * k + 129], s2));
-            s3 = fma(a3.x, vj[2 * k + 192], fma(a3.y, vj[2 * k + 193], s3));
+            s0 = fmaf(h_to_f32(a0.x), vj[2 * k], fmaf(h_to_f32(a0.y), vj[2 * k + 1], s0));
+            s1 = fmaf(h_to_f32(a1.x), vj[2 * k + 64], fmaf(h_to_f32(a1.y), vj[2 * k + 65], s1));
+            s2 = fmaf(h_to_f32(a2.x), vj[2 * k + 128], fmaf(h_to_f32(a2.y), vj[2 * k + 129], s2));
+            s3 = fmaf(h_to_f32(a3.x), vj[2 * k + 192], fmaf(h_to_f32(a3.y), vj[2 * k + 193], s3));
         }
         for (; k < m; k += 32) {
             const double2 a0 = h2[k];
-            s0 = fma(a0.x, vj[2 * k], fma(a0.y, vj[2 * k + 1], s0));
+            s0 = fmaf(h_to_f32(a0.x), vj[2 * k], fmaf(h_to_f32(a0.y), vj[2 * k + 1], s0));
         }
         if (lane == 0) {
-            if (j0) s1 = fma(h[0], v[0], s1);
-            if ((n - j0) & 1) s2 = fma(h[n - 1], v[n - 1], s2);
+            if (j0) s1 = fmaf(h_to_f32(h[0]), v[0], s1);
+            if ((n - j0) & 1) s2 = fmaf(h_to_f32(h[n - 1]), v[n - 1], s2);
         }
-        const double s = warp_sum((s0 + s1) + (s2 + s3));
+        const double s = warp_sum(static_cast<double>((s0 + s1) + (s2 + s3)));
         if (lane == 0) {
-            w[row] = s;
-            part = fma(s, v[row], part);
+            w[row] = static_cast<float>(s);
+            part += s * static_cast<double>(v[row]);
         }
     }
     __shared__ double red[kWarps];
@@ -208,21 +228,22 @@ __global__ void k_lanczos_update(const MmaProb *probs, int k0, int j) {
     SolveState *st = pr.st;
     if (!st->lz_on || st->lz_k < 0) return;
     const int n = pr.n;
-    double *vp = pr.lzv, *v = pr.lzv + n, *w = pr.lzv + 2 * static_cast<size_t>(n);
+    float *vp = pr.lzv, *v = pr.lzv + n, *w = pr.lzv + 2 * static_cast<size_t>(n);
     __shared__ double sh[1024];
     double a = 0.0;
     for (int b = threadIdx.x; b < kLzBlocks; b += blockDim.x) a += pr.part[static_cast<size_t>(b) * kPartStride];
     const double alpha = block_sum_1024(a, sh);
     const double beta = st->lz_b[j];
-    double ss = 0.0;
+    const float af = static_cast<float>(alpha), bf = static_cast<float>(beta);
+    float ssf = 0.0f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double x = w[i] - alpha * v[i] - beta * vp[i];
+        const float x = fmaf(-af, v[i], fmaf(-bf, vp[i], w[i]));
         w[i] = x;
-        ss += x * x;
+        ssf = fmaf(x, x, ssf);
     }
-    const double bn = sqrt(block_sum_1024(ss, sh));
-    const bool stop = !(bn > 1e-12 * fmax(fabs(alpha), 1e-300));  // invariant subspace found
-    const double inv = stop ? 0.0 : 1.0 / bn;
+    const double bn = sqrt(block_sum_1024(static_cast<double>(ssf), sh));
+    const bool stop = !(bn > 1e-6 * fmax(fabs(alpha), 1e-300));  // invariant subspace (to FP32 accuracy)
+    const float inv = stop ? 0.0f : static_cast<float>(1.0 / bn);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         vp[i] = v[i];
         v[i] = w[i] * inv;

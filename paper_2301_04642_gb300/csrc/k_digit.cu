@@ -103,23 +103,61 @@ __device__ __forceinline__ long long fixed54(double x) {
 
 }  // namespace
 
+// round(y 2^54) for an FP32 y, by integer operations on its encoding: the
+// same value fixed54 gives for the (exact) FP64 widening of y
+__device__ __forceinline__ long long fixed54_f(float y) {
+    constexpr long long kLim = 35668509048774328LL;  // 1.98 * 2^54
+    const unsigned bits = __float_as_uint(y);
+    const int e = static_cast<int>((bits >> 23) & 0xFFu);
+    const long long m = static_cast<long long>((bits & 0x7FFFFFu) | 0x800000u);  // |y| = m 2^(e - 150)
+    const int sh = e - 96;                                                        // |y| 2^54 = m 2^sh
+    long long v;
+    if (e == 0) v = 0;                  // zero or subnormal (below 2^-126)
+    else if (sh > 31) v = kLim;         // |y| >= 2^9, Inf, NaN
+    else if (sh >= 0) v = m << sh;
+    else if (sh > -25) v = (m + (1LL << (-sh - 1))) >> (-sh);  // round half away from zero
+    else v = 0;
+    v = v > kLim ? kLim : v;
+    return (bits >> 31) ? -v : v;
+}
+
+// balanced base-256 digits of V (least significant first), two elements at a time
+__device__ __forceinline__ void put_digits2(const MmaProb &pr, size_t at, long long V0, long long V1) {
+#pragma unroll
+    for (int a = kDigits - 1; a >= 0; --a) {
+        const long long d0 = ((V0 + 128) & 255) - 128, d1 = ((V1 + 128) & 255) - 128;
+        *reinterpret_cast<__half2 *>(pr.dig[a] + at) =
+            __halves2half2(__int2half_rn(static_cast<int>(d0)), __int2half_rn(static_cast<int>(d1)));
+        V0 = (V0 - d0) >> 8;
+        V1 = (V1 - d1) >> 8;
+    }
+}
+
 __global__ void k_digit_prep(const MmaProb *probs, int nprobs) {
     for (int p = 0; p < nprobs; ++p) {
         const MmaProb &pr = probs[p];
         const SolveState *st = pr.st;
         if (step_kind(st) != kDigit) continue;
         const int n = pr.n;
+        const bool xf = st->x_fp64 != 0;
+        // V = round(X/4 * 2^56) = round(x 2^54), two adjacent columns per
+        // thread (lds is even: one 4-byte store per digit array); off the
+        // diagonal the FP32 iterate c I + Y is just Y, converted without FP64
+        // arithmetic, and the diagonal takes the FP64 sum y + c
         for (int i = blockIdx.x; i < n; i += gridDim.x) {
-            for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                // V = round(X/4 * 2^56)
-                long long V = fixed54(x_at(pr, st, i, j));
-                const size_t at = static_cast<size_t>(i) * pr.lds + j;
-#pragma unroll
-                for (int a = kDigits - 1; a >= 0; --a) {
-                    const long long d = ((V + 128) & 255) - 128;
-                    pr.dig[a][at] = __int2half_rn(static_cast<int>(d));
-                    V = (V - d) >> 8;
+            for (int j = 2 * threadIdx.x; j < n; j += 2 * blockDim.x) {
+                const bool two = j + 1 < n;
+                long long V0, V1 = 0;
+                if (xf) {
+                    const double *X = pr.Xd[st->xcur] + static_cast<size_t>(i) * pr.ldx;
+                    V0 = fixed54(X[j]);
+                    if (two) V1 = fixed54(X[j + 1]);
+                } else {
+                    const float2 y2 = *reinterpret_cast<const float2 *>(pr.Y + static_cast<size_t>(i) * pr.ldy + j);
+                    V0 = (i == j) ? fixed54(static_cast<double>(y2.x) + st->c) : fixed54_f(y2.x);
+                    if (two) V1 = (i == j + 1) ? fixed54(static_cast<double>(y2.y) + st->c) : fixed54_f(y2.y);
                 }
+                put_digits2(pr, static_cast<size_t>(i) * pr.lds + j, V0, V1);
             }
         }
     }

@@ -464,6 +464,7 @@ def bench_batch(args, torch, fe):
         torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1)
     launches = ctx.launch_count() - l0
+    phases = ctx.phase_ms()  # the last timed batch: set-up, step loop, output
     ctx.profile(True)
     one()
     kern = _kernel_times(ctx, sizes)
@@ -478,6 +479,7 @@ def bench_batch(args, torch, fe):
                       "l2": "256 MiB buffer written before every step"},
            "effective_tflops": products * args.steps / (t_ms / 1e3) / 1e12,
            "max_trace_err": max(abs(r["trace"] - p.ne) for r, p in zip(res, probs)),
+           "phases_ms": phases,
            "gpu_launches": launches, "kernels": kern, "clocks": clk.summary(), "cpu_baseline": None}
     print(json.dumps(out), flush=True)
     ctx.close()

@@ -120,40 +120,72 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
     // then in FP64 across rows
     const float inv_wf = static_cast<float>(inv_w), hb0f = static_cast<float>(hb0);
     double tr = 0.0, sq = 0.0;
-    // block b takes rows b, b + grid, ...; thread t columns t, t + blockDim, ...
+    // block b takes rows b, b + grid, ...; thread t the column pairs (2t, 2t + 1),
+    // (2t + 2 blockDim, ...), ...: 16-byte loads of Hp where its row is aligned,
+    // 8-byte FP32 and 4-byte FP16 stores (ldy and lds are even)
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         float sqr = 0.0f;
         double sqd = 0.0;
-#pragma unroll 4
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const double h = pr.H[static_cast<long long>(i) * pr.ldh + j];
+        const double *hrow = pr.H + static_cast<long long>(i) * pr.ldh;
+        const bool h16 = (reinterpret_cast<uintptr_t>(hrow) & 15u) == 0;
+        for (int j = 2 * threadIdx.x; j < n; j += 2 * blockDim.x) {
+            const bool two = j + 1 < n;
+            double h0, h1 = 0.0;
+            if (two && h16) {
+                const double2 hv = *reinterpret_cast<const double2 *>(hrow + j);
+                h0 = hv.x;
+                h1 = hv.y;
+            } else {
+                h0 = hrow[j];
+                if (two) h1 = hrow[j + 1];
+            }
+            if (fp64) {
+                double *xr = pr.Xd[0] + static_cast<long long>(i) * pr.ldx;
+                const double x0 = ((i == j) ? st->emax - h0 : -h0) * inv_w;
+                xr[j] = x0;
+                if (i == j) tr += x0;
+                sqd += x0 * x0;
+                if (two) {
+                    const double x1 = ((i == j + 1) ? st->emax - h1 : -h1) * inv_w;
+                    xr[j + 1] = x1;
+                    if (i == j + 1) tr += x1;
+                    sqd += x1 * x1;
+                }
+                continue;
+            }
+            float y0, y1;
+            float sc;
+            const MatSlot *ms;
             if (fermi) {
                 // z0~ = (beta0 / 2)(H - mu0 I); its identity part is 0
-                const float zf = (i == j) ? static_cast<float>(hb0 * (h - mu0)) : hb0f * static_cast<float>(h);
-                const MatSlot &mz = pr.mats[kMatZ];
-                mz.master[static_cast<long long>(i) * pr.ldy + j] = zf;
-                const float zs = zf * sz;
-                const __half hh = __float2half_rn(zs);
-                mz.sl[0][static_cast<long long>(i) * pr.lds + j] = hh;
-                mz.sl[1][static_cast<long long>(i) * pr.lds + j] = __float2half_rn(zs - __half2float(hh));
-                if (i == j) tr += zf;
-                sqr = fmaf(zf, zf, sqr);
-            } else if (fp64) {
-                const double x = ((i == j) ? st->emax - h : -h) * inv_w;
-                pr.Xd[0][static_cast<long long>(i) * pr.ldx + j] = x;
-                if (i == j) tr += x;
-                sqd += x * x;
+                y0 = (i == j) ? static_cast<float>(hb0 * (h0 - mu0)) : hb0f * static_cast<float>(h0);
+                y1 = (i == j + 1) ? static_cast<float>(hb0 * (h1 - mu0)) : hb0f * static_cast<float>(h1);
+                ms = &pr.mats[kMatZ];
+                sc = sz;
             } else {
-                const float yf = (i == j) ? static_cast<float>(-h * inv_w + dshift) : -inv_wf * static_cast<float>(h);
-                pr.Y[static_cast<long long>(i) * pr.ldy + j] = yf;
-                const float ys = yf * s0;
-                const __half hh = __float2half_rn(ys);
-                const MatSlot &my = pr.mats[kMatY0];
-                my.sl[0][static_cast<long long>(i) * pr.lds + j] = hh;
-                my.sl[1][static_cast<long long>(i) * pr.lds + j] = __float2half_rn(ys - __half2float(hh));
-                if (i == j) tr += yf;
-                sqr = fmaf(yf, yf, sqr);
+                y0 = (i == j) ? static_cast<float>(-h0 * inv_w + dshift) : -inv_wf * static_cast<float>(h0);
+                y1 = (i == j + 1) ? static_cast<float>(-h1 * inv_w + dshift) : -inv_wf * static_cast<float>(h1);
+                ms = &pr.mats[kMatY0];
+                sc = s0;
             }
+            if (!two) y1 = 0.0f;
+            float *mrow = ms->master + static_cast<long long>(i) * pr.ldy;
+            const size_t so = static_cast<size_t>(i) * pr.lds + j;
+            const float ys0 = y0 * sc, ys1 = y1 * sc;
+            const __half a0 = __float2half_rn(ys0), a1 = __float2half_rn(ys1);
+            const __half b0 = __float2half_rn(ys0 - __half2float(a0)), b1 = __float2half_rn(ys1 - __half2float(a1));
+            if (two) {
+                *reinterpret_cast<float2 *>(mrow + j) = make_float2(y0, y1);
+                *reinterpret_cast<__half2 *>(ms->sl[0] + so) = __halves2half2(a0, a1);
+                *reinterpret_cast<__half2 *>(ms->sl[1] + so) = __halves2half2(b0, b1);
+            } else {
+                mrow[j] = y0;
+                ms->sl[0][so] = a0;
+                ms->sl[1][so] = b0;
+            }
+            if (i == j) tr += y0;
+            if (i == j + 1) tr += y1;
+            sqr = fmaf(y0, y0, fmaf(y1, y1, sqr));
         }
         sq += static_cast<double>(sqr) + sqd;
     }
@@ -191,22 +223,46 @@ __global__ void k_finalize(const MmaProb *probs, int prob, double *D, long long 
     // tr D = N_e.  It is the first-order change of D for mu -> mu + gamma/beta.
     const double gamma = (fermi && st->tr_q > 0.0) ? (st->ne - st->tr_d0) / st->tr_q : 0.0;
     double tr = 0.0, eb = 0.0;
-    // block b takes rows b, b + grid, ...; thread t columns t, t + blockDim, ...
-    for (int i = blockIdx.x; i < n; i += gridDim.x)
-#pragma unroll 4
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double d;
+    // block b takes rows b, b + grid, ...; thread t the column pairs (2t, 2t + 1),
+    // (2t + 2 blockDim, ...), ...: 16-byte accesses wherever a row is 16-byte
+    // aligned (the D row for its store, the Hp row for its load)
+    auto d_at = [&](int i, int j) -> double {
         if (fermi) {
             const long long at = static_cast<long long>(i) * pr.ldx + j;
-            d = pr.Xd[0][at] + gamma * pr.Xd[1][at];
-        } else if (from_x) {
-            d = X[static_cast<long long>(i) * pr.ldx + j];
-        } else {
-            d = static_cast<double>(pr.Y[static_cast<long long>(i) * pr.ldy + j]) + (i == j ? c : 0.0);
+            return pr.Xd[0][at] + gamma * pr.Xd[1][at];
         }
-        if (D) D[static_cast<long long>(i) * ldd + j] = d;
-        if (i == j) tr += d;
-        eb += d * pr.H[static_cast<long long>(i) * pr.ldh + j];
+        if (from_x) return X[static_cast<long long>(i) * pr.ldx + j];
+        return static_cast<double>(pr.Y[static_cast<long long>(i) * pr.ldy + j]) + (i == j ? c : 0.0);
+    };
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const double *hrow = pr.H + static_cast<long long>(i) * pr.ldh;
+        double *drow = D ? D + static_cast<long long>(i) * ldd : nullptr;
+        const bool h16 = (reinterpret_cast<uintptr_t>(hrow) & 15u) == 0;
+        const bool d16 = drow && (reinterpret_cast<uintptr_t>(drow) & 15u) == 0;
+        for (int j = 2 * threadIdx.x; j < n; j += 2 * blockDim.x) {
+            const bool two = j + 1 < n;
+            const double d0 = d_at(i, j), d1 = two ? d_at(i, j + 1) : 0.0;
+            double h0, h1 = 0.0;
+            if (two && h16) {
+                const double2 hv = *reinterpret_cast<const double2 *>(hrow + j);
+                h0 = hv.x;
+                h1 = hv.y;
+            } else {
+                h0 = hrow[j];
+                if (two) h1 = hrow[j + 1];
+            }
+            if (drow) {
+                if (two && d16) {
+                    *reinterpret_cast<double2 *>(drow + j) = make_double2(d0, d1);
+                } else {
+                    drow[j] = d0;
+                    if (two) drow[j + 1] = d1;
+                }
+            }
+            if (i == j) tr += d0;
+            if (i == j + 1) tr += d1;
+            eb = fma(d0, h0, fma(d1, h1, eb));
+        }
     }
     __shared__ double red[2][32];
     tr = warp_sum(tr);

@@ -193,6 +193,43 @@ def traffic_record(kernel_name, src_file):
     return rec.get("bytes_per_launch") if rec.get("src_sha256") == h else None
 
 
+def reference_occupations(lam, ne, kT):
+    """Occupations of the constructed spectrum: the N_e lowest states at zero
+    temperature, Fermi-Dirac with mu from bisection on sum f = N_e otherwise."""
+    import numpy as np
+    lam = np.asarray(lam, dtype=np.float64)
+    if kT == 0.0:
+        return (np.arange(lam.size) < int(ne)).astype(np.float64)
+    lo, hi = lam.min() - 40 * kT, lam.max() + 40 * kT
+    for _ in range(200):
+        mu = 0.5 * (lo + hi)
+        f = 0.5 * (1.0 - np.tanh((lam - mu) / (2.0 * kT)))
+        if f.sum() > ne:
+            hi = mu
+        else:
+            lo = mu
+    return 0.5 * (1.0 - np.tanh((lam - 0.5 * (lo + hi)) / (2.0 * kT)))
+
+
+def probe_errors(torch, D, Q, lam, f, ne, kT, res, nprobe=4, seed=7):
+    """Error of a solve against the constructed D_ref = Q diag(f) Q^T, on this
+    GPU in FP64: ||D - D_ref||_F / sqrt(N_e) and ||D^2 - D||_F estimated with
+    Gaussian probes (E ||A v||^2 = ||A||_F^2), and |E_band - sum f lambda| / N_e."""
+    import numpy as np
+    dev = D.device
+    Qd = Q.to(dev, torch.float64) if torch.is_tensor(Q) else torch.from_numpy(np.asarray(Q)).to(dev)
+    fd = torch.from_numpy(np.asarray(f, dtype=np.float64)).to(dev)
+    g = torch.Generator(device=dev).manual_seed(seed)
+    V = torch.randn(D.shape[0], nprobe, dtype=torch.float64, device=dev, generator=g)
+    DV = D @ V
+    err = DV - Qd @ (fd[:, None] * (Qd.T @ V))
+    out = {"eps1_probe": float(torch.sqrt((err ** 2).sum() / nprobe)) / math.sqrt(ne),
+           "e_err_per_electron": abs(res["e_band"] - float(np.dot(np.asarray(f), np.asarray(lam)))) / ne}
+    if kT == 0.0:
+        out["idem_probe"] = float(torch.sqrt(((D @ DV - DV) ** 2).sum() / nprobe))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -279,6 +316,9 @@ def main():
     launches = ctx.launch_count() - l0
     phases = ctx.phase_ms()  # the last timed solve: set-up, step loop, output
     t_ms = e0.elapsed_time(e1)
+    # the last timed solve's error against the constructed reference (outside the timing)
+    torch.cuda.synchronize()
+    accuracy = probe_errors(torch, D, p.Q, p.lam, reference_occupations(p.lam, p.ne, kT), p.ne, kT, r)
     if dist:
         tt = torch.tensor([t_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -382,7 +422,7 @@ def main():
            "phases_ms": phases,
            "effective_tflops": iters * 2.0 * n ** 3 * value / 1e12,
            "products_per_solve": iters, "iters_by_phase": r["iters_by_phase"],
-           "accuracy": {"trace_err": abs(r["trace"] - p.ne)},
+           "accuracy": dict({"trace_err": abs(r["trace"] - p.ne)}, **accuracy),
            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * n * n,
                    "d2h_bytes_per_step": 8 * n * n},
            "gpu_launches": launches, "roofline": roof, "kernels": kernels,
@@ -394,7 +434,19 @@ def main():
         # the same expansion with every product in FP64 on this GPU
         t0 = time.perf_counter()
         r64 = ctx.solve(H, p.ne, tol=p.tol, D=D, precision="fp64")
-        base["fp64_gpu_sp2"] = {"solves_per_s": 1e3 / r64["ms"], "products": r64["iters"]}
+        f_ref = reference_occupations(p.lam, p.ne, 0.0)
+        torch.cuda.synchronize()
+        base["fp64_gpu_sp2"] = {"solves_per_s": 1e3 / r64["ms"], "products": r64["iters"],
+                                "accuracy": probe_errors(torch, D, p.Q, p.lam, f_ref, p.ne, 0.0, r64)}
+        # the other precision schedules of the configuration (FP32-class split
+        # products without the FP64-accurate polish; single-FP16 bulk until
+        # RelTr < 5e-4, then split, then polish), each with its error
+        for name in ("fp32", "try_fp16"):
+            rs = ctx.solve(H, p.ne, tol=p.tol, D=D, precision=name, check=False)
+            torch.cuda.synchronize()
+            base["schedule_" + name] = {"solves_per_s": 1e3 / rs["ms"], "status": rs["status"],
+                                        "iters_by_phase": rs["iters_by_phase"],
+                                        "accuracy": probe_errors(torch, D, p.Q, p.lam, f_ref, p.ne, 0.0, rs)}
         # cuSOLVER syevd (torch.linalg.eigh, FP64) + D = V_occ V_occ^T
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

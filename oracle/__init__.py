@@ -18,8 +18,8 @@ passage each routine follows:
   doubling reading).
 * ``metrics``                   -- eps1, eps2 ingredients (Sec. III-C).
 
-Parity status of every function is listed in the design doc; every function
-here is pinned by a test in ``tests/test_oracle.py``.
+Every function here is pinned by a test in ``tests/test_oracle.py`` against
+closed forms, invariants, brute force on tiny inputs or a library routine.
 """
 import ctypes
 import os

@@ -240,6 +240,8 @@ def main():
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--precision", default=None, choices=["mixed", "try_fp16", "fp32", "fp64"],
                     help="override the workload's precision schedule")
+    ap.add_argument("--tiles", default="auto", choices=["auto", "256", "128"],
+                    help="tensor-core tile width: autotuned per size (untimed, before the warm-up) or fixed")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -285,6 +287,7 @@ def main():
     D = torch.empty_like(H)
     stream = torch.cuda.Stream(device=dev)
     ctx = fe.Context(device=local_rank, stream=stream.cuda_stream)
+    tiles = apply_tiles(ctx, [n], prec, args.tiles)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
     def one():
@@ -417,7 +420,8 @@ def main():
            "data": "synthetic",
            "config": {"workload": args.workload, "n": n, "n_e": p.ne, "kT": kT,
                       "precision": prec, "parallelism": "replicas" if world > 1 else "single",
-                      "l2": "256 MiB buffer written before every step; working set > 129 MB L2"},
+                      "l2": "256 MiB buffer written before every step; working set > 129 MB L2",
+                      "tiles": tiles},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
            "phases_ms": phases,
            "effective_tflops": iters * 2.0 * n ** 3 * value / 1e12,
@@ -476,6 +480,23 @@ def main():
         dist.destroy_process_group()
 
 
+def apply_tiles(ctx, sizes, prec, mode):
+    """Tile widths of the tensor-core products for these sizes: 'auto' runs
+    the library's autotuner on them (outside the timed region), '256' / '128'
+    fix the width.  Returns the config record."""
+    if prec == "fp64":
+        return None
+    sizes = sorted(set(int(n) for n in sizes))
+    if mode == "auto":
+        ents = ctx.autotune(sizes, precision=prec, reps=2)
+        return {"mode": "autotuned", "narrow_sizes": sum(e["bn"] == 128 for e in ents),
+                "sizes": len(ents),
+                "table": [[e["n"], e["bn"], round(e["ms_256"], 4), round(e["ms_128"], 4)] for e in ents]}
+    for n in sizes:
+        ctx.set_tile_width(n, int(mode), prec)
+    return {"mode": "fixed", "bn": int(mode)}
+
+
 def _kernel_times(ctx, n_list):
     """Per-kernel CUDA-event times of the last profiled solve or batch."""
     prof = ctx.profile_read()
@@ -495,6 +516,15 @@ def bench_batch(args, torch, fe):
         items.append(dict(H=H, ne=p.ne, tol=p.tol, D=torch.empty_like(H), precision="mixed"))
     stream = torch.cuda.Stream(device=dev)
     ctx = fe.Context(device=0, stream=stream.cuda_stream)
+    if args.tiles == "auto":
+        # tuned on the batch itself (outside the timed region): per-size
+        # timings do not carry over to a launch that holds every problem's tiles
+        trials = ctx.autotune_batch(items, reps=2)
+        widths = [ctx.tile_width(n) for n in sizes]
+        tiles = {"mode": "autotuned on the batch", "narrow_problems": sum(w == 128 for w in widths),
+                 "trial_batch_ms": [round(t, 3) for t in trials]}
+    else:
+        tiles = apply_tiles(ctx, sizes, "mixed", args.tiles)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
     def one():
@@ -528,7 +558,7 @@ def bench_batch(args, torch, fe):
            "scaling": "weak", "vs_baseline": None, "dtype": "f16x2+f16digits", "data": "synthetic",
            "config": {"workload": "ragged_batch64", "problems": len(items), "n_min": min(sizes),
                       "n_max": max(sizes), "n_e": "round(0.85 n)", "parallelism": "single",
-                      "l2": "256 MiB buffer written before every step"},
+                      "l2": "256 MiB buffer written before every step", "tiles": tiles},
            "effective_tflops": products * args.steps / (t_ms / 1e3) / 1e12,
            "max_trace_err": max(abs(r["trace"] - p.ne) for r, p in zip(res, probs)),
            "phases_ms": phases,

@@ -85,7 +85,8 @@ typedef struct {
     int max_iters;            /* cap on expansion products per phase; 0 = 100     */
     uint32_t precision_policy;/* default FE_PREC_* when a problem leaves it 0     */
     void *cuda_stream;        /* cudaStream_t to run on; NULL = library stream    */
-    const char *autotune_path;/* reserved, must be NULL                           */
+    const char *autotune_path;/* tile-shape table file: loaded by fe_create when it
+                                 exists, rewritten by fe_autotune; NULL = none    */
 } fe_config;
 
 typedef struct {
@@ -119,8 +120,18 @@ typedef struct {
 
 typedef uint64_t fe_ticket;
 
+/* One tile-shape table entry as fe_autotune reports it. */
+typedef struct {
+    int64_t n;       /* problem dimension                                          */
+    int bn;          /* tensor-core tile width chosen: 256 (128 x 256 tiles) or 128 */
+    double ms_256;   /* best device time (ms) per solve of a synthetic batch of this
+                        size with 128 x 256 tiles                                  */
+    double ms_128;   /* the same with 128 x 128 tiles                               */
+} fe_tune;
+
 /* Create a context on cfg->device.  cfg may be NULL (defaults).
- * Errors: FE_EINVAL (bad device / autotune_path != NULL), FE_ECUDA. */
+ * Errors: FE_EINVAL (bad device, unreadable or malformed autotune_path file),
+ * FE_ECUDA. */
 FE_API int fe_create(fe_ctx **out, const fe_config *cfg);
 
 /* Wait for outstanding work, free all device memory.  NULL is accepted. */
@@ -152,6 +163,45 @@ FE_API int fe_submit(fe_ctx *ctx, const fe_problem *p, fe_ticket *t);
 /* FE_PENDING while the ticket's solve is queued or running; otherwise the
  * final status, with r filled.  Never blocks. */
 FE_API int fe_poll(fe_ctx *ctx, fe_ticket t, fe_result *r);
+
+/* Tile-shape autotuner.  The split-FP16 / single-FP16 symmetric products
+ * (Sec. III-B: the matrix product is the cost) run over upper-triangle tiles of
+ * 128 x 256 or 128 x 128 elements.  Wide tiles halve the operand traffic per
+ * flop; narrow ones waste less work at the diagonal and the ragged edge and
+ * give more tiles to balance over the SMs, which pays for small n.  The
+ * context keeps a table from (number of 128-row panels, precision policy) to
+ * the width; a problem uses the entry for its panel count, else the nearest
+ * one under its policy, else 256.  Problems of different widths share one
+ * launch in fe_solve_batch.
+ * fe_autotune fills the table for the panel counts of ns[0..count): for each
+ * it times `reps` batches of synthetic gapped solves of that size (N_e =
+ * 0.85 n, device Hp, no output; enough copies per batch, at most 16, for two
+ * waves of 128 x 256 tiles over the SMs, so that the time per solve measures
+ * throughput as in a busy batch or server) with each width under precision
+ * policy `prec` (0 = the context's default; FE_PREC_FP64 has no tiles), keeps
+ * the width with the lower time per solve, and writes the table to the
+ * context's autotune_path if one was given.  out (may be NULL) receives one
+ * entry per ns[i].  The solves run on the context's stream like
+ * fe_solve_batch; n must lie in [2, 2^20].
+ * Errors: FE_EINVAL, FE_ENOMEM, any fe_solve status. */
+FE_API int fe_autotune(fe_ctx *ctx, int count, const int64_t *ns, uint32_t prec, int reps, fe_tune *out);
+
+/* Tile widths for a recurring batch.  fe_autotune times each size on its own
+ * (copies of one problem); in a mixed batch the widths interact (one launch
+ * holds every problem's tiles), so this tunes on the batch itself: it times
+ * fe_solve_batch on ps[0..count) (outputs not written: every D is ignored)
+ * with 128 x 256 tiles for every problem, then makes the problems of the
+ * smallest panel count narrow (128 x 128), then those of the next one, and so
+ * on while each step lowers the batch's device time by more than 0.5%; the
+ * first step that does not is undone and ends the search.  The result is left
+ * in the context's table (and its autotune_path file).  Each trial is one
+ * untimed batch then the best of `reps` (< 1: 2).  trial_ms[0..max_trials)
+ * receives the trials' batch times (ms; [0] = all 128 x 256), *ntrials their
+ * number (both may be NULL / 0).
+ * Errors: FE_EINVAL (count < 1, an invalid problem), any fe_solve_batch
+ * status (the table is then left as it was). */
+FE_API int fe_autotune_batch(fe_ctx *ctx, int count, const fe_problem *ps, int reps, double *trial_ms,
+                             int max_trials, int *ntrials);
 
 /* One-line description of the last error on this context (or of the last
  * fe_create failure when ctx is NULL).  Valid until the next call. */

@@ -96,6 +96,15 @@ FE_API int fe_k_narrow_bounds(fe_ctx *ctx, double factor);
  * ran.  Zeros before the first solve. */
 FE_API int fe_k_phase_ms(fe_ctx *ctx, double *out4);
 
+/* Tile-shape table hooks (tests; see fe_autotune in fe.h).  set: make problems
+ * with n's number of 128-row panels under policy prec (an FE_PREC_* value,
+ * FE_PREC_MIXED = 0 included) use tile width bn (128 or 256; 0 removes the
+ * entry).  get: the width such a problem would use now (HOST out).
+ * fe_k_sym_square looks its width up under FE_PREC_FP32 (two slices) or
+ * FE_PREC_TRY_FP16 (one slice). */
+FE_API int fe_k_set_tile_width(fe_ctx *ctx, int64_t n, uint32_t prec, int bn);
+FE_API int fe_k_tile_width(fe_ctx *ctx, int64_t n, uint32_t prec, int *bn);
+
 /* Number of kernels this context has launched since fe_create (HOST out). */
 FE_API int fe_k_launch_count(fe_ctx *ctx, int64_t *out);
 

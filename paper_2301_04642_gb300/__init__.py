@@ -34,6 +34,11 @@ class FeProblem(ctypes.Structure):
                 ("D", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
 
 
+class FeTune(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("bn", ctypes.c_int), ("ms_256", ctypes.c_double),
+                ("ms_128", ctypes.c_double)]
+
+
 class FeResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
                 ("iters_by_phase", ctypes.c_int * 4), ("e_band", ctypes.c_double),
@@ -83,10 +88,17 @@ def load(build=True):
     L.fe_k_launch_count.argtypes = [P, ctypes.POINTER(i64)]
     L.fe_k_history.argtypes = [P, ctypes.c_int, ctypes.POINTER(dbl), ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int)]
+    L.fe_autotune.argtypes = [P, ctypes.c_int, ctypes.POINTER(i64), ctypes.c_uint32, ctypes.c_int,
+                              ctypes.POINTER(FeTune)]
+    L.fe_autotune_batch.argtypes = [P, ctypes.c_int, ctypes.POINTER(FeProblem), ctypes.c_int,
+                                    ctypes.POINTER(dbl), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.fe_k_set_tile_width.argtypes = [P, i64, ctypes.c_uint32, ctypes.c_int]
+    L.fe_k_tile_width.argtypes = [P, i64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int)]
     for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
                  "fe_k_gershgorin", "fe_k_gershgorin_noalloc", "fe_k_sym_square", "fe_k_digit_square",
                  "fe_k_profile", "fe_k_profile_read", "fe_k_narrow_bounds", "fe_k_phase_ms", "fe_k_profile_steps",
-                 "fe_k_launch_count", "fe_k_history"):
+                 "fe_k_launch_count", "fe_k_history", "fe_autotune", "fe_autotune_batch", "fe_k_set_tile_width",
+                 "fe_k_tile_width"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -145,10 +157,12 @@ def gershgorin_noalloc(H, out4, stream=None):
 class Context:
     """One library context (fe_create) on one GPU."""
 
-    def __init__(self, device=0, hbm_budget_bytes=0, max_iters=0, precision="mixed", stream=None):
+    def __init__(self, device=0, hbm_budget_bytes=0, max_iters=0, precision="mixed", stream=None,
+                 autotune_path=None):
         self.L = load()
         cfg = FeConfig(device, hbm_budget_bytes, max_iters, PREC[precision],
-                       ctypes.c_void_p(stream) if stream else None, None)
+                       ctypes.c_void_p(stream) if stream else None,
+                       os.fsencode(autotune_path) if autotune_path else None)
         h = ctypes.c_void_p()
         rc = self.L.fe_create(ctypes.byref(h), ctypes.byref(cfg))
         if rc != FE_OK:
@@ -292,6 +306,52 @@ class Context:
         rc = self.L.fe_k_digit_square(self.h, xp, X.shape[0], X.stride(0), pp, P.stride(0))
         if rc != FE_OK:
             raise FeError(rc, self.last_error())
+
+    # ---- tile-shape autotuner ---------------------------------------------------
+    def autotune(self, ns, precision="mixed", reps=2):
+        """Time synthetic solves of each size in `ns` with 128 x 256 and
+        128 x 128 tensor-core tiles and keep the faster width per size
+        (fe_autotune); returns one dict per size."""
+        ns = [int(x) for x in ns]
+        arr = (ctypes.c_int64 * max(1, len(ns)))(*ns)
+        out = (FeTune * max(1, len(ns)))()
+        rc = self.L.fe_autotune(self.h, len(ns), arr, PREC[precision], int(reps), out)
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+        return [{"n": t.n, "bn": t.bn, "ms_256": t.ms_256, "ms_128": t.ms_128} for t in out[: len(ns)]]
+
+    def autotune_batch(self, items, reps=2, max_trials=64):
+        """Tune the tile widths on a batch (fe_autotune_batch; items as for
+        solve_batch, outputs not written).  Returns the trials' batch times
+        (ms; the first with 128 x 256 tiles everywhere)."""
+        probs = (FeProblem * len(items))()
+        keep = []
+        for k, it in enumerate(items):
+            p, kp = self._problem(it["H"], it["ne"], it.get("kT", 0.0), it.get("tol", 0.0), None,
+                                  it.get("precision", "mixed"), it.get("method", FE_METHOD_AUTO))
+            probs[k] = p
+            keep.append(kp)
+        out = (ctypes.c_double * max_trials)()
+        nt = ctypes.c_int()
+        rc = self.L.fe_autotune_batch(self.h, len(items), probs, int(reps), out, int(max_trials),
+                                      ctypes.byref(nt))
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+        return list(out[: min(nt.value, max_trials)])
+
+    def set_tile_width(self, n, bn, precision="mixed"):
+        """Make problems with n's number of 128-row panels use tile width bn
+        (128 or 256; 0 removes the entry)."""
+        rc = self.L.fe_k_set_tile_width(self.h, int(n), PREC[precision], int(bn))
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+
+    def tile_width(self, n, precision="mixed"):
+        v = ctypes.c_int()
+        rc = self.L.fe_k_tile_width(self.h, int(n), PREC[precision], ctypes.byref(v))
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+        return v.value
 
     # ---- measurement hooks ----------------------------------------------------
     def profile(self, enable=True):

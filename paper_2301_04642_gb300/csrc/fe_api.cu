@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cfloat>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -70,7 +71,8 @@ struct Slot {
     RowInfo *rowinfo = nullptr;
     int *bad = nullptr;
     int ldy = 0, lds = 0, ldx = 0;
-    std::vector<TileEnt> tiles;
+    std::vector<TileEnt> tiles;   // tensor-core tiles 128 x 256
+    std::vector<TileEnt> tilesN;  // tensor-core tiles 128 x 128
     std::vector<Tile64> tiles64;
     std::vector<TileEnt> tilesD;  // digit-product tiles (zero temperature)
     MmaProb hp;  // host image of the device descriptor (H filled per solve)
@@ -113,6 +115,15 @@ struct Engine {
     std::vector<uintptr_t> gkey;     // what the instantiated graph was built for
 };
 
+// One entry of the tile-shape table: the tensor-core tile width chosen for
+// problems with a given number of 128-row panels under one precision policy,
+// with the solve times (ms) the autotuner measured for each width (0: not
+// measured, the entry was set directly).
+struct TuneEnt {
+    int bn = kTileN;
+    double ms_w = 0.0, ms_n = 0.0;
+};
+
 // One fe_submit request.
 struct Req {
     fe_ticket id = 0;
@@ -121,6 +132,7 @@ struct Req {
     Slot *slot = nullptr;
     bool staged = false;            // Hp already copied into slot->Hcopy
     bool gershgorin = false;        // the spectral-bound estimate proved too tight: use Gershgorin
+    int bn = 0;                     // tensor-core tile width, fixed when the solve starts
     bool done = false;
     fe_result res{};
     std::chrono::steady_clock::time_point t_submit;
@@ -145,6 +157,10 @@ struct fe_ctx {
     std::atomic<long long> launches{0};  // kernels launched by this context
     std::atomic<double> lz_narrow{1.0};  // test hook: scale of the estimated bound interval
     double phase_ms[4] = {};             // last blocking solve: set-up, step loop, output; steps
+    // tile-shape table: (128-row panels, FE_PREC_*) -> tile width (fe_autotune)
+    std::mutex tmu;
+    std::map<std::pair<int, uint32_t>, TuneEnt> tune;
+    std::string tune_path;               // file the table is loaded from / saved to ("" = none)
     std::recursive_mutex mu;  // eng, profiling state (blocking calls)
     // continuous batching (fe_submit / fe_poll): a worker thread with its own engine
     Engine seng;
@@ -199,15 +215,16 @@ void push_banded(std::vector<TileEnt> &out, int nI, int nJ, int band, Jmin jmin)
 }
 
 // 128-row panels per band: the tensor-core tiles read 128 x K and 256 x K
-// panels (two FP16 slices each), the digit tiles 128 x K and 64 x K panels of
-// seven digits; the bands balance row-panel and column-panel bytes over a
-// wave of about 150 tiles.
-constexpr int kBandTc = 16, kBandDigit = 8;
+// (or 128 x K) panels (two FP16 slices each), the digit tiles 128 x K and
+// 64 x K panels of seven digits; the bands balance row-panel and column-panel
+// bytes over a wave of about 150 tiles.
+constexpr int kBandTc = 16, kBandTcN = 12, kBandDigit = 8;
 
 void build_tiles(Slot *s) {
     const int T = ceil_div(s->n, kTileM);
     const int TP = ceil_div(T, 2);
     push_banded(s->tiles, T, TP, kBandTc, [](int I) { return I / 2; });
+    push_banded(s->tilesN, T, T, kBandTcN, [](int I) { return I; });
     s->tiles64.clear();
     const int T64 = ceil_div(s->n, kTile64);
     int slot = 0;
@@ -232,7 +249,7 @@ size_t slot_bytes(int n, int method, int *ldy, int *lds, int *ldx, size_t *npart
     *ldx = n;
     const int T = ceil_div(n, kTileM);
     const int T64 = ceil_div(n, kTile64);
-    const size_t ntiles = static_cast<size_t>(T) * ceil_div(T, 2);
+    const size_t ntiles = static_cast<size_t>(T) * (T + 1) / 2;  // >= T ceil(T/2): either width
     const size_t nt64 = static_cast<size_t>(T64) * (T64 + 1) / 2;
     const size_t TD = static_cast<size_t>(ceil_div(n, kDigitN));
     size_t ntD = 0;
@@ -396,6 +413,7 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
     s->hp.ldy = ldy;
     s->hp.lds = lds;
     s->hp.ntiles = static_cast<int>(s->tiles.size());
+    s->hp.bn = kTileN;
     s->hp.ntiles64 = static_cast<int>(s->tiles64.size());
     s->hp.ntilesD = static_cast<int>(s->tilesD.size());
     s->hp.lzv = s->lzv;
@@ -424,6 +442,24 @@ uint32_t prec_of(const fe_ctx *ctx, const fe_problem *p) {
     uint32_t pr = p->flags & FE_PREC_MASK;
     if (pr == 0) pr = ctx->prec_default & FE_PREC_MASK;
     return pr;
+}
+
+// Tensor-core tile width for a problem of dimension n under precision policy
+// prec: the table's entry for its number of 128-row panels, else the entry
+// nearest in panels under the same policy, else 256.
+int tile_width(fe_ctx *ctx, int64_t n, uint32_t prec) {
+    const int T = static_cast<int>((n + kTileM - 1) / kTileM);
+    std::lock_guard<std::mutex> lk(ctx->tmu);
+    int best = kTileN, dist = INT_MAX;
+    for (const auto &kv : ctx->tune) {
+        if (kv.first.second != prec) continue;
+        const int d = std::abs(kv.first.first - T);
+        if (d < dist) {
+            dist = d;
+            best = kv.second.bn;
+        }
+    }
+    return best;
 }
 
 int method_of(const fe_problem *p) {
@@ -510,6 +546,7 @@ struct Job {
     const double *stage = nullptr;  // host Hp copied into slot->Hcopy at set-up, or null
     int64_t ldstage = 0;
     bool lanczos = true;            // estimate the spectral bounds (else Gershgorin)
+    int bn = 0;                     // tensor-core tile width, fixed for the whole solve (0: look up)
 };
 
 Job make_job(const fe_problem *p, Slot *s) {
@@ -603,8 +640,14 @@ int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
         hprobs[k].tc_ntiles = 0;
         if (pr != FE_PREC_FP64 || fermi) {
             e.any_tc = true;
-            for (TileEnt t : j.slot->tiles) { t.prob = k; tiles.push_back(t); }
-            hprobs[k].tc_ntiles = static_cast<int>(j.slot->tiles.size());
+            // a problem keeps its width for the whole solve: the control step
+            // reduces the partial slots of the previous product's tiles
+            const int bn = j.bn ? j.bn : tile_width(ctx, j.p->n, pr);
+            const std::vector<TileEnt> &tl = (bn == kTileM) ? j.slot->tilesN : j.slot->tiles;
+            for (TileEnt t : tl) { t.prob = k; tiles.push_back(t); }
+            hprobs[k].tc_ntiles = static_cast<int>(tl.size());
+            hprobs[k].ntiles = static_cast<int>(tl.size());
+            hprobs[k].bn = bn;
         }
         e.off64[k] = static_cast<int>(tiles64.size());
         e.cnt64[k] = 0;
@@ -1115,6 +1158,7 @@ Job job_of(Req *r) {
         j.ldstage = r->p.n;
     }
     j.lanczos = !r->gershgorin;
+    j.bn = r->bn;
     return j;
 }
 
@@ -1143,6 +1187,7 @@ void serve_loop(fe_ctx *ctx) {
                 }
                 r->slot = s;
             }
+            if (r->bn == 0) r->bn = tile_width(ctx, r->p.n, prec_of(ctx, &r->p));
             started.push_back(r);
         }
         if (!started.empty() || !failed.empty()) {
@@ -1244,6 +1289,49 @@ void serve_loop(fe_ctx *ctx) {
     for (Req *r : running) release_slot(ctx, r->slot);
 }
 
+// ---------------------------------------------------------------- tile table file
+// Text: a header line "fe-autotune 1", then one line per entry:
+// <128-row panels> <FE_PREC_* value> <tile width> <ms with 256> <ms with 128>.
+
+int load_tune(fe_ctx *ctx, const std::string &path) {
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return FE_OK;  // no table yet
+    char head[32] = {};
+    int ver = 0;
+    int rc = FE_OK;
+    if (fscanf(f, "%31s %d", head, &ver) != 2 || std::string(head) != "fe-autotune" || ver != 1) {
+        rc = set_err(nullptr, FE_EINVAL, "autotune file " + path + ": bad header");
+    } else {
+        int T = 0, bn = 0;
+        unsigned prec = 0;
+        double a = 0, b = 0;
+        int got;
+        while ((got = fscanf(f, "%d %u %d %lf %lf", &T, &prec, &bn, &a, &b)) == 5) {
+            if (T < 1 || (bn != kTileM && bn != kTileN) || (prec & ~FE_PREC_MASK) != 0) {
+                rc = set_err(nullptr, FE_EINVAL, "autotune file " + path + ": bad entry");
+                break;
+            }
+            ctx->tune[{T, prec}] = TuneEnt{bn, a, b};
+        }
+        if (rc == FE_OK && got != EOF) rc = set_err(nullptr, FE_EINVAL, "autotune file " + path + ": bad entry");
+    }
+    fclose(f);
+    return rc;
+}
+
+// caller holds ctx->tmu
+int save_tune(fe_ctx *ctx) {
+    if (ctx->tune_path.empty()) return FE_OK;
+    FILE *f = fopen(ctx->tune_path.c_str(), "w");
+    if (!f) return set_err(ctx, FE_EINVAL, "cannot write autotune file " + ctx->tune_path);
+    fprintf(f, "fe-autotune 1\n");
+    for (const auto &kv : ctx->tune)
+        fprintf(f, "%d %u %d %.6f %.6f\n", kv.first.first, kv.first.second, kv.second.bn, kv.second.ms_w,
+                kv.second.ms_n);
+    const bool ok = fclose(f) == 0;
+    return ok ? FE_OK : set_err(ctx, FE_EINVAL, "cannot write autotune file " + ctx->tune_path);
+}
+
 }  // namespace
 
 // ============================================================== C ABI
@@ -1253,7 +1341,6 @@ extern "C" int fe_create(fe_ctx **out, const fe_config *cfg) {
     *out = nullptr;
     fe_config c{};
     if (cfg) c = *cfg;
-    if (c.autotune_path) return set_err(nullptr, FE_EINVAL, "autotune_path must be NULL");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0)
@@ -1267,6 +1354,15 @@ extern "C" int fe_create(fe_ctx **out, const fe_config *cfg) {
         return set_err(nullptr, FE_ECUDA, "this library is built for sm_103a (GB300) only");
     if (!get_encode()) return set_err(nullptr, FE_ECUDA, "cuTensorMapEncodeTiled not available");
     fe_ctx *ctx = new fe_ctx();
+    if (c.autotune_path) {
+        ctx->tune_path = c.autotune_path;
+        const int lrc = load_tune(ctx, ctx->tune_path);
+        if (lrc != FE_OK) {
+            const std::string why = g_err;
+            delete ctx;
+            return set_err(nullptr, lrc, why);
+        }
+    }
     ctx->device = c.device;
     ctx->num_sms = prop.multiProcessorCount;
     ctx->max_iters = c.max_iters > 0 ? c.max_iters : 100;
@@ -1540,19 +1636,23 @@ extern "C" int fe_k_sym_square(fe_ctx *ctx, const float *Y, int64_t n, int64_t l
     op.out[0].flags = kOutMaster | kOutSlices;
     op.out[0].a = 1.0f;
     op.out[0].s = 1.0f;
+    // tile width from the context's table for this n (split: FE_PREC_FP32, single: FE_PREC_TRY_FP16)
+    const int bn = tile_width(ctx, n, nslices == 2 ? FE_PREC_FP32 : FE_PREC_TRY_FP16);
+    const std::vector<TileEnt> &tl = (bn == kTileM) ? s->tilesN : s->tiles;
     rc = ensure_dev(ctx, &eg.d_probs, &eg.probs_cap, 1);
-    if (rc == FE_OK) rc = ensure_dev(ctx, &eg.d_tiles, &eg.tiles_cap, s->tiles.size());
+    if (rc == FE_OK) rc = ensure_dev(ctx, &eg.d_tiles, &eg.tiles_cap, tl.size());
     if (rc != FE_OK) { release_slot(ctx, s); return rc; }
     MmaProb hp = s->hp;
     hp.tc_tile0 = 0;
-    hp.tc_ntiles = static_cast<int>(s->tiles.size());
+    hp.tc_ntiles = static_cast<int>(tl.size());
+    hp.ntiles = static_cast<int>(tl.size());
+    hp.bn = bn;
     cudaMemcpyAsync(eg.d_probs, &hp, sizeof(MmaProb), cudaMemcpyHostToDevice, q);
-    cudaMemcpyAsync(eg.d_tiles, s->tiles.data(), sizeof(TileEnt) * s->tiles.size(),
-                    cudaMemcpyHostToDevice, q);
+    cudaMemcpyAsync(eg.d_tiles, tl.data(), sizeof(TileEnt) * tl.size(), cudaMemcpyHostToDevice, q);
     cudaMemsetAsync(eg.d_skcnt, 0, sizeof(int) * 2 * ctx->num_sms, q);
     cudaMemcpyAsync(s->st, &st0, sizeof(SolveState), cudaMemcpyHostToDevice, q);
     cudaMemsetAsync(eg.d_err, 0, sizeof(int), q);
-    const int nt = static_cast<int>(s->tiles.size());
+    const int nt = static_cast<int>(tl.size());
     k_sym_mma<<<ctx->num_sms, kSymThreads, mma_smem_bytes(), q>>>(eg.d_probs, 1, eg.d_tiles, nt, eg.d_err,
                                                                    eg.d_skws, eg.d_skcnt);
     ctx->launches += 2;
@@ -1668,5 +1768,195 @@ extern "C" int fe_k_history(fe_ctx *ctx, int index, double *out, int max_rows, i
     for (int i = 0; i < r; ++i)
         for (int j = 0; j < kHistCols; ++j) out[i * kHistCols + j] = st.hist[i][j];
     *rows = r;
+    return FE_OK;
+}
+
+extern "C" int fe_autotune(fe_ctx *ctx, int count, const int64_t *ns, uint32_t prec, int reps, fe_tune *out) {
+    if (!ctx || count < 0 || (count > 0 && !ns)) return set_err(ctx, FE_EINVAL, "bad arguments");
+    if ((prec & ~FE_PREC_MASK) != 0) return set_err(ctx, FE_EINVAL, "unknown precision flag");
+    if (prec == 0) prec = ctx->prec_default & FE_PREC_MASK;
+    if (prec != FE_PREC_MIXED && prec != FE_PREC_FP32 && prec != FE_PREC_TRY_FP16)
+        return set_err(ctx, FE_EINVAL, "only the tensor-core schedules (MIXED, FP32, TRY_FP16) have tiles to tune");
+    if (reps < 1) reps = 2;
+    // the largest n given for each panel count is the one timed
+    std::map<int, int64_t> Tn;
+    for (int i = 0; i < count; ++i) {
+        if (ns[i] < 2 || ns[i] > (1 << 20)) return set_err(ctx, FE_EINVAL, "n out of range (2 .. 2^20)");
+        const int T = static_cast<int>((ns[i] + kTileM - 1) / kTileM);
+        Tn[T] = std::max(Tn[T], ns[i]);
+    }
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t q = ctx->eng.stream;
+    for (const auto &tn : Tn) {
+        const int T = tn.first;
+        const int64_t n = tn.second;
+        // synthetic gapped Hp: diagonal, N_e = round(0.85 n) levels evenly in
+        // [-1, -0.05], the rest evenly in [0.05, 0.5] (the tensor-core work of a
+        // product does not depend on the values)
+        const int64_t ne = std::min<int64_t>(n - 1, std::max<int64_t>(1, llround(0.85 * static_cast<double>(n))));
+        std::vector<double> diag(static_cast<size_t>(n));
+        for (int64_t i = 0; i < n; ++i)
+            diag[i] = (i < ne) ? -1.0 + 0.95 * static_cast<double>(i) / static_cast<double>(std::max<int64_t>(1, ne - 1))
+                               : 0.05 + 0.45 * static_cast<double>(i - ne) / static_cast<double>(std::max<int64_t>(1, n - ne - 1));
+        double *dH = nullptr;
+        const size_t bytes = sizeof(double) * static_cast<size_t>(n) * static_cast<size_t>(n);
+        if (cudaMalloc(&dH, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(ctx, FE_ENOMEM, "autotune: no device memory for Hp");
+        }
+        int rc = FE_OK;
+        if (cudaMemsetAsync(dH, 0, bytes, q) != cudaSuccess ||
+            cudaMemcpy2DAsync(dH, sizeof(double) * static_cast<size_t>(n + 1), diag.data(), sizeof(double),
+                              sizeof(double), static_cast<size_t>(n), cudaMemcpyHostToDevice, q) != cudaSuccess ||
+            cudaStreamSynchronize(q) != cudaSuccess)
+            rc = set_err(ctx, FE_ECUDA, std::string("autotune: ") + cudaGetErrorString(cudaGetLastError()));
+        fe_problem p{};
+        p.Hp = dH;
+        p.n = n;
+        p.ld = n;
+        p.n_e = static_cast<double>(ne);
+        p.flags = FE_PTR_DEVICE | FE_METHOD_SP2 | prec;
+        // throughput, not latency: enough copies of the problem in one batch
+        // for two waves of 128 x 256 tiles over the SMs (at most 16 copies;
+        // they share the read-only Hp)
+        const int wide_tiles = T * ((T + 1) / 2);
+        const int copies = std::max(1, std::min(16, (2 * ctx->num_sms + wide_tiles - 1) / wide_tiles));
+        std::vector<fe_problem> ps(copies, p);
+        std::vector<fe_result> rs(copies);
+        double best[2] = {DBL_MAX, DBL_MAX};
+        // a warm-up batch per width (slots, graph), then `reps` rounds taking turns
+        for (int r = 0; r <= reps && rc == FE_OK; ++r)
+            for (int w = 0; w < 2 && rc == FE_OK; ++w) {
+                {
+                    std::lock_guard<std::mutex> tl(ctx->tmu);
+                    ctx->tune[{T, prec}] = TuneEnt{w == 0 ? kTileN : kTileM, 0.0, 0.0};
+                }
+                rc = fe_solve_batch(ctx, copies, ps.data(), rs.data());
+                double ms = 0.0;
+                for (const fe_result &x : rs) ms = std::max(ms, x.ms);
+                if (rc == FE_OK && r > 0) best[w] = std::min(best[w], ms / copies);
+            }
+        cudaFree(dH);
+        std::lock_guard<std::mutex> tl(ctx->tmu);
+        if (rc != FE_OK) {
+            ctx->tune.erase({T, prec});
+            return rc;
+        }
+        ctx->tune[{T, prec}] = TuneEnt{best[1] < best[0] ? kTileM : kTileN, best[0], best[1]};
+    }
+    if (out)
+        for (int i = 0; i < count; ++i) {
+            const int T = static_cast<int>((ns[i] + kTileM - 1) / kTileM);
+            std::lock_guard<std::mutex> tl(ctx->tmu);
+            const TuneEnt &e = ctx->tune[{T, prec}];
+            out[i].n = ns[i];
+            out[i].bn = e.bn;
+            out[i].ms_256 = e.ms_w;
+            out[i].ms_128 = e.ms_n;
+        }
+    std::lock_guard<std::mutex> tl(ctx->tmu);
+    return save_tune(ctx);
+}
+
+extern "C" int fe_autotune_batch(fe_ctx *ctx, int count, const fe_problem *ps, int reps, double *trial_ms,
+                                 int max_trials, int *ntrials) {
+    if (ntrials) *ntrials = 0;
+    if (!ctx || count < 1 || !ps || max_trials < 0 || (max_trials > 0 && !trial_ms))
+        return set_err(ctx, FE_EINVAL, "bad arguments");
+    if (reps < 1) reps = 2;
+    for (int k = 0; k < count; ++k) {
+        const int rc = validate(ctx, &ps[k]);
+        if (rc != FE_OK) return rc;
+    }
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    // the batch's tile classes (panel count, policy), smallest first
+    std::vector<std::pair<int, uint32_t>> cls;
+    for (int k = 0; k < count; ++k) {
+        const uint32_t pr = prec_of(ctx, &ps[k]);
+        if (pr == FE_PREC_FP64 && method_of(&ps[k]) != kMethodFermi) continue;
+        cls.push_back({static_cast<int>((ps[k].n + kTileM - 1) / kTileM), pr});
+    }
+    std::sort(cls.begin(), cls.end());
+    cls.erase(std::unique(cls.begin(), cls.end()), cls.end());
+    if (cls.empty()) return FE_OK;
+    std::map<std::pair<int, uint32_t>, TuneEnt> saved;
+    {
+        std::lock_guard<std::mutex> tl(ctx->tmu);
+        for (const auto &c : cls) {
+            auto it = ctx->tune.find(c);
+            if (it != ctx->tune.end()) saved[c] = it->second;
+            ctx->tune[c] = TuneEnt{kTileN, 0.0, 0.0};
+        }
+    }
+    // the batch without its outputs
+    std::vector<fe_problem> q(ps, ps + count);
+    for (fe_problem &x : q) x.D = nullptr;
+    std::vector<fe_result> rs(count);
+    auto time_batch = [&](double *out) {
+        double best = DBL_MAX;
+        for (int r = 0; r <= reps; ++r) {  // the first run builds slots and the graph
+            const int rc = fe_solve_batch(ctx, count, q.data(), rs.data());
+            if (rc != FE_OK) return rc;
+            double ms = 0.0;
+            for (const fe_result &x : rs) ms = std::max(ms, x.ms);
+            if (r > 0) best = std::min(best, ms);
+        }
+        *out = best;
+        return FE_OK;
+    };
+    auto set_bn = [&](const std::pair<int, uint32_t> &c, int bn) {
+        std::lock_guard<std::mutex> tl(ctx->tmu);
+        ctx->tune[c] = TuneEnt{bn, 0.0, 0.0};
+    };
+    int nt = 0;
+    auto log = [&](double ms) {
+        if (nt < max_trials) trial_ms[nt] = ms;
+        ++nt;
+    };
+    double best = 0.0;
+    int rc = time_batch(&best);
+    if (rc == FE_OK) log(best);
+    // narrow tiles for the smallest classes, one class more per trial, while
+    // the batch gets faster (by more than 0.5%)
+    for (size_t c = 0; c < cls.size() && rc == FE_OK; ++c) {
+        set_bn(cls[c], kTileM);
+        double ms = 0.0;
+        rc = time_batch(&ms);
+        if (rc != FE_OK) break;
+        log(ms);
+        if (ms < best * 0.995) {
+            best = ms;
+        } else {
+            set_bn(cls[c], kTileN);
+            break;
+        }
+    }
+    if (ntrials) *ntrials = nt;
+    std::lock_guard<std::mutex> tl(ctx->tmu);
+    if (rc != FE_OK) {
+        for (const auto &c : cls) {
+            auto it = saved.find(c);
+            if (it != saved.end()) ctx->tune[c] = it->second;
+            else ctx->tune.erase(c);
+        }
+        return rc;
+    }
+    return save_tune(ctx);
+}
+
+extern "C" int fe_k_set_tile_width(fe_ctx *ctx, int64_t n, uint32_t prec, int bn) {
+    if (!ctx || n < 1 || (prec & ~FE_PREC_MASK) != 0 || (bn != 0 && bn != kTileM && bn != kTileN))
+        return set_err(ctx, FE_EINVAL, "bad arguments");
+    const int T = static_cast<int>((n + kTileM - 1) / kTileM);
+    std::lock_guard<std::mutex> tl(ctx->tmu);
+    if (bn == 0) ctx->tune.erase({T, prec});
+    else ctx->tune[{T, prec}] = TuneEnt{bn, 0.0, 0.0};
+    return FE_OK;
+}
+
+extern "C" int fe_k_tile_width(fe_ctx *ctx, int64_t n, uint32_t prec, int *bn) {
+    if (!ctx || !bn || n < 1 || (prec & ~FE_PREC_MASK) != 0) return set_err(ctx, FE_EINVAL, "bad arguments");
+    *bn = tile_width(ctx, n, prec);
     return FE_OK;
 }

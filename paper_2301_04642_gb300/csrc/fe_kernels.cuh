@@ -33,8 +33,8 @@ struct MmaProb {
     MatSlot mats[kNumMats];
     SolveState *st;
     double *part;                    // per-tile partial slots (kPartStride doubles each)
-    int n, ldy, lds, ntiles;
-    int ntiles64, pad1;
+    int n, ldy, lds, ntiles;         // ntiles: tensor-core tiles of the problem's tile width
+    int ntiles64, bn;                // bn: tensor-core tile width, 128 or 256 columns
     int tc_tile0, tc_ntiles;         // this problem's range in the launch's tensor-core tile list
     float *lzv;                      // Lanczos vectors: v_prev, v, w (n FP32 each)
     float *Y;                        // FP32 master of the zero-temperature iterate
@@ -49,7 +49,8 @@ struct MmaProb {
     int ntilesD, padD;
 };
 
-// One tensor-core tile: rows [I*128, I*128+128) x columns [Jp*256, Jp*256+256).
+// One tensor-core tile: rows [I*128, I*128+128) x columns [Jp*bn, Jp*bn+bn)
+// for the problem's tile width bn (256: 2Jp + 1 >= I; 128: Jp >= I).
 struct TileEnt {
     int prob;
     int I;

@@ -15,8 +15,10 @@
 // squares used as the idempotency measure ||X^2 - X||_F^2).  The step to run
 // is described by the ProdOp the control kernel wrote into the solve state.
 //
-// One persistent CTA per SM walks a list of tiles (of one or many problems):
-// 128 rows (block I) x 256 columns (blocks 2Jp, 2Jp+1).
+// One persistent CTA per SM walks a list of tiles (of one or many problems).
+// A problem's tile width bn is 256 (128 rows of block I x the blocks 2Jp,
+// 2Jp+1) or 128 (block I x block J = Jp, J >= I), as the host's tile-shape
+// table chose for its n; one launch may mix both.
 //
 // Accuracy: the tensor core adds every MMA into its FP32 accumulator with a
 // one-sided rounding, so an accumulator that lives for the whole K loop
@@ -29,13 +31,13 @@
 //
 // Warp roles (384 threads; warpgroup 0 hands registers to warpgroups 1-2):
 //   warp 0      TMA producer: per K chunk one box per slice for the A panel
-//               (128 rows) and the B panel (256 rows).
+//               (128 rows) and the B panel (bn rows).
 //   warp 1      TMEM owner and MMA issuer: per chunk 4 x (1 or 3) MMAs
-//               M128 N256 K16 into one of two chunk buffers (2 x 256 cols).
+//               M128 Nbn K16 into one of two chunk buffers (2 x 256 cols).
 //   warps 2-3   idle (give their registers away)
 //   warps 4-11  drain + epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
-//               and columns 128 ((w - 4) / 4) .. +127, i.e. one 128x128 block,
-//               two 64-column loads per chunk.
+//               and the columns bn/2 ((w - 4) / 4) .. +bn/2-1 (one 128x128
+//               block, or half of one when bn = 128) in 64-column loads.
 // Every wait is bounded; on a timeout the kernel records an error code,
 // drains its own copies and MMAs, frees TMEM and returns.
 #include "fe_dev.cuh"
@@ -50,6 +52,20 @@ struct alignas(1024) StageSmem {
     uint8_t b[kMaxSlices][kSliceBBytes];
 };
 
+// The launch's schedule table, in shared memory when the launch has at most
+// kSchedProbs problems: per problem (table order) the inclusive prefix sums
+// of active tiles and of work units, and the units of one of its tiles (0:
+// no tensor-core work in this step).  Built once per launch; without it every
+// tile hand-out would walk the problem table in global memory, a chain of
+// dependent loads per problem.
+constexpr int kSchedProbs = 256;
+struct SchedTab {
+    long long units[kSchedProbs];
+    int tiles[kSchedProbs];
+    int w[kSchedProbs];
+    int bnmin, wmin, wmax, pad;
+};
+
 struct MmaSmemTail {
     uint64_t full[kStages];
     uint64_t empty[kStages];
@@ -61,6 +77,7 @@ struct MmaSmemTail {
     int vote[kEpiWarps];
     int sk_ticket, sk_ok;             // split-tile hand-off (drain warp 0 writes, all read)
     double stage[kEpiWarps][32 * 9];  // per-warp staging of 32 rows x 8 columns (direct writes)
+    SchedTab sch;
 };
 
 constexpr size_t kMmaSmemBytes = 1024 + sizeof(StageSmem) * kStages + sizeof(MmaSmemTail);
@@ -78,6 +95,9 @@ __device__ __forceinline__ bool tile_active(const SolveState *st) {
 __device__ __forceinline__ int step_chunks(const SolveState *st, int n) {
     return step_kind(st) == kTcElem ? 0 : (n + kTileK - 1) / kTileK;
 }
+
+// tile width of a problem: 128 or 256 columns
+__device__ __forceinline__ int tile_bn(const MmaProb &pr) { return pr.bn == kTileM ? kTileM : kTileN; }
 
 __device__ __forceinline__ void record_error(int *err, int code) { atomicCAS(err, 0, code); }
 
@@ -109,7 +129,9 @@ __device__ __forceinline__ void put_slices(const MatSlot &m, size_t at, float ys
 
 // ---- Schedule: data-parallel waves, then Stream-K.  The launch's work is the
 // sequence, over the active problems in table order, of their tiles, each
-// worth `units` = its 64-wide K chunks (1 for an epilogue-only step).
+// worth `units` = its 64-wide K chunks (1 for an epilogue-only step) times its
+// width over the narrowest width in the launch (so a 128 x 256 tile weighs
+// twice a 128 x 128 one when both are present).
 // When every tile is worth the same and there are at least two waves, whole
 // waves go first, tile t to CTA t mod grid: all CTAs then step through K
 // together on tiles that are neighbours in the list (the host orders tiles in
@@ -120,8 +142,9 @@ __device__ __forceinline__ void put_slices(const MatSlot &m, size_t at, float ys
 // phases) fall at different times in different CTAs and the last wave is not
 // left half empty.  At most G = W / (largest tile) CTAs take part, so a tile
 // spans at most two ranges: a head segment at the end of one CTA's range and
-// a tail segment at the start of the next one's.  Every role of a CTA walks
-// the same segments.
+// a tail segment at the start of the next one's.  A chunk worth f units
+// belongs to the range that holds its first unit; a range part that holds no
+// chunk's first unit is skipped.  Every role of a CTA walks the same segments.
 struct Seg {
     int tile;   // index into the launch's tile list
     int prob;   // index of its problem in the launch's table
@@ -131,30 +154,153 @@ struct Seg {
     bool head;  // this CTA has its first chunks (else its last)
 };
 
-__device__ __forceinline__ int tile_units(const MmaProb &pr) {
+// chunks of a tile, counting an epilogue-only step's tile as one
+__device__ __forceinline__ int tile_chunks(const MmaProb &pr) {
     const int nk = step_chunks(pr.st, pr.n);
     return nk > 0 ? nk : 1;
 }
 
+// Fill the schedule table (every thread of the CTA calls this between two
+// CTA barriers, `warp0` says whether it is in warp 0).  Pass 1, all threads:
+// chunks, width and tiles of each problem.  Pass 2, warp 0 after a barrier:
+// the narrowest width, the units per tile, and prefix sums (each lane scans
+// a contiguous run of problems, then the run totals are scanned across the
+// warp).
+__device__ void sched_pass1(SchedTab *t, const MmaProb *probs, int np) {
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+        const MmaProb &pr = probs[q];
+        const bool act = pr.tc_ntiles > 0 && tile_active(pr.st);
+        t->w[q] = act ? tile_chunks(pr) : 0;
+        t->tiles[q] = act ? pr.tc_ntiles : 0;
+        t->units[q] = act ? tile_bn(pr) : 0;
+    }
+}
+
+__device__ void sched_pass2(SchedTab *t, int np, int lane) {
+    int bm = kTileN;
+    for (int q = lane; q < np; q += 32)
+        if (t->w[q] > 0) bm = static_cast<int>(t->units[q]) < bm ? static_cast<int>(t->units[q]) : bm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int y = __shfl_xor_sync(0xffffffffu, bm, o);
+        bm = y < bm ? y : bm;
+    }
+    const int per = (np + 31) / 32;
+    const int q0 = lane * per, q1 = (q0 + per < np) ? q0 + per : np;
+    long long su = 0;
+    int st = 0, wmin = 0x7fffffff, wmax = 1;
+    for (int q = q0; q < q1; ++q) {
+        const int c = t->w[q];
+        const int w = c > 0 ? c * (static_cast<int>(t->units[q]) / bm) : 0;
+        if (c > 0) {
+            wmin = w < wmin ? w : wmin;
+            wmax = w > wmax ? w : wmax;
+        }
+        su += static_cast<long long>(t->tiles[q]) * w;
+        st += t->tiles[q];
+        t->w[q] = w;
+        t->units[q] = su;
+        t->tiles[q] = st;
+    }
+    long long eu = su;
+    int et = st;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long yu = __shfl_up_sync(0xffffffffu, eu, o);
+        const int yt = __shfl_up_sync(0xffffffffu, et, o);
+        if (lane >= o) {
+            eu += yu;
+            et += yt;
+        }
+    }
+    eu -= su;
+    et -= st;
+    for (int q = q0; q < q1; ++q) {
+        t->units[q] += eu;
+        t->tiles[q] += et;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int a = __shfl_xor_sync(0xffffffffu, wmin, o);
+        const int b = __shfl_xor_sync(0xffffffffu, wmax, o);
+        wmin = a < wmin ? a : wmin;
+        wmax = b > wmax ? b : wmax;
+    }
+    if (lane == 0) {
+        t->bnmin = bm;
+        t->wmin = wmin;
+        t->wmax = wmax;
+    }
+}
+
 struct SegIter {
     const MmaProb *probs;
+    const SchedTab *tab;   // the shared-memory table, or null: walk the table in global memory
     int nprobs;
+    int bnmin;             // narrowest tile width among the active problems
     long long dp, dp_end;  // data-parallel part: next tile index (over active tiles), end
     long long g, end;      // Stream-K part: this CTA's range of work units
 
-    __device__ void init(const MmaProb *p, int np) {
+    __device__ int unit_f(const MmaProb &pr) const { return tile_bn(pr) / bnmin; }
+    __device__ int tile_units(const MmaProb &pr) const { return tile_chunks(pr) * unit_f(pr); }
+
+    // the problem holding active tile r (tiles = true) or work unit r of the
+    // launch, with r made relative to the problem's first; nprobs if none
+    __device__ int find(long long &r, bool tiles) const {
+        if (nprobs <= 0) return nprobs;
+        if (tab) {
+            int lo = 0, hi = nprobs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const long long v = tiles ? tab->tiles[mid] : tab->units[mid];
+                if (v > r) hi = mid;
+                else lo = mid + 1;
+            }
+            const long long v = tiles ? tab->tiles[lo] : tab->units[lo];
+            if (v <= r) return nprobs;
+            if (lo > 0) r -= tiles ? tab->tiles[lo - 1] : tab->units[lo - 1];
+            return lo;
+        }
+        for (int q = 0; q < nprobs; ++q) {
+            const MmaProb &pr = probs[q];
+            if (pr.tc_ntiles == 0 || !tile_active(pr.st)) continue;
+            const long long span = tiles ? pr.tc_ntiles : static_cast<long long>(pr.tc_ntiles) * tile_units(pr);
+            if (r < span) return q;
+            r -= span;
+        }
+        return nprobs;
+    }
+
+    __device__ void init(const MmaProb *p, int np, const SchedTab *t) {
         probs = p;
         nprobs = np;
+        tab = t;
         long long W = 0, T = 0;
         int wmax = 1, wmin = 0x7fffffff;
-        for (int q = 0; q < np; ++q) {
-            const MmaProb &pr = p[q];
-            if (pr.tc_ntiles == 0 || !tile_active(pr.st)) continue;
-            const int w = tile_units(pr);
-            W += static_cast<long long>(pr.tc_ntiles) * w;
-            T += pr.tc_ntiles;
-            wmax = w > wmax ? w : wmax;
-            wmin = w < wmin ? w : wmin;
+        if (t) {
+            bnmin = t->bnmin;
+            if (np > 0) {
+                W = t->units[np - 1];
+                T = t->tiles[np - 1];
+            }
+            wmin = t->wmin;
+            wmax = t->wmax;
+        } else {
+            bnmin = kTileN;
+            for (int q = 0; q < np; ++q) {
+                const MmaProb &pr = p[q];
+                if (pr.tc_ntiles == 0 || !tile_active(pr.st)) continue;
+                bnmin = tile_bn(pr) < bnmin ? tile_bn(pr) : bnmin;
+            }
+            for (int q = 0; q < np; ++q) {
+                const MmaProb &pr = p[q];
+                if (pr.tc_ntiles == 0 || !tile_active(pr.st)) continue;
+                const int w = tile_units(pr);
+                W += static_cast<long long>(pr.tc_ntiles) * w;
+                T += pr.tc_ntiles;
+                wmax = w > wmax ? w : wmax;
+                wmin = w < wmin ? w : wmin;
+            }
         }
         const long long grid = gridDim.x;
         const long long b = blockIdx.x;
@@ -178,43 +324,40 @@ struct SegIter {
         if (dp < dp_end) {
             long long r = dp;
             dp += gridDim.x;
-            for (int q = 0; q < nprobs; ++q) {
+            const int q = find(r, true);
+            if (q < nprobs) {
                 const MmaProb &pr = probs[q];
-                if (pr.tc_ntiles == 0 || !tile_active(pr.st)) continue;
-                if (r < pr.tc_ntiles) {
-                    sg.tile = pr.tc_tile0 + static_cast<int>(r);
-                    sg.prob = q;
-                    sg.k0 = 0;
-                    sg.nch = (step_chunks(pr.st, pr.n) > 0) ? tile_units(pr) : 0;
-                    sg.split = false;
-                    sg.head = true;
-                    return true;
-                }
-                r -= pr.tc_ntiles;
+                sg.tile = pr.tc_tile0 + static_cast<int>(r);
+                sg.prob = q;
+                sg.k0 = 0;
+                sg.nch = (step_chunks(pr.st, pr.n) > 0) ? tile_chunks(pr) : 0;
+                sg.split = false;
+                sg.head = true;
+                return true;
             }
             dp = dp_end;
         }
-        if (g >= end) return false;
-        long long r = g;
-        for (int q = 0; q < nprobs; ++q) {
+        while (g < end) {
+            long long r = g;
+            const int q = find(r, false);
+            if (q == nprobs) break;
             const MmaProb &pr = probs[q];
-            if (pr.tc_ntiles == 0 || !tile_active(pr.st)) continue;
-            const int w = tile_units(pr);
-            const long long span = static_cast<long long>(pr.tc_ntiles) * w;
-            if (r < span) {
-                const int k = static_cast<int>(r % w);
-                const long long left = end - g;
-                const int k1 = (left < w - k) ? k + static_cast<int>(left) : w;
-                sg.tile = pr.tc_tile0 + static_cast<int>(r / w);
-                sg.prob = q;
-                sg.k0 = k;
-                sg.nch = (step_chunks(pr.st, pr.n) > 0) ? k1 - k : 0;
-                sg.split = (k > 0) || (k1 < w);
-                sg.head = (k == 0);
-                g += k1 - k;
-                return true;
-            }
-            r -= span;
+            const int f = unit_f(pr);
+            const int w = tab ? tab->w[q] : tile_units(pr);
+            const int nkc = w / f;
+            const int ku = static_cast<int>(r % w);   // first unit of this range in the tile
+            const long long left = end - g;
+            const int k1u = (left < w - ku) ? ku + static_cast<int>(left) : w;
+            g += k1u - ku;
+            const int k = (ku + f - 1) / f, k1 = (k1u + f - 1) / f;  // chunks starting in [ku, k1u)
+            if (k == k1) continue;
+            sg.tile = pr.tc_tile0 + static_cast<int>(r / w);
+            sg.prob = q;
+            sg.k0 = k;
+            sg.nch = (step_chunks(pr.st, pr.n) > 0) ? k1 - k : 0;
+            sg.split = (k > 0) || (k1 < nkc);
+            sg.head = (k == 0);
+            return true;
         }
         g = end;
         return false;
@@ -264,10 +407,14 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         tail->abort_flag = 0;
         fence_barrier_init();
     }
+    const SchedTab *tab = (nprobs <= kSchedProbs) ? &tail->sch : nullptr;
+    if (tab) sched_pass1(&tail->sch, probs, nprobs);
     if (warp == 1) tmem_alloc(&tail->tmem_base, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (tab && warp == 0) sched_pass2(&tail->sch, nprobs, lane);
+    __syncthreads();
     const uint32_t tmem_base = tail->tmem_base;
 
     if (warp < kSymEpiWarp0) setmaxnreg_dec<kSymRegsLow>();
@@ -279,7 +426,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         bool issued[kStages];
         for (int s = 0; s < kStages; ++s) { issued[s] = false; last_phase[s] = 0; }
         SegIter it;
-        it.init(probs, nprobs);
+        it.init(probs, nprobs, tab);
         Seg sg;
         while (ok && it.next(sg)) {
             if (sg.tile >= ntiles) break;
@@ -289,7 +436,9 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             const int S = (step_kind(st) == kTcSplit) ? 2 : 1;
             const MatSlot &ma = pr.mats[st->op.A];
             const MatSlot &mb = pr.mats[st->op.B];
-            const uint32_t bytes = static_cast<uint32_t>(S * (kSliceABytes + kSliceBBytes));
+            const bool wide = tile_bn(pr) == kTileN;
+            const CUtensorMap *tmb = wide ? mb.tmB : mb.tmA;  // B panel: 256 or 128 rows
+            const uint32_t bytes = static_cast<uint32_t>(S * (kSliceABytes + (wide ? kSliceBBytes : kSliceABytes)));
             for (int kc = sg.k0; kc < sg.k0 + sg.nch; ++kc) {
                 bool got = true;
                 if (lane == 0) got = mbar_wait_bounded(&tail->empty[stage], phase ^ 1u);
@@ -304,8 +453,8 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                     for (int s = 0; s < S; ++s) {
                         tma_load_2d(stages[stage].a[s], &ma.tmA[s], &tail->full[stage],
                                     kc * kTileK, te.I * kTileM);
-                        tma_load_2d(stages[stage].b[s], &mb.tmB[s], &tail->full[stage],
-                                    kc * kTileK, te.Jp * kTileN);
+                        tma_load_2d(stages[stage].b[s], &tmb[s], &tail->full[stage],
+                                    kc * kTileK, te.Jp * (wide ? kTileN : kTileM));
                     }
                 }
                 __syncwarp();
@@ -329,9 +478,10 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         uint32_t chunk = 0;  // chunk counter of this CTA: buffer = chunk & 1
         bool ok = true;
         bool any_commit = false;
-        constexpr uint32_t idesc = idesc_f16(kTileM, kTileN, 0);
+        constexpr uint32_t idesc_w = idesc_f16(kTileM, kTileN, 0);
+        constexpr uint32_t idesc_n = idesc_f16(kTileM, kTileM, 0);
         SegIter it;
-        it.init(probs, nprobs);
+        it.init(probs, nprobs, tab);
         Seg sg;
         while (ok && it.next(sg)) {
             if (sg.tile >= ntiles) break;
@@ -339,6 +489,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             const MmaProb &pr = probs[sg.prob];
             const SolveState *st = pr.st;
             const int S = (step_kind(st) == kTcSplit) ? 2 : 1;
+            const uint32_t idesc = (tile_bn(pr) == kTileN) ? idesc_w : idesc_n;
             for (int kc = sg.k0; kc < sg.k0 + sg.nch; ++kc) {
                 const uint32_t buf = chunk & 1u;
                 const uint32_t cph = (chunk >> 1) & 1u;
@@ -405,12 +556,12 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         setmaxnreg_inc<kSymRegsHigh>();
         const int ew = warp - kSymEpiWarp0;    // 0..7
         const int q = warp & 3;                // TMEM lane quadrant (hardware rule: warp % 4)
-        const int h = ew >> 2;                 // column half: 128-block 2Jp + h
+        const int h = ew >> 2;                 // column half of the tile
         const int row_local = q * 32 + lane;
         uint32_t chunk = 0;
         bool ok = true;
         SegIter it;
-        it.init(probs, nprobs);
+        it.init(probs, nprobs, tab);
         Seg sg;
         while (ok && it.next(sg)) {
             if (sg.tile >= ntiles) break;
@@ -418,6 +569,8 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             const MmaProb &pr = probs[sg.prob];
             const SolveState *st = pr.st;
             const int n = pr.n;
+            const bool wide = tile_bn(pr) == kTileN;
+            const int ncol = wide ? 128 : 64;  // columns of this warp's strip
             float acc[128];
 #pragma unroll
             for (int c = 0; c < 128; ++c) acc[c] = 0.0f;
@@ -433,13 +586,15 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
-                                       buf * kTileN + static_cast<uint32_t>(h * 128);
+                                       buf * kTileN + static_cast<uint32_t>(h * ncol);
 #pragma unroll
                 for (int c2 = 0; c2 < 2; ++c2) {
-                    float v[64];
-                    tmem_ld64(tbase + c2 * 64, v);
+                    if (c2 * 64 < ncol) {
+                        float v[64];
+                        tmem_ld64(tbase + c2 * 64, v);
 #pragma unroll
-                    for (int u = 0; u < 64; ++u) acc[c2 * 64 + u] += v[u];
+                        for (int u = 0; u < 64; ++u) acc[c2 * 64 + u] += v[u];
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -474,7 +629,8 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 if (ticket == 0) {
 #pragma unroll
                     for (int c = 0; c < 32; ++c)
-                        wsp[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+                        if (4 * c < ncol)
+                            wsp[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
                     __threadfence();
                     epi_bar();
                     if (ew == 0 && lane == 0) atomicExch(&cnt[2 * slot + 1], 1);
@@ -492,6 +648,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 __threadfence();
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
+                    if (4 * c >= ncol) break;
                     const float4 p4 = __ldcg(wsp + c);
                     acc[4 * c] += p4.x;
                     acc[4 * c + 1] += p4.y;
@@ -505,7 +662,8 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 }
             }
 
-            // ---- store phase for block J = 2 Jp + h
+            // ---- store phase for the strip of block J (J = 2 Jp + h when bn =
+            // 256, else J = Jp and columns 64 h .. 64 h + 63 of it)
             // Lane = row i of the warp's 32-row strip.  The masters E1/E2 are
             // symmetric, so they are read at (j, i): lanes on consecutive
             // addresses.  Mirrored writes (j, i) are coalesced the same way;
@@ -523,13 +681,15 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             const float ra = op.ra, rb = op.rb, rc = op.rc;
             const int i0 = te.I * kTileM + q * 32;
             const int i = i0 + lane;
-            const int J = 2 * te.Jp + h;
+            const int J = wide ? 2 * te.Jp + h : te.Jp;
+            const int cb = J * kTileM + (wide ? 0 : 64 * h);  // first column of the strip
+            const int ng = ncol / 8;                            // its 8-column groups
             double tr = 0.0, sq = 0.0, tr1 = 0.0, rr = 0.0;
             double *stg = tail->stage[ew];
             float *stf = reinterpret_cast<float *>(stg);
             const int rsub = lane >> 3, csub = lane & 7;  // direct-write lane layout
             const bool lean = nout == 1 && pout == 0 && !E2 && op.out[0].flags == (kOutMaster | kOutSlices);
-            if (lean && J >= te.I && J * kTileM < n && i0 < n) {
+            if (lean && J >= te.I && cb < n && i0 < n) {
                 // the zero-temperature step: one output a v + b1 E1 + c [i == j].
                 // An 8-column group wholly inside the matrix and above the
                 // diagonal (every element exists and counts twice) takes the
@@ -551,21 +711,21 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 // above the diagonal; its E1 row segment is loaded one group
                 // ahead, so the load's latency overlaps the previous group
                 auto vec_group = [&](int c) {
-                    const int jc = J * kTileM + c * 8;
+                    const int jc = cb + c * 8;
                     return i0 + 32 <= n && jc + 8 <= n && (!diag || jc >= i0 + 32);
                 };
                 float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
                 if (vec_group(0)) {
-                    const size_t r0 = static_cast<size_t>(i) * ldy + J * kTileM;
+                    const size_t r0 = static_cast<size_t>(i) * ldy + cb;
                     pa = *reinterpret_cast<const float4 *>(E1 + r0);
                     pb = *reinterpret_cast<const float4 *>(E1 + r0 + 4);
                 }
 #pragma unroll
                 for (int c8 = 0; c8 < kTileM / 8; ++c8) {
-                    const int j0 = J * kTileM + c8 * 8;
-                    if (j0 >= n) break;
+                    const int j0 = cb + c8 * 8;
+                    if (c8 >= ng || j0 >= n) break;
                     const float4 ea = pa, eb = pb;  // this group's E1 (when it is a vector group)
-                    if (c8 + 1 < kTileM / 8 && vec_group(c8 + 1)) {
+                    if (c8 + 1 < ng && vec_group(c8 + 1)) {
                         const size_t rn = static_cast<size_t>(i) * ldy + j0 + 8;
                         pa = *reinterpret_cast<const float4 *>(E1 + rn);
                         pb = *reinterpret_cast<const float4 *>(E1 + rn + 4);
@@ -654,7 +814,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                     }
                     __syncwarp();
                 }
-            } else if (J >= te.I && J * kTileM < n && i0 < n) {
+            } else if (J >= te.I && cb < n && i0 < n) {
                 // any other step (1-3 outputs, E1/E2, FP64 outputs): groups
                 // wholly above the diagonal take the 16-byte path as in the
                 // zero-temperature step (one output after another; an output
@@ -665,8 +825,8 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 const int mr = lane >> 2, mc = (lane & 3) * 8;
 #pragma unroll
                 for (int c8 = 0; c8 < kTileM / 8; ++c8) {
-                    const int j0 = J * kTileM + c8 * 8;
-                    if (j0 >= n) break;
+                    const int j0 = cb + c8 * 8;
+                    if (c8 >= ng || j0 >= n) break;
                     if (diag && j0 + 7 < i0) continue;  // strictly below the diagonal
                     if (!has_f64 && i0 + 32 <= n && j0 + 8 <= n && (!diag || j0 >= i0 + 32)) {
                         const size_t ro = static_cast<size_t>(i) * ldy + j0;

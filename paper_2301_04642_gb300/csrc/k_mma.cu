@@ -52,7 +52,7 @@ struct alignas(1024) StageSmem {
     uint8_t b[kMaxSlices][kSliceBBytes];
 };
 
-// The launch's schedule table, in shared memory when the launch has at most
+// The launch's schedule table, in shared memory when the launch has 2 to
 // kSchedProbs problems: per problem (table order) the inclusive prefix sums
 // of active tiles and of work units, and the units of one of its tiles (0:
 // no tensor-core work in this step).  Built once per launch; without it every
@@ -407,14 +407,17 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         tail->abort_flag = 0;
         fence_barrier_init();
     }
-    const SchedTab *tab = (nprobs <= kSchedProbs) ? &tail->sch : nullptr;
+    // (one problem: its table entry is read directly)
+    const SchedTab *tab = (nprobs > 1 && nprobs <= kSchedProbs) ? &tail->sch : nullptr;
     if (tab) sched_pass1(&tail->sch, probs, nprobs);
     if (warp == 1) tmem_alloc(&tail->tmem_base, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tab && warp == 0) sched_pass2(&tail->sch, nprobs, lane);
-    __syncthreads();
+    if (tab) {
+        if (warp == 0) sched_pass2(&tail->sch, nprobs, lane);
+        __syncthreads();
+    }
     const uint32_t tmem_base = tail->tmem_base;
 
     if (warp < kSymEpiWarp0) setmaxnreg_dec<kSymRegsLow>();

@@ -57,6 +57,8 @@ WORKLOADS = {
                                                          device="cuda", name="gapped_n16384"),
                           precision="mixed"),
     "fermi_n16384": dict(make=lambda: hp_synth.workload_n16384_ft(device="cuda"), precision="mixed"),
+    # the paper's own synthetic Hamiltonian (Sec. IV), N_e = 0.9 n: a continuous band, gap ~1.4/n
+    "paper_matrix_n8192": dict(make=lambda: hp_synth.paper_matrix(8192, device="cuda"), precision="mixed"),
     # many problems per step (see bench_batch / bench_serve)
     "ragged_batch64": dict(make=None, precision="mixed"),
     "serve_poisson": dict(make=None, precision="mixed"),
@@ -255,7 +257,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        if wl["make"] is None or args.workload in ("gapped_n8192", "gapped_n16384", "fermi_n16384"):
+        if wl["make"] is None or args.workload in ("gapped_n8192", "gapped_n16384", "fermi_n16384",
+                                                   "paper_matrix_n8192"):
             print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm is timed on the "
                               "single-solve workloads gapped_n4096 and gapped_n256_fp64"}), flush=True)
             return
@@ -321,7 +324,18 @@ def main():
     t_ms = e0.elapsed_time(e1)
     # the last timed solve's error against the constructed reference (outside the timing)
     torch.cuda.synchronize()
-    accuracy = probe_errors(torch, D, p.Q, p.lam, reference_occupations(p.lam, p.ne, kT), p.ne, kT, r)
+    if p.Q is None:
+        # a matrix given by a formula: the reference eigenpairs come from
+        # cuSOLVER syevd (FP64) on this GPU, outside the timing
+        lam_ref, Q_ref = torch.linalg.eigh(H)
+        accuracy = probe_errors(torch, D, Q_ref, lam_ref.cpu().numpy(),
+                                reference_occupations(lam_ref.cpu().numpy(), p.ne, kT), p.ne, kT, r)
+        accuracy["reference"] = "cuSOLVER syevd (FP64) eigenpairs"
+        gap_at_ne = float(lam_ref[int(p.ne)] - lam_ref[int(p.ne) - 1]) if 0 < p.ne < n else None
+        del Q_ref
+    else:
+        accuracy = probe_errors(torch, D, p.Q, p.lam, reference_occupations(p.lam, p.ne, kT), p.ne, kT, r)
+        gap_at_ne = None
     if dist:
         tt = torch.tensor([t_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -421,7 +435,7 @@ def main():
            "config": {"workload": args.workload, "n": n, "n_e": p.ne, "kT": kT,
                       "precision": prec, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "256 MiB buffer written before every step; working set > 129 MB L2",
-                      "tiles": tiles},
+                      "tiles": tiles, "gap_at_ne": gap_at_ne},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
            "phases_ms": phases,
            "effective_tflops": iters * 2.0 * n ** 3 * value / 1e12,
@@ -432,7 +446,7 @@ def main():
            "gpu_launches": launches, "roofline": roof, "kernels": kernels,
            "clocks": clk.summary()}
 
-    small_zero_t = n <= 4096 and kT == 0.0  # plain FP64 / syevd / CPU arms only where they finish
+    small_zero_t = n <= 4096 and kT == 0.0 and p.Q is not None  # plain FP64 / syevd / CPU arms only where they finish
     if rank == 0 and not args.no_baselines and small_zero_t:
         base = {}
         # the same expansion with every product in FP64 on this GPU

@@ -110,11 +110,12 @@ def assemble(Q, lam):
 
 
 class Problem:
-    """One synthetic solve: Hp with its exact eigendecomposition."""
+    """One synthetic solve: Hp with its exact eigendecomposition (Q, lam), or
+    Q = lam = None for a matrix given by a formula."""
 
     def __init__(self, name, H, Q, lam, ne, kT, tol, seed):
         self.name, self.H, self.Q, self.lam = name, H, Q, lam
-        self.n = lam.shape[0]
+        self.n = H.shape[0]
         self.ne, self.kT, self.tol, self.seed = ne, kT, tol, seed
 
     def __repr__(self):
@@ -171,3 +172,21 @@ def ragged_member(i, seed=2000, device=None, lo=512, hi=6144):
     ne = int(round(0.85 * n))
     return gapped(n, ne, (-3.0, -gap / 2), (gap / 2, 1.0), seed + i, device=device,
                   name="ragged_%d" % i)
+
+
+def paper_matrix(n, frac=0.9, tol=5e-8, device=None):
+    """The synthetic Hamiltonian of the paper's scaling runs (Sec. IV):
+    H_ij = exp(-0.5 |i - j|) sin(i + 1) as printed is not symmetric; the reading
+    used here takes the smaller index, H_ij = H_ji = exp(-0.5 |i - j|)
+    sin(min(i, j) + 1), 0-based indices, radians.  N_e = round(frac n) (0.9 at
+    zero temperature).  Its spectrum is a continuous band in [-1.87, 1.87]:
+    the gap at N_e = 0.9 n is about 1.4 / n."""
+    ne = float(int(round(frac * n)))
+    if device is None:
+        i = np.arange(n, dtype=np.float64)
+        H = np.exp(-0.5 * np.abs(i[:, None] - i[None, :])) * np.sin(np.minimum(i[:, None], i[None, :]) + 1.0)
+    else:
+        import torch
+        i = torch.arange(n, dtype=torch.float64, device=device)
+        H = torch.exp(-0.5 * (i[:, None] - i[None, :]).abs()) * torch.sin(torch.minimum(i[:, None], i[None, :]) + 1.0)
+    return Problem("paper_matrix_n%d" % n, H, None, None, ne, 0.0, tol, 0)

@@ -65,6 +65,22 @@ def test_mixed_medium(n, ne):
     assert m["tr_err"] <= TOL_TR and m["idem"] <= TOL_IDEM
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_paper_matrix_n1000(precision):
+    """The paper's own synthetic Hamiltonian (Sec. IV) at N_e = 0.9 n: a
+    continuous band whose gap at N_e is 1.4e-3 Ha at n = 1000 (against 3.7 Ha
+    of spectrum), far narrower than the gapped workloads'.  D_ref from the
+    oracle's own eigensolver.  Measured: mixed eps1 6.2e-7 (44 + 2 products),
+    FP64 5.5e-14."""
+    p = hp_synth.paper_matrix(1000)
+    D, res = run(p, precision)
+    m = check_zero_t(p, D, res, use_eig=True)
+    print(precision, res["iters_by_phase"], m)
+    assert res["status"] == 0
+    assert m["eps1"] <= TOL_EPS1 and m["e_err"] <= TOL_E
+    assert m["tr_err"] <= TOL_TR and m["idem"] <= TOL_IDEM
+
+
 @pytest.mark.parametrize("n,ne", [(300, 250), (1000, 850), (2000, 1500)])
 def test_try_fp16_reports_its_error(n, ne):
     """Single FP16 products while RelTr >= 5e-4 (Sec. III-A's switch point),

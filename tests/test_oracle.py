@@ -44,6 +44,21 @@ def test_semicircle_moments():
     assert lam.min() >= -1 and lam.max() <= 1
 
 
+def test_paper_matrix_entries():
+    """The paper's synthetic Hamiltonian (Sec. IV), read as symmetric with the
+    smaller index inside the sine: entries written out by hand."""
+    p = hp_synth.paper_matrix(40)
+    H = p.H
+    assert H.shape == (40, 40) and p.ne == 36.0 and p.Q is None and p.n == 40
+    assert np.array_equal(H, H.T)
+    assert H[0, 0] == math.sin(1.0)
+    assert H[7, 7] == math.sin(8.0)
+    assert abs(H[2, 5] - math.exp(-1.5) * math.sin(3.0)) < 1e-16
+    assert abs(H[5, 2] - math.exp(-1.5) * math.sin(3.0)) < 1e-16
+    assert abs(H[0, 39] - math.exp(-19.5) * math.sin(1.0)) < 1e-22
+    assert hp_synth.paper_matrix(100, 0.85).ne == 85.0
+
+
 # ---------------------------------------------------------------- eigensolvers
 
 @pytest.mark.parametrize("solver", [oracle.eigh_ql, oracle.eigh_jacobi])

@@ -195,6 +195,19 @@ def traffic_record(kernel_name, src_file):
     return rec.get("bytes_per_launch") if rec.get("src_sha256") == h else None
 
 
+def job_rate(torch, dist, device, steps, t_ms):
+    """Whole-job solves/s of the replicas: every rank solved `steps` problems
+    and the job lasted as long as its slowest rank (the maximum over ranks of
+    the timed region).  Returns (rate, slowest t_ms)."""
+    world = 1
+    if dist is not None:
+        tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        world = dist.get_world_size()
+    return world * steps / (t_ms / 1e3), t_ms
+
+
 def reference_occupations(lam, ne, kT):
     """Occupations of the constructed spectrum: the N_e lowest states at zero
     temperature, Fermi-Dirac with mu from bisection on sum f = N_e otherwise."""
@@ -336,11 +349,7 @@ def main():
     else:
         accuracy = probe_errors(torch, D, p.Q, p.lam, reference_occupations(p.lam, p.ne, kT), p.ne, kT, r)
         gap_at_ne = None
-    if dist:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * args.steps / (t_ms / 1e3)
+    value, t_ms = job_rate(torch, dist, dev, args.steps, t_ms)
 
     # ---- end to end through the C ABI with pinned host buffers
     Hh = (p.H.cpu() if torch.is_tensor(p.H) else torch.from_numpy(p.H)).pin_memory()
@@ -358,11 +367,7 @@ def main():
     f1.record(stream)
     torch.cuda.synchronize()
     te_ms = f0.elapsed_time(f1)
-    if dist:
-        tt = torch.tensor([te_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te_ms = float(tt.item())
-    e2e = world * args.steps / (te_ms / 1e3)
+    e2e, te_ms = job_rate(torch, dist, dev, args.steps, te_ms)
 
     # ---- per-kernel times (one profiled solve, CUDA events on the launch stream)
     ctx.profile(True)

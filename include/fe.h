@@ -130,8 +130,8 @@ typedef struct {
 } fe_tune;
 
 /* Create a context on cfg->device.  cfg may be NULL (defaults).
- * Errors: FE_EINVAL (bad device, unreadable or malformed autotune_path file),
- * FE_ECUDA. */
+ * Errors: FE_EINVAL (bad device, malformed autotune_path file; a file that
+ * cannot be opened starts an empty table), FE_ECUDA. */
 FE_API int fe_create(fe_ctx **out, const fe_config *cfg);
 
 /* Wait for outstanding work, free all device memory.  NULL is accepted. */

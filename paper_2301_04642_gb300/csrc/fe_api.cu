@@ -1,8 +1,9 @@
 // Host side of the C ABI declared in include/fe.h and include/fe_kernels.h.
 //
 // A context owns one CUDA stream, an HBM-budgeted pool of per-problem "slots"
-// (Hp copy, FP32 master, FP16 slice sets, FP64 buffers, partials, state) and
-// the launch sequences.  A solve (or a batch of solves) is:
+// (Hp copy, FP32 master, FP16 slice sets, FP64 buffers, partials, state), the
+// launch sequences and the tile-shape table (tensor-core tile width per
+// number of 128-row panels and precision policy, filled by the autotuners).  A solve (or a batch of solves) is:
 //   bounds rows + reduce + X0 init              (per problem)
 //   repeat:  control (1 block / problem)  ->  tensor-core step over the tiles
 //            of all problems  ->  FP64 step over the 64x64 tiles of all

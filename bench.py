@@ -172,8 +172,8 @@ def reference_arm(args, p, wl_name):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl_name, "n": p.n, "n_e": p.ne,
-                                             "parallelism": "replicas"},
+            "data": "synthetic", "config": {"workload": wl_name, "n": p.n, "n_e": p.ne, "kT": 0.0,
+                                             "parallelism": "replicas" if args.gpus > 1 else "single"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

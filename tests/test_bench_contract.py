@@ -1,0 +1,38 @@
+"""The benchmark's JSON contract on the paths that run without a GPU: the
+CPU reference arm (the oracle timed on the host cores) and its refusal on
+workloads it does not time."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench(*args, env=None):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + list(args),
+                       capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    d = _bench("--impl", "reference", "--workload", "gapped_n256_fp64", "--steps", "2", "--warmup", "3")
+    assert d["impl"] == "reference"
+    assert d["metric"] == "fermi_expansion_solves_per_s" and d["unit"] == "solves/s"
+    assert d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 3
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    assert d["config"]["workload"] == "gapped_n256_fp64" and d["config"]["n"] == 256
+    assert d["config"]["parallelism"] == "single"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_unavailable_on_large_workloads():
+    d = _bench("--impl", "reference", "--workload", "gapped_n16384")
+    assert d["impl"] == "reference" and "unavailable" in d

@@ -614,6 +614,7 @@ def bench_serve(args, torch, fe):
     # warm the kernels and slots on the first request
     t = ctx.submit(reqs[0][4], reqs[0][1], kT=reqs[0][2], tol=reqs[0][3], D=reqs[0][5])
     ctx.wait(t)
+    l0 = ctx.launch_count()
     with ClockSampler(0) as clk:
         t0 = time.perf_counter()
         tickets = []
@@ -625,6 +626,7 @@ def bench_serve(args, torch, fe):
             tickets.append(ctx.submit(H, ne, kT=kT, tol=tol, D=D))
         res = [ctx.wait(tk, timeout_s=1800) for tk in tickets]
         t1 = time.perf_counter()
+    launches = ctx.launch_count() - l0
     lat = [r["ms"] for r in res]
     ok = sum(1 for r in res if r["status"] == 0)
     value = ok / (t1 - t0)
@@ -635,7 +637,7 @@ def bench_serve(args, torch, fe):
                       "n": "log-uniform [1024, 8192]", "mix": "70% gapped, 30% finite T",
                       "parallelism": "single"},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-           "completed_ok": ok, "clocks": clk.summary(), "cpu_baseline": None}
+           "completed_ok": ok, "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": None}
     print(json.dumps(out), flush=True)
     ctx.close()
 

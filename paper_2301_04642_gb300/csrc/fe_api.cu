@@ -1826,6 +1826,17 @@ extern "C" int fe_autotune(fe_ctx *ctx, int count, const int64_t *ns, uint32_t p
         std::vector<fe_problem> ps(copies, p);
         std::vector<fe_result> rs(copies);
         double best[2] = {DBL_MAX, DBL_MAX};
+        // the entry before tuning, put back if a trial fails
+        bool had = false;
+        TuneEnt prev;
+        {
+            std::lock_guard<std::mutex> tl(ctx->tmu);
+            auto it = ctx->tune.find({T, prec});
+            if (it != ctx->tune.end()) {
+                had = true;
+                prev = it->second;
+            }
+        }
         // a warm-up batch per width (slots, graph), then `reps` rounds taking turns
         for (int r = 0; r <= reps && rc == FE_OK; ++r)
             for (int w = 0; w < 2 && rc == FE_OK; ++w) {
@@ -1841,7 +1852,8 @@ extern "C" int fe_autotune(fe_ctx *ctx, int count, const int64_t *ns, uint32_t p
         cudaFree(dH);
         std::lock_guard<std::mutex> tl(ctx->tmu);
         if (rc != FE_OK) {
-            ctx->tune.erase({T, prec});
+            if (had) ctx->tune[{T, prec}] = prev;
+            else ctx->tune.erase({T, prec});
             return rc;
         }
         ctx->tune[{T, prec}] = TuneEnt{best[1] < best[0] ? kTileM : kTileN, best[0], best[1]};

@@ -588,15 +588,18 @@ def bench_batch(args, torch, fe):
 
 def bench_serve(args, torch, fe):
     """Continuous batching: Poisson arrivals of mixed zero-T / finite-T requests
-    (n log-uniform in [1024, 8192]: the sub-capacity variant of the serving
-    configuration), submitted at their arrival times; latency = submit to done."""
+    (by default n log-uniform in [1024, 8192] at 20/s: the sub-capacity variant
+    of the serving configuration; FE_SERVE_NMAX=32768 FE_SERVE_RATE=200 asks for
+    the full one), submitted at their arrival times; latency = submit to done."""
     dev = torch.device("cuda", 0)
     rate = float(os.environ.get("FE_SERVE_RATE", "20"))
     count = int(os.environ.get("FE_SERVE_COUNT", "40"))
+    nmin = int(os.environ.get("FE_SERVE_NMIN", "1024"))
+    nmax = int(os.environ.get("FE_SERVE_NMAX", "8192"))
     u = hp_synth.uniform(3000, 4 * count)
     reqs = []
     for k in range(count):
-        n = int(round(math.exp(math.log(1024) + u[4 * k] * (math.log(8192) - math.log(1024)))))
+        n = int(round(math.exp(math.log(nmin) + u[4 * k] * (math.log(nmax) - math.log(nmin)))))
         n = max(64, n)
         ne = round(0.85 * n)
         if u[4 * k + 1] < 0.7:
@@ -634,7 +637,7 @@ def bench_serve(args, torch, fe):
            "ms_per_step": (t1 - t0) * 1e3 / count, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f16x2+f16digits", "data": "synthetic",
            "config": {"workload": "serve_poisson", "requests": count, "rate_per_s": rate,
-                      "n": "log-uniform [1024, 8192]", "mix": "70% gapped, 30% finite T",
+                      "n": "log-uniform [%d, %d]" % (nmin, nmax), "mix": "70% gapped, 30% finite T",
                       "parallelism": "single"},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
            "completed_ok": ok, "gpu_launches": launches, "clocks": clk.summary(), "cpu_baseline": None}

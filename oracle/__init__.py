@@ -14,6 +14,8 @@ passage each routine follows:
 * ``density`` / ``density_from_eig`` / ``density_entries`` -- D = Q f Q^T.
 * ``sp2``                       -- CPU SP2, Sec. II-B1 Eq. (1), with the trace
   rule of Sec. III-B and the RelTr stop of Sec. III-A.
+* ``sp2_accel``                 -- accelerated SP2 (A-Z-RFOE, Sec. II-B2): the
+  SP2 polynomials shifted and scaled with HOMO/LUMO bounds.
 * ``fermi_recursion``           -- finite-T recursive expansion (Sec. II-B3,
   doubling reading).
 * ``metrics``                   -- eps1, eps2 ingredients (Sec. III-C).
@@ -50,6 +52,7 @@ def lib():
             "oracle_density_entry": (d, [i, _D, _D, i, i]),
             "oracle_density": (i, [i, _D, d, d, i, _D, _D, _D, _D]),
             "oracle_sp2": (i, [i, _D, d, d, i, _D, _I]),
+            "oracle_sp2_accel": (i, [i, _D, d, d, d, d, i, _D, _I]),
             "oracle_fermi_recursion": (i, [i, _D, d, d, i, _D]),
             "oracle_metrics": (None, [i, _D, _D, _D, _D]),
         }
@@ -155,6 +158,18 @@ def sp2(H, ne, tol=5e-8, max_iter=200):
     br = np.zeros(max_iter, dtype=np.int32)
     it = lib().oracle_sp2(n, _p(H), float(ne), float(tol), int(max_iter), _p(X),
                           br.ctypes.data_as(_I))
+    return X, it, br[: max(it, 0) if it >= 0 else max_iter].copy()
+
+
+def sp2_accel(H, ne, homo, lumo, tol=5e-8, max_iter=200):
+    """Accelerated SP2 (A-Z-RFOE reading) with HOMO/LUMO estimates ->
+    (X, iterations, branches); iterations = -1 if not converged."""
+    H = _c64(H)
+    n = H.shape[0]
+    X = np.empty((n, n))
+    br = np.zeros(max_iter, dtype=np.int32)
+    it = lib().oracle_sp2_accel(n, _p(H), float(ne), float(homo), float(lumo), float(tol), int(max_iter),
+                                _p(X), br.ctypes.data_as(_I))
     return X, it, br[: max(it, 0) if it >= 0 else max_iter].copy()
 
 

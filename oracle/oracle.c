@@ -24,8 +24,11 @@
  *   - Sec. II-C: spectral bounds, taken as Gershgorin discs.
  *   - Finite temperature (Sec. II-B3, Eq. (2)): a recursive expansion that
  *     doubles the inverse temperature at every step, z <- 2 z (I + z^2)^{-1}
- *     with z = I - 2D = tanh(beta (H - mu)/2); see the reading notes in the
- *     design document.  The inverse is a plain Cholesky solve.
+ *     with z = I - 2D = tanh(beta (H - mu)/2) (the paper's truncated form
+ *     stops short of Fermi-Dirac; this one converges to it).  The inverse is
+ *     a plain Cholesky solve.
+ *   - Sec. II-B2: accelerated SP2 (A-Z-RFOE), read as the SP2 polynomials
+ *     shifted and scaled with bounds on the HOMO and LUMO eigenvalues.
  *
  * All matrices are dense, row-major, n x n, FP64.  No blocking or fusion
  * beyond what each definition states; the only parallelism is an OpenMP loop
@@ -424,6 +427,71 @@ int oracle_sp2(int n, const double *H, double ne, double tol, int max_iter,
             memcpy(X, X2, sizeof(double) * (size_t)n * n);
         } else {
             for (size_t k = 0; k < (size_t)n * n; ++k) X[k] = 2.0 * X[k] - X2[k];
+        }
+        if (branches) branches[it] = sq;
+        ++it;
+        const double t1n = oracle_trace(n, X);
+        if (fabs(t1n - t1) <= tol * ne) done = 1;
+        t1 = t1n;
+    }
+    free(X2);
+    return done ? it : -1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Accelerated SP2 (A-Z-RFOE, Sec. II-B2)                               */
+/* ------------------------------------------------------------------ */
+/* The paper moves the eigenvalues toward 0 or 1 faster by shifting and
+ * scaling the SP2 polynomials with the HOMO and LUMO eigenvalues (homo <
+ * lumo, estimates from the caller).  With X0 as in oracle_sp2, unoccupied
+ * eigenvalues of X lie in [0, a] and occupied ones in [b, 1], where
+ * a = (emax - lumo)/w and b = (emax - homo)/w.  Each step takes the branch
+ * by the SP2 trace rule on t1 = tr X, t2 = tr X^2 and applies its polynomial
+ * folded over the interval that has to shrink:
+ *   X^2 branch:     p(x) = ((x - s)/(1 - s))^2,        s = a/2,
+ *                   so p(0) = p(a), p(1) = 1;
+ *   2X - X^2 branch: q(x) = (2 (1 - s) x - x^2)/(1 - s)^2, s = (1 - b)/2,
+ *                   so q(b) = q(1), q(0) = 0;
+ * then a <- f(a), b <- f(b) for the polynomial f applied.  With s = 0 (no
+ * gap information: a = 0, b = 1, or bounds that do not bracket a gap) a step
+ * is the SP2 step.  Stop as oracle_sp2.  Returns the number of products, or
+ * -1 if max_iter was reached. */
+int oracle_sp2_accel(int n, const double *H, double ne, double homo, double lumo, double tol,
+                     int max_iter, double *X, int *branches)
+{
+    double emin, emax;
+    oracle_gershgorin(n, H, &emin, &emax);
+    const double w = emax - emin;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            X[IDX(i, j, n)] = ((i == j ? emax : 0.0) - H[IDX(i, j, n)]) / w;
+    double a = (emax - lumo) / w, b = (emax - homo) / w;
+    if (!(a >= 0.0 && b <= 1.0 && a < b)) {
+        a = 0.0;
+        b = 1.0;
+    }
+    double *X2 = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double t1 = oracle_trace(n, X);
+    int it = 0, done = 0;
+    while (it < max_iter && !done) {
+        double t2 = 0.0;
+        for (size_t k = 0; k < (size_t)n * n; ++k) t2 += X[k] * X[k];
+        const int sq = fabs(t2 - ne) <= fabs(2.0 * t1 - t2 - ne);
+        oracle_matmul(n, X, X, X2);
+        const double s = sq ? 0.5 * a : 0.5 * (1.0 - b);
+        const double r = 1.0 / ((1.0 - s) * (1.0 - s));
+        if (sq) {
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    const size_t k = IDX(i, j, n);
+                    X[k] = (X2[k] - 2.0 * s * X[k] + (i == j ? s * s : 0.0)) * r;
+                }
+            a = (a - s) * (a - s) * r;
+            b = (b - s) * (b - s) * r;
+        } else {
+            for (size_t k = 0; k < (size_t)n * n; ++k) X[k] = (2.0 * (1.0 - s) * X[k] - X2[k]) * r;
+            a = (2.0 * (1.0 - s) * a - a * a) * r;
+            b = (2.0 * (1.0 - s) * b - b * b) * r;
         }
         if (branches) branches[it] = sq;
         ++it;

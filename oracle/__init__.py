@@ -18,6 +18,8 @@ passage each routine follows:
   SP2 polynomials shifted and scaled with HOMO/LUMO bounds.
 * ``fermi_recursion``           -- finite-T recursive expansion (Sec. II-B3,
   doubling reading).
+* ``trfoe``                     -- the truncated SP2 expansion of Sec. II-B3,
+  Eq. (2) as printed (T-RFOE), on the eigenvalues.
 * ``metrics``                   -- eps1, eps2 ingredients (Sec. III-C).
 
 Every function here is pinned by a test in ``tests/test_oracle.py`` against
@@ -54,6 +56,7 @@ def lib():
             "oracle_sp2": (i, [i, _D, d, d, i, _D, _I]),
             "oracle_sp2_accel": (i, [i, _D, d, d, d, d, i, _D, _I]),
             "oracle_fermi_recursion": (i, [i, _D, d, d, i, _D]),
+            "oracle_trfoe": (i, [i, _D, d, d, d, d, i, _D, _I, _D]),
             "oracle_metrics": (None, [i, _D, _D, _D, _D]),
         }
         for name, (res, args) in sig.items():
@@ -171,6 +174,28 @@ def sp2_accel(H, ne, homo, lumo, tol=5e-8, max_iter=200):
     it = lib().oracle_sp2_accel(n, _p(H), float(ne), float(homo), float(lumo), float(tol), int(max_iter),
                                 _p(X), br.ctypes.data_as(_I))
     return X, it, br[: max(it, 0) if it >= 0 else max_iter].copy()
+
+
+def sp2_accel_status(it):
+    """Meaning of sp2_accel's iteration count: 'ok', 'cap' (-1) or
+    'inconsistent' (-2: the HOMO/LUMO estimates do not lie inside the gap)."""
+    return "ok" if it >= 0 else ("cap" if it == -1 else "inconsistent")
+
+
+def trfoe(lam, ne, kT, emin, emax, max_iter=200):
+    """Truncated SP2 at finite temperature (Sec. II-B3, Eq. (2)) on the
+    eigenvalues lam of H with spectral bounds [emin, emax]:
+    -> (g, m, branches, mu) with g = G_m((emax - lam)/(emax - emin)) the
+    occupations (D = Q diag(g) Q^T), m the steps (-1: max_iter reached),
+    branches[k] = 1 for X^2, and mu the energy where G_m crosses 1/2."""
+    lam = _c64(lam)
+    n = lam.shape[0]
+    g = np.empty(n)
+    br = np.zeros(max_iter + 1, dtype=np.int32)
+    mu = ctypes.c_double()
+    m = lib().oracle_trfoe(n, _p(lam), float(ne), 1.0 / float(kT), float(emin), float(emax), int(max_iter),
+                           _p(g), br.ctypes.data_as(_I), ctypes.byref(mu))
+    return g, m, br[: (m if m >= 0 else max_iter)].copy(), mu.value
 
 
 def fermi_recursion(H, mu, kT, m):

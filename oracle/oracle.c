@@ -29,6 +29,9 @@
  *     a plain Cholesky solve.
  *   - Sec. II-B2: accelerated SP2 (A-Z-RFOE), read as the SP2 polynomials
  *     shifted and scaled with bounds on the HOMO and LUMO eigenvalues.
+ *   - Sec. II-B3, Eq. (2), as printed: the truncated SP2 expansion G_m(H)
+ *     (T-RFOE), with m read as the first step whose step function is as
+ *     steep as Fermi-Dirac at the Fermi level.
  *
  * All matrices are dense, row-major, n x n, FP64.  No blocking or fusion
  * beyond what each definition states; the only parallelism is an OpenMP loop
@@ -454,8 +457,19 @@ int oracle_sp2(int n, const double *H, double ne, double tol, int max_iter,
  *                   so q(b) = q(1), q(0) = 0;
  * then a <- f(a), b <- f(b) for the polynomial f applied.  With s = 0 (no
  * gap information: a = 0, b = 1, or bounds that do not bracket a gap) a step
- * is the SP2 step.  Stop as oracle_sp2.  Returns the number of products, or
- * -1 if max_iter was reached. */
+ * is the SP2 step.
+ *
+ * The folds are valid only while every eigenvalue stays in [0, a] u [b, 1],
+ * i.e. when the estimates lie inside the true gap (homo >= HOMO, lumo <=
+ * LUMO).  With N_e states in [b, 1] and n - N_e in [0, a] after a step,
+ *     N_e b <= tr X <= N_e + (n - N_e) a   and
+ *     tr X - tr X^2 = sum x (1 - x) <= (n - N_e) a + N_e (1 - b);
+ * estimates that put a state on the wrong side, or leave one between a and
+ * b, break one of these by a whole state once a and 1 - b have shrunk, so a
+ * violation by more than 1/2 stops the recursion with -2 (the caller then
+ * runs plain SP2).  Stop as oracle_sp2 otherwise.  Returns the number of
+ * products, -1 if max_iter was reached, or -2 if the estimates were found
+ * inconsistent with the spectrum. */
 int oracle_sp2_accel(int n, const double *H, double ne, double homo, double lumo, double tol,
                      int max_iter, double *X, int *branches)
 {
@@ -470,6 +484,7 @@ int oracle_sp2_accel(int n, const double *H, double ne, double homo, double lumo
         a = 0.0;
         b = 1.0;
     }
+    const int informed = !(a == 0.0 && b == 1.0);
     double *X2 = (double *)malloc(sizeof(double) * (size_t)n * n);
     double t1 = oracle_trace(n, X);
     int it = 0, done = 0;
@@ -496,11 +511,89 @@ int oracle_sp2_accel(int n, const double *H, double ne, double homo, double lumo
         if (branches) branches[it] = sq;
         ++it;
         const double t1n = oracle_trace(n, X);
+        if (informed) {
+            double t2n = 0.0;
+            for (size_t k = 0; k < (size_t)n * n; ++k) t2n += X[k] * X[k];
+            const double lo = ne * b, hi = ne + ((double)n - ne) * a;
+            const double spread = ((double)n - ne) * a + ne * (1.0 - b);
+            if (t1n < lo - 0.5 || t1n > hi + 0.5 || t1n - t2n > spread + 0.5) {
+                free(X2);
+                return -2;
+            }
+        }
         if (fabs(t1n - t1) <= tol * ne) done = 1;
         t1 = t1n;
     }
     free(X2);
     return done ? it : -1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Truncated SP2 at finite temperature (T-RFOE, Sec. II-B3, Eq. (2))    */
+/* ------------------------------------------------------------------ */
+/* The paper smears the zero-temperature step with an intermediate iterate
+ * of the SP2 recursion: D = G_m(H) = F_m(F_{m-1}(... F_0(X_0))), the same
+ * trace-driven branches as oracle_sp2, stopped after m steps, with m larger
+ * for lower temperature.  Its references fixing m are not in the text; the
+ * reading used: every F is increasing on [0, 1], so G_k(x) crosses 1/2 at
+ * one point x*_k, and the expansion stops at the first k whose step function
+ * is as steep there as the Fermi-Dirac function at mu,
+ *     |d G_k / d eps| (eps*) = (1/w) prod_j F_j'(u_j) >= beta / 4,
+ * with u_0 = x*_k, u_{j+1} = F_j(u_j), u_k = 1/2, F' = 2u (X^2) or
+ * 2 - 2u (2X - X^2), x = (emax - eps)/w, w = emax - emin.  The u_j follow
+ * backwards from u_k = 1/2 by the closed-form inverses sqrt(y) and
+ * 1 - sqrt(1 - y); eps* = emax - w u_0 is reported as mu.
+ *
+ * Because every step is a polynomial in H, G_m(H) = Q diag(G_m(x(lambda)))
+ * Q^T: the recursion is run on the scalars x_i = (emax - lambda_i)/w of the
+ * given eigenvalues, with t1 = sum x_i and t2 = sum x_i^2 deciding the
+ * branch exactly as the matrix recursion's traces would, and x_out receives
+ * G_m(x_i).  emin/emax are the spectral bounds of the matrix recursion
+ * (Gershgorin, Sec. II-C).  branches[k] records 1 for X^2, 0 for 2X - X^2.
+ * Returns m, or -1 if max_iter steps did not reach the slope. */
+static double trfoe_slope(const int *bits, int m, double w, double *mid)
+{
+    double u = 0.5, d = 1.0;
+    for (int k = m - 1; k >= 0; --k) {
+        u = bits[k] ? sqrt(u) : 1.0 - sqrt(1.0 - u);   /* u_k = F_k^{-1}(u_{k+1}) */
+        d *= bits[k] ? 2.0 * u : 2.0 - 2.0 * u;        /* F_k'(u_k) */
+    }
+    *mid = u;
+    return d / w;
+}
+
+int oracle_trfoe(int n, const double *lam, double ne, double beta, double emin, double emax,
+                 int max_iter, double *x_out, int *branches, double *mu)
+{
+    const double w = emax - emin;
+    int *bits = (int *)malloc(sizeof(int) * (size_t)(max_iter + 1));
+    for (int i = 0; i < n; ++i) x_out[i] = (emax - lam[i]) / w;
+    int m = 0, reached = 0;
+    for (;;) {
+        double mid;
+        const double slope = trfoe_slope(bits, m, w, &mid);
+        *mu = emax - w * mid;
+        if (slope >= 0.25 * beta) {
+            reached = 1;
+            break;
+        }
+        if (m >= max_iter) break;
+        double t1 = 0.0, t2 = 0.0;
+        for (int i = 0; i < n; ++i) {
+            t1 += x_out[i];
+            t2 += x_out[i] * x_out[i];
+        }
+        const int sq = fabs(t2 - ne) <= fabs(2.0 * t1 - t2 - ne);
+        for (int i = 0; i < n; ++i) {
+            const double x = x_out[i];
+            x_out[i] = sq ? x * x : 2.0 * x - x * x;
+        }
+        bits[m] = sq;
+        if (branches) branches[m] = sq;
+        ++m;
+    }
+    free(bits);
+    return reached ? m : -1;
 }
 
 /* ------------------------------------------------------------------ */

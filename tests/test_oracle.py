@@ -266,8 +266,11 @@ def test_sp2_accel_without_gap_information_is_sp2():
 def test_sp2_accel_reaches_projector_in_fewer_products(make):
     """With the exact HOMO/LUMO the folded recursion reaches the same
     projector as SP2 in about 40% fewer products (the paper reports about
-    30 against 50, Sec. IV); with estimates five gaps too wide it still
-    converges, in between."""
+    30 against 50, Sec. IV); with estimates inside the gap but 40% short of
+    each edge it still converges, in between.  Estimates outside the gap
+    (five gaps too wide) are not what the folds need: the recursion either
+    still lands on the projector or reports the estimates as inconsistent
+    (-2), never a wrong projector."""
     p = make()
     ne = int(p.ne)
     w = np.linalg.eigvalsh(p.H)          # the library routine only supplies the estimates
@@ -278,9 +281,156 @@ def test_sp2_accel_reaches_projector_in_fewer_products(make):
     assert it > 0 and np.abs(X - D).max() < 1e-9
     assert it <= 0.7 * it0
     g = l - h
+    Xi, iti, _ = oracle.sp2_accel(p.H, p.ne, h + 0.4 * g, l - 0.4 * g, tol=1e-12)
+    assert iti > 0 and np.abs(Xi - D).max() < 1e-9
+    assert it <= iti <= it0
     Xl, itl, _ = oracle.sp2_accel(p.H, p.ne, h - 5 * g, l + 5 * g, tol=1e-12)
-    assert itl > 0 and np.abs(Xl - D).max() < 1e-9
-    assert it <= itl <= it0
+    assert itl == -2 or (itl > 0 and np.abs(Xl - D).max() < 1e-9)
+
+
+@pytest.mark.parametrize("shift", [-1, 1, 2])
+def test_sp2_accel_flags_misplaced_estimates(shift):
+    """Estimates that put the gap between the wrong pair of states (`shift`
+    states up or down) cannot give the projector onto the N_e lowest states:
+    the trace bounds N_e b <= tr X <= N_e + (n - N_e) a (or the spread bound
+    on tr(X - X^2)) fail by a whole state, and the oracle returns -2 within
+    about as many products as SP2 takes."""
+    p = hp_synth.gapped(200, 150, (-3.0, -0.02), (0.02, 1.0), 21)
+    ne = 150
+    lam = p.lam
+    h, l = lam[ne - 1 + shift], lam[ne + shift]
+    _, it0, _ = oracle.sp2(p.H, p.ne, tol=1e-12)
+    _, it, _ = oracle.sp2_accel(p.H, p.ne, h + 0.1 * (l - h), l - 0.1 * (l - h), tol=1e-12, max_iter=200)
+    assert it == -2
+    assert oracle.sp2_accel_status(it) == "inconsistent"
+
+
+def test_sp2_accel_estimates_inside_the_gap_are_never_flagged():
+    """Random gapped problems (n, N_e, gap, spectral scaling) with HOMO/LUMO
+    estimates drawn anywhere inside the true gap: every one converges to the
+    projector; the consistency test never fires on valid estimates."""
+    rng = np.random.default_rng(5)
+    for t in range(12):
+        n = int(rng.integers(40, 160))
+        ne = int(rng.integers(1, n))
+        gap = 10 ** rng.uniform(-3, -0.7)
+        p = hp_synth.gapped(n, ne, (-3.0, -gap / 2), (gap / 2, 1.0), 600 + t)
+        h, l = p.lam[ne - 1], p.lam[ne]
+        u = np.sort(rng.uniform(0.0, 1.0, 2))
+        hh, ll = h + u[0] * (l - h), h + max(u[1], u[0] + 1e-3) * (l - h)
+        X, it, _ = oracle.sp2_accel(p.H, p.ne, hh, ll, tol=1e-12)
+        f = (np.arange(n) < ne).astype(float)
+        assert it > 0, (t, n, ne, gap, u)
+        assert np.abs(X - oracle.density_from_eig(p.Q, f)).max() < 1e-8
+
+
+# ---------------------------------------------------------------- truncated SP2 at finite T
+
+def _apply_branches(x, branches):
+    """The SP2 maps of Eq. (1) applied in the given order to scalars."""
+    x = np.array(x, dtype=float)
+    for b in branches:
+        x = x * x if b else 2.0 * x - x * x
+    return x
+
+
+def test_trfoe_first_steps_by_hand():
+    """H = diag(-1, -0.5, 0.5, 1), N_e = 2, bounds [-1, 1] (w = 2):
+    x0 = (1, 0.75, 0.25, 0).  At step 0 the slope is 1/w = 0.5, so beta = 1
+    (beta/4 = 0.25) stops at once with mu = 0.  With beta = 4 (beta/4 = 1):
+    t1 = 2, t2 = 1.625 is a tie (0.375 either way) and goes to X^2: x1 =
+    (1, 0.5625, 0.0625, 0), midpoint u0 = sqrt(1/2), slope 2 u0 / 2 =
+    0.7071 < 1; then t1 = 1.625, t2 = 1.3203125 pick 2X - X^2 (|t2 - 2| =
+    0.68 > |2 t1 - t2 - 2| = 0.0703): u1 = 1 - sqrt(1/2), u0 = sqrt(u1),
+    slope (2 - 2 u1) (2 u0) / 2 = 0.7654 < 1; and so on."""
+    lam = np.array([-1.0, -0.5, 0.5, 1.0])
+    g, m, br, mu = oracle.trfoe(lam, 2.0, 1.0, -1.0, 1.0)
+    assert m == 0 and mu == 0.0 and np.array_equal(g, [1.0, 0.75, 0.25, 0.0])
+    g2, m2, br2, _ = oracle.trfoe(lam, 2.0, 0.25, -1.0, 1.0, max_iter=2)
+    assert m2 == -1 and list(br2[:2]) == [1, 0]  # cap reached before the slope
+    assert np.allclose(g2, [1.0, 0.80859375, 0.12109375, 0.0], rtol=0, atol=1e-15)
+
+
+def test_trfoe_stop_rule_against_finite_differences():
+    """The stop rule compares |dG_m/de| at the midpoint G_m = 1/2 with
+    beta/4.  Here G_k is evaluated by applying the recorded branches to
+    energies on a grid, its midpoint found by bisection and its slope by a
+    central difference (no use of the closed-form inverses): the slope after
+    m - 1 steps is below beta/4 and after m steps at or above it, and the
+    reported mu is the midpoint of G_m."""
+    p = hp_synth.smeared(300, 240.0, 0.004, -2.0, 1.0, 51)
+    lo, hi = oracle.gershgorin(p.H)
+    w = hi - lo
+    beta = 1.0 / p.kT
+    g, m, br, mu = oracle.trfoe(p.lam, p.ne, p.kT, lo, hi)
+    assert m > 5
+
+    def G(eps, k):
+        return _apply_branches((hi - np.asarray(eps)) / w, br[:k])
+
+    def midpoint_and_slope(k):
+        a, b = lo, hi                        # G_k falls from 1 at lo to 0 at hi
+        for _ in range(200):
+            c = 0.5 * (a + b)
+            if G(c, k) > 0.5:
+                a = c
+            else:
+                b = c
+        c = 0.5 * (a + b)
+        h = 1e-7 * w
+        return c, abs(G(c + h, k) - G(c - h, k)) / (2 * h)
+
+    c_prev, s_prev = midpoint_and_slope(m - 1)
+    c_m, s_m = midpoint_and_slope(m)
+    assert s_prev < beta / 4 <= s_m * (1 + 1e-6)
+    assert abs(c_m - mu) <= 1e-9 * w
+    assert np.allclose(g, G(p.lam, m), rtol=0, atol=1e-14)
+
+
+def test_trfoe_matrix_recursion_equals_scalar_on_eigenvalues():
+    """The recursion is polynomial in H, so the matrix form (traces of the
+    matrix deciding each branch, plain numpy products) equals
+    Q diag(G_m(x(lambda))) Q^T with the oracle's branches."""
+    p = hp_synth.smeared(120, 100.0, 0.01, -2.0, 1.0, 52)
+    lo, hi = oracle.gershgorin(p.H)
+    g, m, br, mu = oracle.trfoe(p.lam, p.ne, p.kT, lo, hi)
+    X = (hi * np.eye(p.n) - p.H) / (hi - lo)
+    for k in range(m):
+        t1, t2 = np.trace(X), np.sum(X * X)
+        sq = abs(t2 - p.ne) <= abs(2 * t1 - t2 - p.ne)
+        assert sq == bool(br[k])
+        X2 = X @ X
+        X = X2 if sq else 2 * X - X2
+    assert np.abs(X - oracle.density_from_eig(p.Q, g)).max() < 1e-11
+
+
+def test_trfoe_low_temperature_limit_is_the_projector():
+    """kT -> 0 on a gapped spectrum: G_m must become the step function, so
+    the truncated expansion equals the zero-temperature projector."""
+    p = hp_synth.gapped(150, 100, (-2.0, -0.1), (0.1, 1.0), 53)
+    lo, hi = oracle.gershgorin(p.H)
+    g, m, _, mu = oracle.trfoe(p.lam, p.ne, 1e-9, lo, hi)
+    assert m > 0
+    f = (np.arange(150) < 100).astype(float)
+    assert np.abs(g - f).max() < 1e-12
+    assert p.lam[99] < mu < p.lam[100]
+
+
+def test_trfoe_distance_to_fermi_dirac_is_the_papers_magnitude():
+    """Sanity band from Sec. IV: on the paper's own matrix at 500 K with
+    N_e = 0.85 n, the truncated expansion takes a few tens of steps and sits
+    at a relative distance of order 1e-3 .. 1e-2 from Fermi-Dirac (the paper
+    quotes ~30 steps and eps1 ~ 1e-3; it is a smeared step, not FD)."""
+    p = hp_synth.paper_matrix(600, frac=0.85)
+    w, _ = oracle.eigh_ql(p.H)
+    lo, hi = oracle.gershgorin(p.H)
+    kT = 1.5834e-3
+    g, m, _, mu = oracle.trfoe(w, p.ne, kT, lo, hi)
+    f, mu_fd = oracle.occupations(w, p.ne, kT)
+    eps1 = np.linalg.norm(g - f) / np.sqrt(p.ne)
+    assert 20 <= m <= 60
+    assert 1e-4 <= eps1 <= 1e-1
+    assert abs(mu - mu_fd) < 0.05
 
 
 # ---------------------------------------------------------------- finite-T recursion

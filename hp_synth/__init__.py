@@ -134,6 +134,96 @@ def smeared(n, ne, kT, a, b, seed, tol=5e-8, device=None, name="smeared"):
     return Problem(name, assemble(Q, lam), Q, lam, float(ne), kT, tol, seed)
 
 
+class ReflectedQ:
+    """Q = H_0 H_1 ... H_{k-1}, H_j = I - 2 v_j v_j^T with unit v_j: an
+    orthogonal factor applied in O(k n^2) (used where a QR of an n x n
+    Gaussian would cost minutes: the serving workload reaches n = 32768).
+    V holds the k vectors as rows (torch tensor on the device, or numpy)."""
+
+    def __init__(self, V):
+        self.V = V
+
+    def _refl(self, X, j):
+        v = self.V[j]
+        return X - 2.0 * v[:, None] * (v[None, :] @ X)
+
+    def mul(self, X):
+        """Q X."""
+        for j in range(self.V.shape[0] - 1, -1, -1):
+            X = self._refl(X, j)
+        return X
+
+    def tmul(self, X):
+        """Q^T X."""
+        for j in range(self.V.shape[0]):
+            X = self._refl(X, j)
+        return X
+
+
+def reflected_q(n, seed, k=8, device=None):
+    V = normal(seed, k * n).reshape(k, n)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    if device is not None:
+        import torch
+        V = torch.from_numpy(V).to(device)
+    return ReflectedQ(V)
+
+
+def assemble_reflected(Q, lam):
+    """Hp = Q diag(lam) Q^T for a ReflectedQ: starting from diag(lam), each
+    reflector acts on both sides, H <- H - 2 v w^T - 2 w v^T + 4 (v^T w) v v^T
+    with w = H v (exact similarity, symmetric by construction)."""
+    V = Q.V
+    if isinstance(V, np.ndarray):
+        H = np.diag(np.asarray(lam, dtype=np.float64))
+        for j in range(V.shape[0] - 1, -1, -1):
+            v = V[j]
+            w = H @ v
+            a = float(v @ w)
+            H -= 2.0 * np.outer(v, w) + 2.0 * np.outer(w, v) - 4.0 * a * np.outer(v, v)
+        return H
+    import torch
+    H = torch.diag(torch.as_tensor(lam, dtype=torch.float64, device=V.device))
+    for j in range(V.shape[0] - 1, -1, -1):
+        v = V[j]
+        w = H @ v
+        a = float(v @ w)
+        H.addr_(v, w, alpha=-2.0).addr_(w, v, alpha=-2.0).addr_(v, v, alpha=4.0 * a)
+    return H
+
+
+def gapped_reflected(n, ne, occ, emp, seed, tol=5e-8, device=None, name="gapped_reflected"):
+    """The gapped recipe with Q from 8 Householder reflectors instead of a QR."""
+    lam = gapped_spectrum(n, ne, occ, emp, seed)
+    Q = reflected_q(n, seed, device=device)
+    return Problem(name, assemble_reflected(Q, lam), Q, lam, float(ne), 0.0, tol, seed)
+
+
+def smeared_reflected(n, ne, kT, a, b, seed, tol=5e-8, device=None, name="smeared_reflected"):
+    """The semicircle recipe with Q from 8 Householder reflectors."""
+    lam = semicircle_spectrum(n, a, b, seed)
+    Q = reflected_q(n, seed, device=device)
+    return Problem(name, assemble_reflected(Q, lam), Q, lam, float(ne), kT, tol, seed)
+
+
+def serve_requests(count, rate, nmin, nmax, seed=3000):
+    """The serving workload's request stream: for request k, n log-uniform in
+    [nmin, nmax], 70% gapped (gap uniform in [0.01, 0.1] Ha at 0) and 30%
+    finite temperature (kT uniform in [0.001, 0.01] Ha, semicircle spectrum
+    on [-2, 1] Ha), N_e = round(0.85 n), and Poisson arrival gaps of mean
+    1/rate.  Returns a list of dicts (n, ne, kT, gap, seed, dt)."""
+    u = uniform(seed, 4 * count)
+    dts = -np.log(1.0 - uniform(seed + 1, count)) / rate
+    out = []
+    for k in range(count):
+        n = int(round(math.exp(math.log(nmin) + u[4 * k] * (math.log(nmax) - math.log(nmin)))))
+        n = max(64, n)
+        finite = u[4 * k + 1] >= 0.7
+        out.append(dict(n=n, ne=int(round(0.85 * n)), kT=(0.001 + 0.009 * u[4 * k + 2]) if finite else 0.0,
+                        gap=0.0 if finite else 0.01 + 0.09 * u[4 * k + 2], seed=seed + 100 + k, dt=float(dts[k])))
+    return out
+
+
 # --- the benchmark workloads (sizes, spectra, seeds) --------------------------
 
 def workload_n256(device=None):

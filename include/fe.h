@@ -67,6 +67,32 @@ extern "C" {
 #define FE_METHOD_AUTO 0x00u  /* SP2 if kT == 0 else FERMI                     */
 #define FE_METHOD_SP2 0x10u   /* zero temperature, Sec. II-B1                   */
 #define FE_METHOD_FERMI 0x20u /* finite temperature, doubling recursion         */
+/* Zero temperature, accelerated SP2 (A-Z-RFOE, Sec. II-B2): the SP2
+ * polynomials shifted and scaled with the caller's HOMO/LUMO estimates
+ * (fe_problem.homo < fe_problem.lumo, e.g. the previous subspace iteration's
+ * Rayleigh-Ritz eigenvalues), so that eigenvalues reach 0 or 1 in fewer
+ * products.  The folds are valid when the estimates lie inside the true gap
+ * (homo >= the HOMO eigenvalue, lumo <= the LUMO eigenvalue).  The device
+ * checks after every product that the traces stay consistent with that
+ * (N_e b <= tr X <= N_e + (n - N_e) a and tr(X - X^2) <= (n - N_e) a +
+ * N_e (1 - b), a and b the folded interval ends, within 1/2); when they do
+ * not, the solve starts again as plain SP2 (fe_result.iters counts both). */
+#define FE_METHOD_ASP2 0x30u
+/* Finite temperature, the truncated SP2 expansion as the paper prints it
+ * (T-RFOE, Sec. II-B3, Eq. (2)): D = G_m(X0), the SP2 recursion with its
+ * trace-driven branches stopped after m products, X0 from the Gershgorin
+ * bounds.  m is the first step at which the step function G_m is as steep
+ * at its midpoint (G_m = 1/2) as the Fermi-Dirac function at mu, i.e.
+ * |dG_m/de| >= beta/4; fe_result.mu is the midpoint energy.  D is a smeared
+ * step, not Fermi-Dirac (the paper quotes eps1 ~ 1e-3 against it), and
+ * tr D is near but not equal to N_e.  The step function is steep
+ * (|dG/dx| = beta w / 4 at its midpoint, w the Gershgorin width), so a
+ * product's rounding error is amplified that much for the states near mu.
+ * Precision: FE_PREC_MIXED (split FP16 until RelTr < 5e-4, the paper's
+ * switch point, then FP64-accurate digit products), FE_PREC_FP32 (split FP16
+ * only) or FE_PREC_FP64 (FP64-accurate digit products on the tensor cores
+ * from an FP64 X0, for results within FP64 rounding times that slope). */
+#define FE_METHOD_TRFOE 0x40u
 #define FE_METHOD_MASK 0xF0u
 
 /* Precision schedules (Sec. III-A).  Bits 8..11. */
@@ -99,6 +125,10 @@ typedef struct {
     double tol;        /* RelTr stop |tr X_k - tr X_{k-1}| / N_e; 0 = 5e-8          */
     double *D;         /* output density matrix (n x n, ld), may be NULL           */
     uint32_t flags;    /* FE_PTR_* | FE_METHOD_* | FE_PREC_*                        */
+    double homo;       /* FE_METHOD_ASP2: estimate of the highest occupied
+                          eigenvalue of Hp (ignored by the other methods)          */
+    double lumo;       /* FE_METHOD_ASP2: estimate of the lowest unoccupied
+                          eigenvalue of Hp, > homo                                 */
 } fe_problem;
 
 typedef struct {
@@ -109,7 +139,8 @@ typedef struct {
     double trace;           /* tr D                                                 */
     double idem_fro;        /* ||X^2 - X||_F of the last product's input, measured in its
                                epilogue (0 T); D, its output, is closer to idempotent */
-    double mu;              /* chemical potential (finite T); NaN at zero T          */
+    double mu;              /* chemical potential (FE_METHOD_FERMI), midpoint energy
+                               of the step function (FE_METHOD_TRFOE); NaN at zero T */
     double eps_min;         /* lower spectral bound the expansion used: a Lanczos
                                estimate widened by its certificate so that it
                                contains the spectrum, within the Gershgorin interval */
@@ -143,8 +174,10 @@ FE_API int fe_destroy(fe_ctx *ctx);
  * cudaHostRegister) by the output kernel directly, other host memory through a
  * staging copy.  r receives the result even on failure.
  * Errors: FE_EINVAL (n < 1, ld < n, N_e out of [0, n], kT < 0, non-integral
- * N_e at kT == 0, tol < 0, NaN/Inf in Hp), FE_ENOMEM, FE_ENOTCONV,
- * FE_ETIMEOUT, FE_ECUDA. */
+ * N_e at kT == 0, tol < 0, NaN/Inf in Hp, FE_METHOD_ASP2 without finite
+ * homo < lumo or with kT != 0, FE_METHOD_TRFOE with kT == 0), FE_ENOMEM,
+ * FE_ENOTCONV (iteration cap, or a polish that cannot reach the trace and
+ * idempotency targets, e.g. a degenerate HOMO/LUMO), FE_ETIMEOUT, FE_ECUDA. */
 FE_API int fe_solve(fe_ctx *ctx, const fe_problem *p, fe_result *r);
 
 /* Solve `count` independent problems (any mix of n) in one launch sequence:

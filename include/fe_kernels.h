@@ -89,6 +89,20 @@ FE_API int fe_k_profile_steps(fe_ctx *ctx, double *out, int max_steps, int *coun
  * Errors: FE_EINVAL (ctx NULL, factor outside (0, 1]). */
 FE_API int fe_k_narrow_bounds(fe_ctx *ctx, double factor);
 
+/* Failure-detection hook (no counterpart in the paper).  Every wait inside
+ * the tensor-core kernels (TMA data, shared-memory stages, tensor-memory
+ * hand-offs, the partner of a tile split between two CTAs) is bounded: when
+ * one runs out the kernel records an error code, waits (bounded) for its own
+ * copies and products in flight, frees its tensor memory and returns; the
+ * control kernel then ends every problem of the run, and the call returns
+ * FE_ETIMEOUT with the context still usable.  This sets the limit of those
+ * waits for later solves on ctx (limit_ms, default 2000) and, with
+ * fail_partner != 0, makes the second CTA of every split tile wait on a word
+ * that nothing writes, so that its wait runs out: a way to exercise the
+ * expiry path without any fault.  Call it while no submitted solve runs.
+ * Errors: FE_EINVAL (ctx NULL, limit_ms outside (0, 60000]), FE_ECUDA. */
+FE_API int fe_k_set_wait(fe_ctx *ctx, double limit_ms, int fail_partner);
+
 /* Where the last blocking solve or batch on ctx spent its device time
  * (measurement hook, no counterpart in the paper; CUDA events, always on).
  * out4 (HOST): [0] ms of set-up (Hp staging, bounds, X0, first control step),
@@ -104,6 +118,14 @@ FE_API int fe_k_phase_ms(fe_ctx *ctx, double *out4);
  * FE_PREC_TRY_FP16 (one slice). */
 FE_API int fe_k_set_tile_width(fe_ctx *ctx, int64_t n, uint32_t prec, int bn);
 FE_API int fe_k_tile_width(fe_ctx *ctx, int64_t n, uint32_t prec, int *bn);
+
+/* Serving counters (measurement hook, no counterpart in the paper), HOST out4:
+ * [0] requests submitted, [1] requests that had to wait at least once for a
+ * free part of the HBM budget (at submission or at a later admission pass),
+ * [2] the largest number of requests waiting at once, [3] the largest
+ * number of requests on the device at once; since fe_create or the last
+ * call with reset != 0. */
+FE_API int fe_k_serve_stats(fe_ctx *ctx, int64_t *out4, int reset);
 
 /* Number of kernels this context has launched since fe_create (HOST out). */
 FE_API int fe_k_launch_count(fe_ctx *ctx, int64_t *out);

@@ -18,7 +18,7 @@ FE_OK, FE_PENDING, FE_EINVAL, FE_ENOMEM, FE_ENOTCONV, FE_ETIMEOUT, FE_ECUDA, FE_
 STATUS_NAMES = {0: "FE_OK", 1: "FE_PENDING", -1: "FE_EINVAL", -2: "FE_ENOMEM", -3: "FE_ENOTCONV",
                 -4: "FE_ETIMEOUT", -5: "FE_ECUDA", -6: "FE_EBUSY"}
 FE_PTR_HOST, FE_PTR_DEVICE = 0x0, 0x1
-FE_METHOD_AUTO, FE_METHOD_SP2, FE_METHOD_FERMI = 0x00, 0x10, 0x20
+FE_METHOD_AUTO, FE_METHOD_SP2, FE_METHOD_FERMI, FE_METHOD_ASP2, FE_METHOD_TRFOE = 0x00, 0x10, 0x20, 0x30, 0x40
 PREC = {"mixed": 0x000, "fp64": 0x100, "fp32": 0x200, "try_fp16": 0x300}
 
 
@@ -31,7 +31,8 @@ class FeConfig(ctypes.Structure):
 class FeProblem(ctypes.Structure):
     _fields_ = [("Hp", ctypes.c_void_p), ("n", ctypes.c_int64), ("ld", ctypes.c_int64),
                 ("n_e", ctypes.c_double), ("kT", ctypes.c_double), ("tol", ctypes.c_double),
-                ("D", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+                ("D", ctypes.c_void_p), ("flags", ctypes.c_uint32), ("homo", ctypes.c_double),
+                ("lumo", ctypes.c_double)]
 
 
 class FeTune(ctypes.Structure):
@@ -82,6 +83,8 @@ def load(build=True):
     L.fe_k_digit_square.argtypes = [P, P, i64, i64, P, i64]
     L.fe_k_profile.argtypes = [P, ctypes.c_int]
     L.fe_k_narrow_bounds.argtypes = [P, dbl]
+    L.fe_k_set_wait.argtypes = [P, dbl, ctypes.c_int]
+    L.fe_k_serve_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.c_int]
     L.fe_k_phase_ms.argtypes = [P, ctypes.POINTER(dbl)]
     L.fe_k_profile_steps.argtypes = [P, ctypes.POINTER(dbl), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.fe_k_profile_read.argtypes = [P, ctypes.POINTER(dbl)]
@@ -96,7 +99,8 @@ def load(build=True):
     L.fe_k_tile_width.argtypes = [P, i64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int)]
     for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
                  "fe_k_gershgorin", "fe_k_gershgorin_noalloc", "fe_k_sym_square", "fe_k_digit_square",
-                 "fe_k_profile", "fe_k_profile_read", "fe_k_narrow_bounds", "fe_k_phase_ms", "fe_k_profile_steps",
+                 "fe_k_profile", "fe_k_profile_read", "fe_k_narrow_bounds", "fe_k_set_wait", "fe_k_serve_stats", "fe_k_phase_ms",
+                 "fe_k_profile_steps",
                  "fe_k_launch_count", "fe_k_history", "fe_autotune", "fe_autotune_batch", "fe_k_set_tile_width",
                  "fe_k_tile_width"):
         getattr(L, name).restype = ctypes.c_int
@@ -141,15 +145,21 @@ def gershgorin_noalloc(H, out4, stream=None):
     not trigger cudaMalloc's device-wide synchronisation).  Queued on `stream`
     (a raw cudaStream_t; default: torch's current stream) without waiting.
     Calls that overlap in time share one scratch array and race."""
+    import torch
     L = load()
-    hp, hdev, _ = _ptr(H)
-    op, odev, _ = _ptr(out4)
-    if not (hdev and odev):
-        raise ValueError("device tensors expected")
+    if not (isinstance(H, torch.Tensor) and isinstance(out4, torch.Tensor)):
+        raise ValueError("torch tensors expected")
+    dev = torch.cuda.current_device()
+    if not (H.is_cuda and out4.is_cuda and H.device.index == dev and out4.device.index == dev):
+        raise ValueError("H and out4 must be on the current CUDA device")
+    if H.dtype != torch.float64 or H.dim() != 2 or H.shape[0] != H.shape[1] or H.stride(1) != 1:
+        raise ValueError("H must be a square float64 matrix with unit column stride")
+    if out4.dtype != torch.float64 or out4.numel() < 4 or not out4.is_contiguous():
+        raise ValueError("out4 must be a contiguous float64 tensor of at least 4 elements")
     if stream is None:
-        import torch
-        stream = torch.cuda.current_stream().cuda_stream
-    rc = L.fe_k_gershgorin_noalloc(hp, H.shape[0], H.stride(0), op, ctypes.c_void_p(stream))
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    rc = L.fe_k_gershgorin_noalloc(H.data_ptr(), H.shape[0], H.stride(0), out4.data_ptr(),
+                                   ctypes.c_void_p(stream))
     if rc != FE_OK:
         raise FeError(rc, L.fe_last_error_string(None).decode())
 
@@ -189,7 +199,7 @@ class Context:
     def last_error(self):
         return self.L.fe_last_error_string(self.h).decode()
 
-    def _problem(self, H, ne, kT, tol, D, precision, method):
+    def _problem(self, H, ne, kT, tol, D, precision, method, homo=0.0, lumo=0.0):
         hp, hdev, keep_h = _ptr(H)
         n = H.shape[0]
         assert H.shape[0] == H.shape[1]
@@ -204,15 +214,16 @@ class Context:
             if dld != ld:
                 raise ValueError("Hp and D must share the leading dimension")
         flags = (FE_PTR_DEVICE if hdev else FE_PTR_HOST) | PREC[precision] | method
-        p = FeProblem(hp, n, ld, float(ne), float(kT), float(tol), dp, flags)
+        p = FeProblem(hp, n, ld, float(ne), float(kT), float(tol), dp, flags, float(homo), float(lumo))
         _ready(H, D)
         return p, (keep_h, keep_d)
 
     def solve(self, H, ne, kT=0.0, tol=0.0, D=None, precision="mixed", method=FE_METHOD_AUTO,
-              check=True):
+              check=True, homo=0.0, lumo=0.0):
         """Solve one problem.  H (n x n FP64, host numpy or device torch); D
-        (same kind, written) or None.  Returns the result dict."""
-        p, keep = self._problem(H, ne, kT, tol, D, precision, method)
+        (same kind, written) or None; homo/lumo: the HOMO/LUMO estimates of
+        FE_METHOD_ASP2.  Returns the result dict."""
+        p, keep = self._problem(H, ne, kT, tol, D, precision, method, homo, lumo)
         r = FeResult()
         rc = self.L.fe_solve(self.h, ctypes.byref(p), ctypes.byref(r))
         if check and rc != FE_OK:
@@ -228,7 +239,7 @@ class Context:
         for k, it in enumerate(items):
             p, kp = self._problem(it["H"], it["ne"], it.get("kT", 0.0), it.get("tol", 0.0),
                                   it.get("D"), it.get("precision", "mixed"),
-                                  it.get("method", FE_METHOD_AUTO))
+                                  it.get("method", FE_METHOD_AUTO), it.get("homo", 0.0), it.get("lumo", 0.0))
             probs[k] = p
             keep.append(kp)
         res = (FeResult * len(items))()
@@ -238,10 +249,11 @@ class Context:
         return rc, [r.as_dict() for r in res]
 
     # ---- continuous batching -------------------------------------------------
-    def submit(self, H, ne, kT=0.0, tol=0.0, D=None, precision="mixed", method=FE_METHOD_AUTO):
+    def submit(self, H, ne, kT=0.0, tol=0.0, D=None, precision="mixed", method=FE_METHOD_AUTO,
+               homo=0.0, lumo=0.0):
         """Queue one problem; returns its ticket.  H may be reused at once; D
         (if given) must stay alive until poll() returns a final status."""
-        p, keep = self._problem(H, ne, kT, tol, D, precision, method)
+        p, keep = self._problem(H, ne, kT, tol, D, precision, method, homo, lumo)
         t = ctypes.c_uint64()
         rc = self.L.fe_submit(self.h, ctypes.byref(p), ctypes.byref(t))
         if rc != FE_OK:
@@ -364,6 +376,13 @@ class Context:
                 "tc_ms_all", "tc_launches_all")
         return dict(zip(keys, list(out)))
 
+    def set_wait(self, limit_ms=2000.0, fail_partner=False):
+        """Failure-detection hook: the limit of the kernels' bounded waits and
+        the test word that makes the split-tile partner wait run out."""
+        rc = self.L.fe_k_set_wait(self.h, float(limit_ms), 1 if fail_partner else 0)
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+
     def narrow_bounds(self, factor):
         """Test hook: shrink the estimated spectral bounds of later solves
         about their centre by `factor` (1 = off)."""
@@ -383,6 +402,15 @@ class Context:
         out = (ctypes.c_double * 4)()
         self.L.fe_k_phase_ms(self.h, out)
         return dict(zip(("setup_ms", "loop_ms", "output_ms", "steps"), list(out)))
+
+    def serve_stats(self, reset=False):
+        """Serving counters: submitted, deferred (waited for HBM), peak
+        waiting queue, peak requests on the device."""
+        out = (ctypes.c_int64 * 4)()
+        rc = self.L.fe_k_serve_stats(self.h, out, 1 if reset else 0)
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+        return dict(zip(("submitted", "deferred", "peak_waiting", "peak_running"), list(out)))
 
     def launch_count(self):
         v = ctypes.c_int64()

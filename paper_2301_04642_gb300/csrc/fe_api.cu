@@ -84,7 +84,7 @@ struct Slot {
 struct Engine {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int *d_err = nullptr;
+    DevCtl *d_err = nullptr;         // error word, wait limit and test hook of the kernels
     MmaProb *d_probs = nullptr;
     size_t probs_cap = 0;
     TileEnt *d_tiles = nullptr;
@@ -133,6 +133,9 @@ struct Req {
     Slot *slot = nullptr;
     bool staged = false;            // Hp already copied into slot->Hcopy
     bool gershgorin = false;        // the spectral-bound estimate proved too tight: use Gershgorin
+    bool accel_off = false;         // FE_METHOD_ASP2 estimates proved inconsistent: plain SP2
+    bool deferred = false;          // waited at least once for a free part of the HBM budget
+    int wasted = 0;                 // products of attempts that were started again
     int bn = 0;                     // tensor-core tile width, fixed when the solve starts
     bool done = false;
     fe_result res{};
@@ -174,6 +177,11 @@ struct fe_ctx {
     std::thread worker;
     bool worker_started = false;
     bool stop = false;
+    // serving counters (under qmu): requests submitted, requests that waited
+    // for HBM at least once, largest queue of waiting requests, largest
+    // number of requests on the device at once
+    long long n_submitted = 0, n_deferred = 0;
+    long long peak_waiting = 0, peak_running = 0;
 };
 
 namespace {
@@ -463,10 +471,18 @@ int tile_width(fe_ctx *ctx, int64_t n, uint32_t prec) {
     return best;
 }
 
+// The expansion a problem runs (the solve state's method): FE_METHOD_ASP2 is
+// the SP2 recursion with its folds switched on, FE_METHOD_TRFOE the truncated
+// SP2 expansion at finite temperature.
 int method_of(const fe_problem *p) {
     const uint32_t m = p->flags & FE_METHOD_MASK;
+    if (m == FE_METHOD_TRFOE) return kMethodTrfoe;
     return (m == FE_METHOD_FERMI || (m == FE_METHOD_AUTO && p->kT > 0.0)) ? kMethodFermi : kMethodSp2;
 }
+
+// The buffers a problem's slot holds: the doubling recursion needs its own
+// set; the SP2 forms (plain, accelerated, truncated) share one layout.
+int slot_method(const fe_problem *p) { return method_of(p) == kMethodFermi ? kMethodFermi : kMethodSp2; }
 
 // Step cap of the finite-temperature expansion: about 12 products per
 // doubling (square, Newton-Schulz pairs, final product) for up to ~40
@@ -485,10 +501,19 @@ int validate(fe_ctx *ctx, const fe_problem *p) {
         return set_err(ctx, FE_EINVAL, "non-integral n_e at kT == 0");
     if (!(p->tol >= 0.0)) return set_err(ctx, FE_EINVAL, "tol < 0");
     const uint32_t m = p->flags & FE_METHOD_MASK;
-    if (m != FE_METHOD_AUTO && m != FE_METHOD_SP2 && m != FE_METHOD_FERMI)
+    if (m != FE_METHOD_AUTO && m != FE_METHOD_SP2 && m != FE_METHOD_FERMI && m != FE_METHOD_ASP2 &&
+        m != FE_METHOD_TRFOE)
         return set_err(ctx, FE_EINVAL, "unknown method flag");
-    if (m == FE_METHOD_SP2 && p->kT != 0.0)
+    if ((m == FE_METHOD_SP2 || m == FE_METHOD_ASP2) && p->kT != 0.0)
         return set_err(ctx, FE_EINVAL, "SP2 needs kT == 0");
+    if (m == FE_METHOD_ASP2 && !(std::isfinite(p->homo) && std::isfinite(p->lumo) && p->homo < p->lumo))
+        return set_err(ctx, FE_EINVAL, "FE_METHOD_ASP2 needs finite homo < lumo");
+    if (m == FE_METHOD_TRFOE) {
+        if (!(p->kT > 0.0)) return set_err(ctx, FE_EINVAL, "FE_METHOD_TRFOE needs kT > 0");
+        const uint32_t pt = prec_of(ctx, p);
+        if (pt != FE_PREC_MIXED && pt != FE_PREC_FP32 && pt != FE_PREC_FP64)
+            return set_err(ctx, FE_EINVAL, "FE_METHOD_TRFOE runs FE_PREC_MIXED, FE_PREC_FP32 or FE_PREC_FP64");
+    }
     const bool fermi = (m == FE_METHOD_FERMI) || (m == FE_METHOD_AUTO && p->kT > 0.0);
     if (fermi && !(p->kT > 0.0)) return set_err(ctx, FE_EINVAL, "FE_METHOD_FERMI needs kT > 0");
     const uint32_t pr = p->flags & FE_PREC_MASK;
@@ -521,6 +546,15 @@ void init_state(const fe_ctx *ctx, const fe_problem *p, SolveState *st) {
     st->fro_hist[0] = st->fro_hist[1] = st->fro_hist[2] = DBL_MAX;
     st->mu = NAN;
     st->method = method_of(p);
+    if ((p->flags & FE_METHOD_MASK) == FE_METHOD_ASP2) {
+        st->acc_on = 1;
+        st->homo = p->homo;
+        st->lumo = p->lumo;
+    }
+    if (st->method == kMethodTrfoe) {
+        st->beta = 1.0 / p->kT;
+        if (st->prec == kPrecTryFp16) st->prec = kPrecMixed;
+    }
     if (st->method == kMethodFermi) {
         st->max_iters = kFermiMaxSteps;
         st->wcur = kMatW0;
@@ -547,6 +581,7 @@ struct Job {
     const double *stage = nullptr;  // host Hp copied into slot->Hcopy at set-up, or null
     int64_t ldstage = 0;
     bool lanczos = true;            // estimate the spectral bounds (else Gershgorin)
+    bool accel = true;              // FE_METHOD_ASP2: folds on (off after an inconsistent attempt)
     int bn = 0;                     // tensor-core tile width, fixed for the whole solve (0: look up)
 };
 
@@ -554,6 +589,7 @@ Job make_job(const fe_problem *p, Slot *s) {
     Job j;
     j.p = p;
     j.slot = s;
+    j.lanczos = method_of(p) != kMethodTrfoe;  // the truncated expansion scales by Gershgorin
     if (p->flags & FE_PTR_DEVICE) {
         j.H = p->Hp;
         j.ldh = p->ld;
@@ -585,7 +621,12 @@ int eng_init(fe_ctx *ctx, Engine &e, cudaStream_t user_stream) {
         FE_CUDA(ctx, cudaStreamCreateWithFlags(&e.stream, cudaStreamNonBlocking));
         e.own_stream = true;
     }
-    FE_CUDA(ctx, cudaMalloc(&e.d_err, sizeof(int)));
+    FE_CUDA(ctx, cudaMalloc(&e.d_err, sizeof(DevCtl)));
+    {
+        DevCtl c0{};
+        c0.wait_ns = kWaitTimeoutNs;
+        FE_CUDA(ctx, cudaMemcpy(e.d_err, &c0, sizeof(DevCtl), cudaMemcpyHostToDevice));
+    }
     FE_CUDA(ctx, cudaMalloc(&e.d_flags, sizeof(StepFlags)));
     FE_CUDA(ctx, cudaMemset(e.d_flags, 0, sizeof(StepFlags)));
     FE_CUDA(ctx, cudaMalloc(&e.d_skws, sizeof(float) * kSkSlotFloats * ctx->num_sms));
@@ -636,6 +677,7 @@ int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
         hprobs[k].H = j.H;
         hprobs[k].ldh = j.ldh;
         const bool fermi = method_of(j.p) == kMethodFermi;
+        const bool trfoe = method_of(j.p) == kMethodTrfoe;  // its FP64 schedule runs digit products
         const uint32_t pr = prec_of(ctx, j.p);
         hprobs[k].tc_tile0 = static_cast<int>(tiles.size());
         hprobs[k].tc_ntiles = 0;
@@ -652,12 +694,12 @@ int eng_upload(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs) {
         }
         e.off64[k] = static_cast<int>(tiles64.size());
         e.cnt64[k] = 0;
-        if (pr == FE_PREC_FP64 && !fermi) {
+        if (pr == FE_PREC_FP64 && !fermi && !trfoe) {
             e.any_fp64 = true;
             for (Tile64 t : j.slot->tiles64) { t.prob = k; tiles64.push_back(t); }
             e.cnt64[k] = static_cast<int>(j.slot->tiles64.size());
         }
-        if ((pr == FE_PREC_MIXED || pr == FE_PREC_TRY_FP16) && !fermi) {
+        if ((pr == FE_PREC_MIXED || pr == FE_PREC_TRY_FP16 || (trfoe && pr == FE_PREC_FP64)) && !fermi) {
             e.any_digit = true;
             for (TileEnt t : j.slot->tilesD) { t.prob = k; tilesD.push_back(t); }
         }
@@ -704,6 +746,7 @@ int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int 
                                            cudaMemcpyHostToDevice, s));
         init_state(ctx, j.p, &e.h_states[k]);
         e.h_states[k].lz_on = j.lanczos ? 1 : 0;
+        if (!j.accel) e.h_states[k].acc_on = 0;
         FE_CUDA(ctx, cudaMemcpyAsync(j.slot->st, &e.h_states[k], sizeof(SolveState),
                                      cudaMemcpyHostToDevice, s));
         FE_CUDA(ctx, cudaMemsetAsync(j.slot->bad, 0, sizeof(int), s));
@@ -742,21 +785,21 @@ int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int 
                                                  cudaMemcpyDeviceToDevice, s));
                 tab = e.d_chk;
             }
-            k_control<<<nt, 256, 0, s>>>(tab, nt, nullptr, 0, 0, 0, 0, 0u);
+            k_control<<<nt, 256, 0, s>>>(tab, nt, e.d_err, nullptr, 0, 0, 0, 0, 0u);
             for (int c = 0; c < kCheckSteps; ++c) {
                 k_sym_mma<<<ctx->num_sms, kSymThreads, mma_smem_bytes(), s>>>(tab, nt, e.d_tiles, e.ntc, e.d_err,
                                                                            e.d_skws, e.d_skcnt);
-                k_control<<<nt, 256, 0, s>>>(tab, nt, nullptr, 0, 0, 0, 0, 0u);
+                k_control<<<nt, 256, 0, s>>>(tab, nt, e.d_err, nullptr, 0, 0, 0, 0, 0u);
             }
             ctx->launches += 1 + 2 * kCheckSteps;
         }
         for (int k : f64_chk) {
             const MmaProb *one = e.d_probs + k;
-            k_control<<<1, 256, 0, s>>>(one, 1, nullptr, 0, 0, 0, 0, 0u);
+            k_control<<<1, 256, 0, s>>>(one, 1, e.d_err, nullptr, 0, 0, 0, 0, 0u);
             for (int c = 0; c < kCheckSteps; ++c) {
                 k_fp64_step<<<std::max(1, std::min(e.cnt64[k], 4 * ctx->num_sms)), 256, 0, s>>>(
                     e.d_probs, e.d_tiles64 + e.off64[k], e.cnt64[k]);
-                k_control<<<1, 256, 0, s>>>(one, 1, nullptr, 0, 0, 0, 0, 0u);
+                k_control<<<1, 256, 0, s>>>(one, 1, e.d_err, nullptr, 0, 0, 0, 0, 0u);
             }
             ctx->launches += 1 + 2 * kCheckSteps;
         }
@@ -766,7 +809,7 @@ int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int 
         for (int k : f64_chk) k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
         ctx->launches += static_cast<long long>(tc_chk.size() + f64_chk.size());
     }
-    k_control<<<m, 256, 0, s>>>(e.d_probs + k0, m, nullptr, 0, 0, 0, 0, 0u);
+    k_control<<<m, 256, 0, s>>>(e.d_probs + k0, m, e.d_err, nullptr, 0, 0, 0, 0, 0u);
     ++ctx->launches;
     // the state images must stay valid until their copies ran
     FE_CUDA(ctx, cudaStreamSynchronize(s));
@@ -801,7 +844,7 @@ void eng_steps(fe_ctx *ctx, Engine &e, int np, int count, const std::vector<cuda
             ctx->launches += 2;
         }
         if (pev) cudaEventRecord((*pev)[4 * it + 3], s);
-        k_control<<<np, 256, 0, s>>>(e.d_probs, np, nullptr, 0, 0, 0, 0, 0u);
+        k_control<<<np, 256, 0, s>>>(e.d_probs, np, e.d_err, nullptr, 0, 0, 0, 0, 0u);
         ++ctx->launches;
     }
 }
@@ -935,7 +978,7 @@ int eng_graph(fe_ctx *ctx, Engine &e, int np) {
         return cudaGraphAddKernelNode(out, gr, dep, dep ? 1 : 0, &kp);
     };
     const MmaProb *probs = e.d_probs;
-    int *err = e.d_err;
+    DevCtl *err = e.d_err;
     cudaGraphNode_t kn, kn2;
     if (e.any_tc) {
         cudaGraph_t ib;
@@ -974,7 +1017,7 @@ int eng_graph(fe_ctx *ctx, Engine &e, int np) {
     {
         int npp = np;
         StepFlags *fl = e.d_flags;
-        void *args[] = {&probs, &npp, &fl, &hl, &ht, &hf, &hd, &hvalid};
+        void *args[] = {&probs, &npp, &err, &fl, &hl, &ht, &hf, &hd, &hvalid};
         FE_CUDA(ctx, add_kernel(body, reinterpret_cast<const void *>(k_control), np, 256, 0, args,
                                 prev ? &prev : nullptr, &kn));
     }
@@ -1088,28 +1131,50 @@ int run_problems_once(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) 
 
 // As run_problems_once; a problem whose spectral-bound estimate proved too
 // tight (an eigenvalue of X left [0, 1]) is solved again from the Gershgorin
-// bounds, which always contain the spectrum.
+// bounds, which always contain the spectrum, and an FE_METHOD_ASP2 problem
+// whose HOMO/LUMO estimates proved inconsistent with its spectrum is solved
+// again as plain SP2 (at most one of each, in that order of discovery);
+// fe_result.iters then includes the products of the abandoned attempts.
 int run_problems(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) {
     int rc = run_problems_once(ctx, jobs, rs);
-    std::vector<Job> again;
-    std::vector<int> where;
-    for (size_t k = 0; k < jobs.size(); ++k)
-        if (rs[k].status == kStatusEscaped) {
-            Job j = jobs[k];
-            j.lanczos = false;
-            again.push_back(j);
-            where.push_back(static_cast<int>(k));
+    std::vector<Job> cur = jobs;
+    std::vector<int> where(jobs.size());
+    for (size_t k = 0; k < jobs.size(); ++k) where[k] = static_cast<int>(k);
+    std::vector<int> wasted(jobs.size(), 0);
+    for (int round = 0; round < 2; ++round) {
+        std::vector<Job> again;
+        std::vector<int> at;
+        for (size_t q = 0; q < cur.size(); ++q) {
+            const int k = where[q];
+            const int st = rs[k].status;
+            if (st == kStatusEscaped && cur[q].lanczos) {
+                Job j = cur[q];
+                j.lanczos = false;
+                again.push_back(j);
+                at.push_back(k);
+            } else if (st == kStatusAccelFailed && cur[q].accel) {
+                Job j = cur[q];
+                j.accel = false;
+                again.push_back(j);
+                at.push_back(k);
+            }
         }
-    if (again.empty()) return rc;
-    std::vector<fe_result> rr(again.size());
-    run_problems_once(ctx, again, rr.data());
-    rc = FE_OK;
-    for (size_t q = 0; q < again.size(); ++q) {
-        if (rr[q].status == kStatusEscaped) rr[q].status = FE_ENOTCONV;
-        rs[where[q]] = rr[q];
+        if (again.empty()) break;
+        std::vector<fe_result> rr(again.size());
+        run_problems_once(ctx, again, rr.data());
+        for (size_t q = 0; q < again.size(); ++q) {
+            wasted[at[q]] += rs[at[q]].iters;
+            rs[at[q]] = rr[q];
+        }
+        cur.swap(again);
+        where.swap(at);
     }
-    for (size_t k = 0; k < jobs.size(); ++k)
+    rc = FE_OK;
+    for (size_t k = 0; k < jobs.size(); ++k) {
+        if (rs[k].status == kStatusEscaped || rs[k].status == kStatusAccelFailed) rs[k].status = FE_ENOTCONV;
+        rs[k].iters += wasted[k];
         if (rs[k].status != FE_OK && rc == FE_OK) rc = rs[k].status;
+    }
     return rc;
 }
 
@@ -1158,7 +1223,8 @@ Job job_of(Req *r) {
         j.stage = r->hbuf.data();
         j.ldstage = r->p.n;
     }
-    j.lanczos = !r->gershgorin;
+    j.lanczos = !r->gershgorin && method_of(&r->p) != kMethodTrfoe;
+    j.accel = !r->accel_off;
     j.bn = r->bn;
     return j;
 }
@@ -1180,7 +1246,12 @@ void serve_loop(fe_ctx *ctx) {
         for (Req *r : cand) {
             if (!r->slot) {
                 Slot *s = nullptr;
-                if (acquire_slot(ctx, static_cast<int>(r->p.n), method_of(&r->p), &s) != FE_OK) {
+                if (acquire_slot(ctx, static_cast<int>(r->p.n), slot_method(&r->p), &s) != FE_OK) {
+                    if (!r->deferred) {
+                        r->deferred = true;
+                        std::lock_guard<std::mutex> lk(ctx->qmu);
+                        ctx->n_deferred += 1;
+                    }
                     // blocking solves may hold the memory for a while; with
                     // nothing of ours running, give up after kAdmitWaitMs
                     if (running.empty() && ms_since(r->t_submit) > kAdmitWaitMs) failed.push_back(r);
@@ -1201,6 +1272,11 @@ void serve_loop(fe_ctx *ctx) {
                                ctx->waiting.end());
         }
         for (Req *r : failed) fail_req(ctx, r, FE_ENOMEM);
+        {
+            std::lock_guard<std::mutex> lk(ctx->qmu);
+            ctx->peak_running = std::max<long long>(ctx->peak_running,
+                                                    static_cast<long long>(running.size() + started.size()));
+        }
         if (running.empty() && started.empty()) {
             // requests wait for memory held elsewhere: poll again shortly
             std::unique_lock<std::mutex> lk(ctx->qmu);
@@ -1215,14 +1291,14 @@ void serve_loop(fe_ctx *ctx) {
         for (Req *r : all) jobs.push_back(job_of(r));
         const int np = static_cast<int>(all.size());
         int rc = FE_OK;
+        cudaMemsetAsync(e.d_err, 0, sizeof(int), e.stream);
+        cudaMemsetAsync(e.d_skcnt, 0, sizeof(int) * 2 * ctx->num_sms, e.stream);
         if (!started.empty()) {
             rc = eng_upload(ctx, e, jobs);
             if (rc == FE_OK) rc = eng_setup(ctx, e, jobs, k0, np);
         }
         int herr = 0;
         if (rc == FE_OK) {
-            cudaMemsetAsync(e.d_err, 0, sizeof(int), e.stream);
-            cudaMemsetAsync(e.d_skcnt, 0, sizeof(int) * 2 * ctx->num_sms, e.stream);
             eng_steps(ctx, e, np, kServeSteps, nullptr);
             for (int k = 0; k < np; ++k)
                 cudaMemcpyAsync(&e.h_done[k], &all[k]->slot->st->done, sizeof(int),
@@ -1258,14 +1334,19 @@ void serve_loop(fe_ctx *ctx) {
             fe_result res;
             fill_result(e.h_states[k], 0, 0.0, res);
             if (rc != FE_OK) res.status = rc;
-            if (res.status == kStatusEscaped && !r->gershgorin) {
-                // start again from the Gershgorin bounds (Hp is in the slot)
-                r->gershgorin = true;
+            if ((res.status == kStatusEscaped && !r->gershgorin) ||
+                (res.status == kStatusAccelFailed && !r->accel_off)) {
+                // start again (Hp is in the slot): from the Gershgorin bounds,
+                // or as plain SP2 when the HOMO/LUMO estimates were inconsistent
+                if (res.status == kStatusEscaped) r->gershgorin = true;
+                else r->accel_off = true;
+                r->wasted += res.iters;
                 r->staged = true;
                 redo.push_back(r);
                 continue;
             }
-            if (res.status == kStatusEscaped) res.status = FE_ENOTCONV;
+            if (res.status == kStatusEscaped || res.status == kStatusAccelFailed) res.status = FE_ENOTCONV;
+            res.iters += r->wasted;
             release_slot(ctx, r->slot);
             r->slot = nullptr;
             publish(ctx, r, res);
@@ -1434,7 +1515,7 @@ extern "C" int fe_solve(fe_ctx *ctx, const fe_problem *p, fe_result *r) {
     if (rc != FE_OK) return r->status = rc;
     cudaSetDevice(ctx->device);
     Slot *s = nullptr;
-    rc = acquire_slot(ctx, static_cast<int>(p->n), method_of(p), &s);
+    rc = acquire_slot(ctx, static_cast<int>(p->n), slot_method(p), &s);
     if (rc != FE_OK) return r->status = rc;
     std::vector<Job> jobs{make_job(p, s)};
     rc = run_problems(ctx, jobs, r);
@@ -1456,7 +1537,7 @@ extern "C" int fe_solve_batch(fe_ctx *ctx, int count, const fe_problem *ps, fe_r
         memset(&rs[k], 0, sizeof(fe_result));
         int rc = validate(ctx, &ps[k]);
         Slot *s = nullptr;
-        if (rc == FE_OK) rc = acquire_slot(ctx, static_cast<int>(ps[k].n), method_of(&ps[k]), &s);
+        if (rc == FE_OK) rc = acquire_slot(ctx, static_cast<int>(ps[k].n), slot_method(&ps[k]), &s);
         if (rc != FE_OK) {
             rs[k].status = rc;
             if (first == FE_OK) first = rc;
@@ -1483,7 +1564,7 @@ extern "C" int fe_submit(fe_ctx *ctx, const fe_problem *p, fe_ticket *t) {
     int rc = validate(ctx, p);
     if (rc != FE_OK) return rc;
     const int n = static_cast<int>(p->n);
-    const int method = method_of(p);
+    const int method = slot_method(p);
     {
         int a, b, c;
         size_t np;
@@ -1533,6 +1614,12 @@ extern "C" int fe_submit(fe_ctx *ctx, const fe_problem *p, fe_ticket *t) {
         r->id = ctx->next_ticket++;
         ctx->reqs[r->id] = r;
         ctx->waiting.push_back(r);
+        ctx->n_submitted += 1;
+        if (!r->slot) {
+            r->deferred = true;  // no room at submission: Hp waits in host memory
+            ctx->n_deferred += 1;
+        }
+        ctx->peak_waiting = std::max<long long>(ctx->peak_waiting, static_cast<long long>(ctx->waiting.size()));
         if (!ctx->worker_started) {
             ctx->worker = std::thread(serve_loop, ctx);
             ctx->worker_started = true;
@@ -1719,6 +1806,35 @@ extern "C" int fe_k_profile(fe_ctx *ctx, int enable) {
     if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     ctx->prof = enable != 0;
+    return FE_OK;
+}
+
+extern "C" int fe_k_serve_stats(fe_ctx *ctx, int64_t *out4, int reset) {
+    if (!ctx || !out4) return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lk(ctx->qmu);
+    out4[0] = ctx->n_submitted;
+    out4[1] = ctx->n_deferred;
+    out4[2] = ctx->peak_waiting;
+    out4[3] = ctx->peak_running;
+    if (reset) ctx->n_submitted = ctx->n_deferred = ctx->peak_waiting = ctx->peak_running = 0;
+    return FE_OK;
+}
+
+extern "C" int fe_k_set_wait(fe_ctx *ctx, double limit_ms, int fail_partner) {
+    if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
+    if (!(limit_ms > 0.0 && limit_ms <= 60000.0)) return set_err(ctx, FE_EINVAL, "limit_ms must be in (0, 60000]");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    DevCtl c{};
+    c.fail_partner = fail_partner ? 1 : 0;
+    c.wait_ns = static_cast<unsigned long long>(limit_ms * 1e6);
+    for (Engine *e : {&ctx->eng, &ctx->seng}) {
+        // every field after the error word; the streams order it after earlier work
+        FE_CUDA(ctx, cudaMemcpyAsync(reinterpret_cast<char *>(e->d_err) + sizeof(int),
+                                     reinterpret_cast<const char *>(&c) + sizeof(int), sizeof(DevCtl) - sizeof(int),
+                                     cudaMemcpyHostToDevice, e->stream));
+        FE_CUDA(ctx, cudaStreamSynchronize(e->stream));
+    }
     return FE_OK;
 }
 

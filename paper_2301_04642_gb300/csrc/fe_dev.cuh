@@ -65,13 +65,31 @@ enum DevErr : int {
     kErrTimeoutPartner = 5, // the partial sums of a split tile never arrived
 };
 
-// bounded waits give up after this many nanoseconds of wall time
+// bounded waits give up after this many nanoseconds of wall time unless the
+// context sets another limit (DevCtl::wait_ns)
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;
+
+// Device control block of one engine, passed to the kernels that wait: the
+// first error code of the run (the host clears it before each run), the
+// limit of every bounded wait, and a test hook.  With fail_partner set, the
+// wait of the second CTA of a split tile in k_sym_mma watches `never` (a word
+// nothing writes) instead of its partner's flag, so the wait runs out, the
+// kernel records kErrTimeoutPartner and returns; it exists to test that
+// expiry path.
+struct DevCtl {
+    int err;
+    int fail_partner;
+    int never;
+    int pad;
+    unsigned long long wait_ns;
+};
 
 constexpr int kHistRows = 160;  // per-step history kept in the solve state
 constexpr int kLanczosSteps = 12;   // Lanczos steps of the spectral-bound estimate
 constexpr int kCheckSteps = 3;      // logistic steps certifying the estimate (T_8)
 constexpr int kStatusEscaped = -100;  // internal: an eigenvalue left [0, 1] (bounds too tight)
+constexpr int kStatusAccelFailed = -101;  // internal: HOMO/LUMO estimates inconsistent (run plain SP2)
+constexpr int kTrfoeMaxSteps = 128;   // branch bits kept for the truncated expansion
 constexpr int kHistCols = 6;
 
 // ---------------------------------------------------------------- state
@@ -83,7 +101,9 @@ enum Kind : int { kNone = 0, kTcSingle = 1, kTcSplit = 2, kFp64 = 3, kDf = 4, kT
                   kDigit = 6 };
 enum Phase : int { kPhaseSingle = 0, kPhaseSplit = 1, kPhaseFp64 = 2, kPhaseDone = 3 };
 enum Prec : int { kPrecMixed = 0, kPrecFp64 = 1, kPrecFp32 = 2, kPrecTryFp16 = 3 };
-enum Method : int { kMethodSp2 = 0, kMethodFermi = 1 };
+// kMethodSp2 also runs the accelerated form (SolveState::acc_on); kMethodTrfoe
+// is the truncated SP2 expansion at finite temperature.
+enum Method : int { kMethodSp2 = 0, kMethodFermi = 1, kMethodTrfoe = 2 };
 
 // Output of one tensor-core step: value = a v + b1 E1 + b2 E2 + c [i == j],
 // v the product (A~ B~)_ij, E1/E2 FP32 masters of the epilogue inputs.
@@ -150,6 +170,15 @@ struct SolveState {
     float s_next;       // slice scale of the zero-temperature iterate after this step
     double c_next;
     double gamma;       // FP64-accurate step: X' = F(X) + gamma (X - X^2) (trace correction)
+    // accelerated SP2 (A-Z-RFOE): with acc_on the unoccupied eigenvalues of X
+    // lie in [acc_a, ...] = [0, acc_a] and the occupied ones in [acc_b, 1];
+    // homo/lumo are the caller's estimates (host), acc_*_next the interval
+    // after the product issued, acc_fold 1 when that product was folded
+    int acc_on, acc_fold;
+    double homo, lumo, acc_a, acc_b, acc_a_next, acc_b_next;
+    // truncated SP2 at finite temperature: branch of product k in bit k
+    unsigned tr_bits[kTrfoeMaxSteps / 32];
+    double tr_slope;    // |dG_m/de| at the midpoint after the last product
     // convergence bookkeeping
     int iter, phase, nparts, done, status;
     int it_phase[4];
@@ -202,12 +231,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase with the given parity; false after kWaitTimeoutNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// Wait for the phase with the given parity; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > kWaitTimeoutNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
     return true;
 }

@@ -73,7 +73,7 @@ struct Tile64 {
 // active problems.  ws: kSkSlotFloats floats per participating CTA (partial
 // sums of a split tile); cnt: 2 ints per CTA, zero between launches.
 __global__ void k_sym_mma(const MmaProb *__restrict__ probs, int nprobs,
-                          const TileEnt *__restrict__ tiles, int ntiles, int *err, float *ws, int *cnt);
+                          const TileEnt *__restrict__ tiles, int ntiles, DevCtl *ctl, float *ws, int *cnt);
 constexpr size_t kSkSlotFloats = static_cast<size_t>(kTileM) * kTileN;  // 128 KiB per slot
 size_t mma_smem_bytes();
 
@@ -156,7 +156,9 @@ struct StepFlags {
 };
 // Control step: one block per problem.  With flags (inside the step graph)
 // the last block to finish also sets the graph's loop and kernel switches.
-__global__ void k_control(const MmaProb *probs, int nprobs, StepFlags *flags,
+// Once a kernel of the run has recorded an error in ctl (a bounded wait ran
+// out), every problem ends with FE_ETIMEOUT.
+__global__ void k_control(const MmaProb *probs, int nprobs, const DevCtl *ctl, StepFlags *flags,
                           cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_tc,
                           cudaGraphConditionalHandle h_fp64, cudaGraphConditionalHandle h_digit,
                           unsigned hvalid);
@@ -168,7 +170,7 @@ __global__ void k_finalize_reduce(const MmaProb *probs, int prob);
 
 // FP64-accurate X^2 on the tensor cores from digit-split operands (kind kDigit).
 __global__ void k_digit_mma(const MmaProb *__restrict__ probs, const TileEnt *__restrict__ tiles,
-                            int ntiles, int *err);
+                            int ntiles, DevCtl *ctl);
 size_t digit_smem_bytes();
 // Digits of the current iterate for every problem whose next step is kDigit.
 __global__ void k_digit_prep(const MmaProb *probs, int nprobs);

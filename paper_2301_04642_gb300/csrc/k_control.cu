@@ -144,6 +144,24 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
         st->xcur ^= 1;
         st->x_fp64 = 1;
     }
+    if (st->acc_fold) {
+        st->acc_a = st->acc_a_next;
+        st->acc_b = st->acc_b_next;
+    }
+    if (st->acc_on && st->iter == 0) {
+        // A-Z-RFOE (Sec. II-B2): with X0 = (eps_max I - H)/w the estimates
+        // put the unoccupied eigenvalues in [0, a] and the occupied ones in
+        // [b, 1]; estimates that do not bracket a gap inside the bounds give
+        // no information (plain SP2)
+        const double w = st->emax - st->emin;
+        const double a = (st->emax - st->lumo) / w, b = (st->emax - st->homo) / w;
+        if (w > 0.0 && a >= 0.0 && b <= 1.0 && a < b) {
+            st->acc_a = a;
+            st->acc_b = b;
+        } else {
+            st->acc_on = 0;
+        }
+    }
     if (prev_kind != kNone) {
         // ||X_k^2 - X_k||_F of the input of the product that just ran
         const double fro = sqrt(fmax(rsq, 0.0));
@@ -191,6 +209,21 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
         st->status = st->lz_on ? kStatusEscaped : -3;  // -3: FE_ENOTCONV
         done = true;
     }
+    if (!done && st->acc_on && st->acc_fold) {
+        // The folds keep N_e eigenvalues in [b, 1] and n - N_e in [0, a] only
+        // when the HOMO/LUMO estimates lie inside the gap.  Then
+        //   N_e b <= tr X <= N_e + (n - N_e) a,
+        //   tr X - tr X^2 = sum x (1 - x) <= (n - N_e) a + N_e (1 - b);
+        // a state on the wrong side, or one left between a and b, breaks one
+        // of these by a whole state once a and 1 - b are small.  A violation
+        // by more than 1/2 ends this attempt; the host runs plain SP2.
+        const double a = st->acc_a, b = st->acc_b;
+        const double spread = (nn - ne) * a + ne * (1.0 - b);
+        if (t1 < ne * b - 0.5 || t1 > ne + (nn - ne) * a + 0.5 || idem > spread + 0.5) {
+            st->status = kStatusAccelFailed;
+            done = true;
+        }
+    }
     if (phase == kPhaseSingle && reltr < 5e-4) phase = kPhaseSplit;  // the paper's switch point
     if (phase == kPhaseSplit && prev_kind == kTcSplit) {
         // The split products carry ~22 bits and the FP32 master 24, so the
@@ -227,7 +260,15 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
             const bool idem_small = idem >= -1e-12 && idem <= 5e-9;
             const bool trace_ok = fabs(t1 - ne) <= 5e-10;
             const bool pair_ok = (nfp64 & 1) == 0 ? f0 * f0 <= 5e-9 : true;
-            if (nfp64 >= 2 && ((idem_small && trace_ok && pair_ok) || nfp64 >= 6)) done = true;
+            if (nfp64 >= 2 && idem_small && trace_ok && pair_ok) {
+                done = true;
+            } else if (nfp64 >= 6) {
+                // three pairs did not reach the trace and idempotency targets
+                // (a HOMO/LUMO gap too small to resolve, or a degenerate
+                // Fermi level split by N_e): D is not the projector
+                st->status = -3;  // FE_ENOTCONV
+                done = true;
+            }
         }
     }
     if (!done && st->iter >= st->max_iters) {
@@ -267,17 +308,144 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
     }
     st->sq = sq;
     st->phase = phase;
+    st->acc_fold = 0;
     if (phase == kPhaseFp64) {
         st->kind = (st->prec == kPrecFp64) ? kFp64 : kDigit;
+        st->acc_on = 0;  // the FP64-accurate steps are plain SP2 (a and 1 - b are ~0 by now)
     } else {
         st->kind = (phase == kPhaseSingle) ? kTcSingle : kTcSplit;
-        // X = c I + Y:  X^2 -> c' = c^2, Y' = 2c Y + Y^2;  2X - X^2 -> c' = 2c - c^2,
-        // Y' = (2 - 2c) Y - Y^2
+        // The step's polynomial, folded over the interval that has to shrink
+        // when A-Z-RFOE is on (fold point sf; sf = 0 is the SP2 step):
+        //   X^2 branch:      X' = r (X - sf I)^2,             sf = a / 2
+        //   2X - X^2 branch: X' = r (2 (1 - sf) X - X^2),    sf = (1 - b) / 2
+        // with r = 1 / (1 - sf)^2.  With X = c I + Y:
+        //   X^2:      c' = r (c - sf)^2,            Y' = r (2 (c - sf) Y + Y^2)
+        //   2X - X^2: c' = r (2 (1 - sf) c - c^2),  Y' = r ((2 (1 - sf) - 2c) Y - Y^2)
+        double sf = 0.0;
+        if (st->acc_on) {
+            sf = sq ? 0.5 * st->acc_a : 0.5 * (1.0 - st->acc_b);
+            const double rr = 1.0 / ((1.0 - sf) * (1.0 - sf));
+            const double a = st->acc_a, b = st->acc_b;
+            st->acc_a_next = sq ? rr * (a - sf) * (a - sf) : rr * (2.0 * (1.0 - sf) * a - a * a);
+            st->acc_b_next = sq ? rr * (b - sf) * (b - sf) : rr * (2.0 * (1.0 - sf) * b - b * b);
+            st->acc_fold = 1;
+        }
+        const double r = 1.0 / ((1.0 - sf) * (1.0 - sf));
+        const double alpha = sq ? 2.0 * (cc - sf) : 2.0 * (1.0 - sf) - 2.0 * cc;
+        const double cn = sq ? r * ((cc - sf) * (cc - sf)) : r * (2.0 * (1.0 - sf) * cc - cc * cc);
+        st->c_next = cn;
+        // entries of Y' = X' - c' I are bounded by its spectral radius:
+        // spec(X') in [0, 1] gives max(c', 1 - c'); also r ||alpha Y + sigma Y^2||_F
+        const double fro = sqrt(fmax(sumsq, 0.0));
+        const double bound = fmin(fmax(cn, 1.0 - cn) + 1e-3, r * (fabs(alpha) * fro + fro * fro));
+        const int cur = st->cur;
+        ProdOp &op = st->op;
+        const double s = st->s_cur;
+        begin_op(op, cur, cur, cur, -1, 1.0 / (s * s));
+        op.nout = 1;
+        set_out(op.out[0], cur ^ 1, kOutMaster | kOutSlices, sq ? r : -r, r * alpha, 0.0, 0.0, bound);
+        st->s_next = op.out[0].s;
+        // ||X^2 - X||: X^2 - X = Y^2 + (2c - 1) Y + (c^2 - c) I
+        op.ra = 1.0f;
+        op.rb = static_cast<float>(2.0 * cc - 1.0);
+        op.rc = static_cast<float>(cc * cc - cc);
+    }
+    st->t1_prev = t1;
+    st->it_phase[phase] += 1;
+    st->iter += 1;
+}
+
+// ------------------------------------------------- truncated SP2 at finite T
+// The paper's T-RFOE (Sec. II-B3, Eq. (2)): D = G_m(X0), the SP2 recursion
+// with the trace rule stopped after m products, X0 from the Gershgorin
+// bounds.  m is read as the first step whose step function is as steep at
+// its midpoint (G_m = 1/2) as Fermi-Dirac at mu: |dG_m/de| >= beta / 4.
+// With u_m = 1/2 and u_k = F_k^{-1}(u_{k+1}) (sqrt(y) after X^2,
+// 1 - sqrt(1 - y) after 2X - X^2), |dG_m/de| = (1/w) prod F_k'(u_k),
+// F' = 2u or 2 - 2u, and the midpoint energy is eps_max - w u_0.
+__device__ double trfoe_slope(const SolveState *st, int m, double w, double *mid) {
+    double u = 0.5, d = 1.0;
+    for (int k = m - 1; k >= 0; --k) {
+        const bool sq = (st->tr_bits[k >> 5] >> (k & 31)) & 1u;
+        u = sq ? sqrt(u) : 1.0 - sqrt(1.0 - u);
+        d *= sq ? 2.0 * u : 2.0 - 2.0 * u;
+    }
+    *mid = u;
+    return d / w;
+}
+
+__device__ void control_trfoe(SolveState *st, double trV, double sumsq) {
+    const int n = st->n;
+    const double ne = st->ne;
+    const double nes = fmax(ne, 1.0);
+    const int prev_kind = st->kind;
+    if (prev_kind == kTcSingle || prev_kind == kTcSplit) {
+        st->c = st->c_next;
+        st->s_cur = st->s_next;
+        st->cur ^= 1;
+    } else if (prev_kind == kFp64 || prev_kind == kDf || prev_kind == kDigit) {
+        st->xcur ^= 1;
+        st->x_fp64 = 1;
+    }
+    double t1, t2;
+    const double cc = st->c;
+    if (st->x_fp64) {
+        t1 = trV;
+        t2 = sumsq;
+    } else {
+        t1 = n * cc + trV;
+        t2 = n * cc * cc + 2.0 * cc * trV + sumsq;
+    }
+    const double reltr = (st->iter > 0) ? fabs(t1 - st->t1_prev) / nes : DBL_MAX;
+    st->t1 = t1;
+    st->t2 = t2;
+    st->reltr = reltr;
+    const int m = st->iter;
+    const double w = st->emax - st->emin;
+    double mid;
+    const double slope = trfoe_slope(st, m, w > 0.0 ? w : 1.0, &mid);
+    st->tr_slope = slope;
+    if (st->iter < kHistRows) {
+        double *h = st->hist[st->iter];
+        h[0] = st->phase;
+        h[1] = prev_kind;
+        h[2] = t1 - ne;
+        h[3] = t1 - t2;
+        h[4] = slope;
+        h[5] = (st->iter > 0) ? reltr : -1.0;
+    }
+    if (slope >= 0.25 * st->beta) {
+        st->mu = st->emax - w * mid;
+        st->done = 1;
+        st->phase = kPhaseDone;
+        st->kind = kNone;
+        return;
+    }
+    const int cap = st->max_iters < kTrfoeMaxSteps ? st->max_iters : kTrfoeMaxSteps;
+    if (m >= cap) {
+        st->status = -3;  // FE_ENOTCONV
+        st->done = 1;
+        st->phase = kPhaseDone;
+        st->kind = kNone;
+        return;
+    }
+    // precision: split FP16 products until RelTr < 5e-4 (the paper's switch
+    // point), then FP64-accurate ones; FP32 keeps the split products
+    int phase = st->phase;
+    if (phase == kPhaseSplit && st->prec == kPrecMixed && m > 0 && reltr < 5e-4) phase = kPhaseFp64;
+    const int sq = fabs(t2 - ne) <= fabs(2.0 * t1 - t2 - ne);
+    if (sq) st->tr_bits[m >> 5] |= 1u << (m & 31);
+    else st->tr_bits[m >> 5] &= ~(1u << (m & 31));
+    st->sq = sq;
+    st->gamma = 0.0;
+    st->phase = phase;
+    if (phase == kPhaseFp64) {
+        st->kind = kDigit;  // FP64-accurate tensor-core products (FE_PREC_FP64 from the start)
+    } else {
+        st->kind = kTcSplit;
         const double alpha = sq ? 2.0 * cc : 2.0 - 2.0 * cc;
         const double cn = sq ? cc * cc : 2.0 * cc - cc * cc;
         st->c_next = cn;
-        // entries of Y' = X' - c' I are bounded by its spectral radius:
-        // spec(X') in [0, 1] gives max(c', 1 - c'); also ||alpha Y + sigma Y^2||_F
         const double fro = sqrt(fmax(sumsq, 0.0));
         const double bound = fmin(fmax(cn, 1.0 - cn) + 1e-3, fabs(alpha) * fro + fro * fro);
         const int cur = st->cur;
@@ -287,7 +455,6 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
         op.nout = 1;
         set_out(op.out[0], cur ^ 1, kOutMaster | kOutSlices, sq ? 1.0 : -1.0, alpha, 0.0, 0.0, bound);
         st->s_next = op.out[0].s;
-        // ||X^2 - X||: X^2 - X = Y^2 + (2c - 1) Y + (c^2 - c) I
         op.ra = 1.0f;
         op.rb = static_cast<float>(2.0 * cc - 1.0);
         op.rc = static_cast<float>(cc * cc - cc);
@@ -538,9 +705,19 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
 
 namespace {
 
-__device__ void control_one(const MmaProb &pr) {
+__device__ void control_one(const MmaProb &pr, const DevCtl *ctl) {
     SolveState *st = pr.st;
     if (st->done) return;
+    if (ctl && *reinterpret_cast<const volatile int *>(&ctl->err) != 0) {
+        // a kernel of this run gave up a bounded wait: its outputs are not
+        // trustworthy, so the expansion stops here
+        if (threadIdx.x == 0) {
+            st->status = -4;  // FE_ETIMEOUT
+            st->done = 1;
+            st->kind = kNone;
+        }
+        return;
+    }
 
     // number of partial slots written by the previous producer
     int nparts;
@@ -579,17 +756,18 @@ __device__ void control_one(const MmaProb &pr) {
     }
     if (st->chk_left > 0 || st->chk) control_check(st, s_a[0], s_b[0]);
     else if (st->method == kMethodFermi) control_fermi(st, s_a[0], s_b[0], s_c[0]);
+    else if (st->method == kMethodTrfoe) control_trfoe(st, s_a[0], s_b[0]);
     else control_sp2(st, s_a[0], s_b[0], s_d[0]);
 }
 
 }  // namespace
 
-__global__ void k_control(const MmaProb *probs, int nprobs, StepFlags *flags,
+__global__ void k_control(const MmaProb *probs, int nprobs, const DevCtl *ctl, StepFlags *flags,
                           cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_tc,
                           cudaGraphConditionalHandle h_fp64, cudaGraphConditionalHandle h_digit,
                           unsigned hvalid) {
     const int p = blockIdx.x;
-    if (p < nprobs) control_one(probs[p]);
+    if (p < nprobs) control_one(probs[p], ctl);
     if (!flags || threadIdx.x != 0) return;
     // Inside the step graph: collect what the next step needs over all
     // problems; the block that finishes last sets the graph's conditions

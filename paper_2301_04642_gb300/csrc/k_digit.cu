@@ -72,7 +72,7 @@ __device__ __forceinline__ int step_kind(const SolveState *st) {
     return *reinterpret_cast<const volatile int *>(&st->kind);
 }
 
-__device__ __forceinline__ void record_error(int *err, int code) { atomicCAS(err, 0, code); }
+__device__ __forceinline__ void record_error(DevCtl *ctl, int code) { atomicCAS(&ctl->err, 0, code); }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
@@ -165,7 +165,7 @@ __global__ void k_digit_prep(const MmaProb *probs, int nprobs) {
 
 __global__ void __launch_bounds__(kMmaThreads, 1)
     k_digit_mma(const MmaProb *__restrict__ probs, const TileEnt *__restrict__ tiles, int ntiles,
-                int *err) {
+                DevCtl *ctl) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t base_u32 = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const uint64_t wait_ns = ctl->wait_ns;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kDigitStages; ++s) {
@@ -209,10 +210,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             const int nk = (pr.n + kDigitK - 1) / kDigitK;
             for (int kc = 0; kc < nk; ++kc) {
                 bool got = true;
-                if (lane == 0) got = mbar_wait_bounded(&tail->empty[stage], phase ^ 1u);
+                if (lane == 0) got = mbar_wait_bounded(&tail->empty[stage], phase ^ 1u, wait_ns);
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
-                    if (lane == 0) record_error(err, kErrTimeoutEmpty);
+                    if (lane == 0) record_error(ctl, kErrTimeoutEmpty);
                     ok = false;
                     break;
                 }
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             tail->abort_flag = 1;
             if (lane == 0)
                 for (int s = 0; s < kDigitStages; ++s)
-                    if (issued[s]) (void)mbar_wait_bounded(&tail->full[s], last_phase[s]);
+                    if (issued[s]) (void)mbar_wait_bounded(&tail->full[s], last_phase[s], wait_ns);
             __syncwarp();
         }
     } else if (warp == 1) {
@@ -254,10 +255,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                 const bool first = (sb == 0);
                 const bool last = (sb == kStagesPerBlock - 1) || (kc == nk - 1);
                 bool got = true;
-                if (lane == 0) got = mbar_wait_bounded(&tail->full[stage], phase);
+                if (lane == 0) got = mbar_wait_bounded(&tail->full[stage], phase, wait_ns);
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
-                    if (lane == 0) record_error(err, kErrTimeoutFull);
+                    if (lane == 0) record_error(ctl, kErrTimeoutFull);
                     ok = false;
                     break;
                 }
@@ -285,8 +286,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                             if (first && a == 0 && got) {
                                 // the drain of these levels' previous block must be done
                                 for (int l = L; l < L + w && got; ++l)
-                                    got = mbar_wait_bounded(&tail->lfree[l], (blk & 1u) ^ 1u);
-                                if (!got) record_error(err, kErrTimeoutTmem);
+                                    got = mbar_wait_bounded(&tail->lfree[l], (blk & 1u) ^ 1u, wait_ns);
+                                if (!got) record_error(ctl, kErrTimeoutTmem);
                             }
                             if (got) {
                                 const uint32_t tmem_d = tmem_base + static_cast<uint32_t>(L * kDigitN);
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             // every issued MMA must finish before TMEM is released
             if (lane == 0 && any_commit) {
                 tc_commit(&tail->abort_bar);
-                (void)mbar_wait_bounded(&tail->abort_bar, 0);
+                (void)mbar_wait_bounded(&tail->abort_bar, 0, wait_ns);
             }
             __syncwarp();
         }
@@ -345,10 +346,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             for (int b = 0; b < nb && ok; ++b) {
 #pragma unroll 1
                 for (int L = 0; L < kDigits; ++L) {
-                    bool got = mbar_wait_bounded(&tail->lfull[L], blk & 1u);
+                    bool got = mbar_wait_bounded(&tail->lfull[L], blk & 1u, wait_ns);
                     got = __all_sync(0xffffffffu, got);
                     if (!got) {
-                        if (lane == 0) record_error(err, kErrTimeoutTmem);
+                        if (lane == 0) record_error(ctl, kErrTimeoutTmem);
                         ok = false;
                         break;
                     }

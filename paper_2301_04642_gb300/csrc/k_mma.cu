@@ -99,7 +99,7 @@ __device__ __forceinline__ int step_chunks(const SolveState *st, int n) {
 // tile width of a problem: 128 or 256 columns
 __device__ __forceinline__ int tile_bn(const MmaProb &pr) { return pr.bn == kTileM ? kTileM : kTileN; }
 
-__device__ __forceinline__ void record_error(int *err, int code) { atomicCAS(err, 0, code); }
+__device__ __forceinline__ void record_error(DevCtl *ctl, int code) { atomicCAS(&ctl->err, 0, code); }
 
 // named barrier of the 8 drain/epilogue warps
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
@@ -370,12 +370,12 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     return v;
 }
 
-// Wait for a flag that a running CTA sets; false after kWaitTimeoutNs.
-__device__ __forceinline__ bool flag_wait_bounded(const int *f) {
+// Wait for a flag that a running CTA sets; false after limit_ns.
+__device__ __forceinline__ bool flag_wait_bounded(const int *f, uint64_t limit_ns) {
     if (ld_acquire(f)) return true;
     const uint64_t t0 = globaltimer();
     while (!ld_acquire(f)) {
-        if (globaltimer() - t0 > kWaitTimeoutNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
         __nanosleep(64);
     }
     return true;
@@ -385,7 +385,7 @@ __device__ __forceinline__ bool flag_wait_bounded(const int *f) {
 
 __global__ void __launch_bounds__(kSymThreads, 1)
     k_sym_mma(const MmaProb *__restrict__ probs, int nprobs, const TileEnt *__restrict__ tiles,
-              int ntiles, int *err, float *ws, int *cnt) {
+              int ntiles, DevCtl *ctl, float *ws, int *cnt) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t base_u32 = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (base_u32 & 1023u)) & 1023u);
@@ -394,6 +394,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const uint64_t wait_ns = ctl->wait_ns;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -444,10 +445,10 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             const uint32_t bytes = static_cast<uint32_t>(S * (kSliceABytes + (wide ? kSliceBBytes : kSliceABytes)));
             for (int kc = sg.k0; kc < sg.k0 + sg.nch; ++kc) {
                 bool got = true;
-                if (lane == 0) got = mbar_wait_bounded(&tail->empty[stage], phase ^ 1u);
+                if (lane == 0) got = mbar_wait_bounded(&tail->empty[stage], phase ^ 1u, wait_ns);
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
-                    if (lane == 0) record_error(err, kErrTimeoutEmpty);
+                    if (lane == 0) record_error(ctl, kErrTimeoutEmpty);
                     ok = false;
                     break;
                 }
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             tail->abort_flag = 1;
             if (lane == 0)
                 for (int s = 0; s < kStages; ++s)
-                    if (issued[s]) (void)mbar_wait_bounded(&tail->full[s], last_phase[s]);
+                    if (issued[s]) (void)mbar_wait_bounded(&tail->full[s], last_phase[s], wait_ns);
             __syncwarp();
         }
     } else if (warp == 1) {
@@ -497,14 +498,14 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 const uint32_t buf = chunk & 1u;
                 const uint32_t cph = (chunk >> 1) & 1u;
                 bool got = true;
-                if (lane == 0) got = mbar_wait_bounded(&tail->cempty[buf], cph ^ 1u);
+                if (lane == 0) got = mbar_wait_bounded(&tail->cempty[buf], cph ^ 1u, wait_ns);
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (got) {
-                    if (lane == 0) got = mbar_wait_bounded(&tail->full[stage], phase);
+                    if (lane == 0) got = mbar_wait_bounded(&tail->full[stage], phase, wait_ns);
                     got = __shfl_sync(0xffffffffu, got, 0);
-                    if (!got && lane == 0) record_error(err, kErrTimeoutFull);
+                    if (!got && lane == 0) record_error(ctl, kErrTimeoutFull);
                 } else if (lane == 0) {
-                    record_error(err, kErrTimeoutTmem);
+                    record_error(ctl, kErrTimeoutTmem);
                 }
                 if (!got) {
                     ok = false;
@@ -550,7 +551,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             if (lane == 0 && any_commit) {
                 uint64_t *drain = &tail->cfull[chunk & 1u];
                 tc_commit(drain);
-                (void)mbar_wait_bounded(drain, (chunk >> 1) & 1u);
+                (void)mbar_wait_bounded(drain, (chunk >> 1) & 1u, wait_ns);
             }
             __syncwarp();
         }
@@ -580,10 +581,10 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             for (int kc = sg.k0; kc < sg.k0 + sg.nch; ++kc) {
                 const uint32_t buf = chunk & 1u;
                 const uint32_t cph = (chunk >> 1) & 1u;
-                bool got = mbar_wait_bounded(&tail->cfull[buf], cph);
+                bool got = mbar_wait_bounded(&tail->cfull[buf], cph, wait_ns);
                 got = __all_sync(0xffffffffu, got);
                 if (!got) {
-                    if (lane == 0) record_error(err, kErrTimeoutTmem);
+                    if (lane == 0) record_error(ctl, kErrTimeoutTmem);
                     ok = false;
                     break;
                 }
@@ -639,12 +640,15 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                     if (ew == 0 && lane == 0) atomicExch(&cnt[2 * slot + 1], 1);
                     continue;
                 }
-                if (ew == 0 && lane == 0) tail->sk_ok = flag_wait_bounded(&cnt[2 * slot + 1]) ? 1 : 0;
+                if (ew == 0 && lane == 0) {
+                    const int *flag = ctl->fail_partner ? &ctl->never : &cnt[2 * slot + 1];
+                    tail->sk_ok = flag_wait_bounded(flag, wait_ns) ? 1 : 0;
+                }
                 epi_bar();
                 const bool got = tail->sk_ok != 0;
                 epi_bar();
                 if (!got) {
-                    if (ew == 0 && lane == 0) record_error(err, kErrTimeoutPartner);
+                    if (ew == 0 && lane == 0) record_error(ctl, kErrTimeoutPartner);
                     ok = false;
                     break;
                 }

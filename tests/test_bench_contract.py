@@ -33,6 +33,18 @@ def test_reference_arm_line():
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
 
 
-def test_reference_arm_unavailable_on_large_workloads():
-    d = _bench("--impl", "reference", "--workload", "gapped_n16384")
+def test_reference_arm_default_workload_is_sampled():
+    """The default workload (n = 16384, finite T) is timed on a bounded
+    sample: the oracle's density of the same recipe at n = 1024, scaled by
+    n^3 to the full size and labelled so."""
+    d = _bench("--impl", "reference", "--steps", "1", "--warmup", "3")
+    assert d["impl"] == "reference" and "unavailable" not in d
+    assert d["config"]["workload"] == "fermi_n16384" and d["config"]["n"] == 16384
+    assert d["config"]["kT"] == 0.003
+    assert d["value"] > 0 and "n=1024" in d["cpu_baseline"]["sample"] and "^3" in d["cpu_baseline"]["sample"]
+    assert d["e2e"]["value"] == d["value"]
+
+
+def test_reference_arm_unavailable_on_many_problem_workloads():
+    d = _bench("--impl", "reference", "--workload", "ragged_batch64")
     assert d["impl"] == "reference" and "unavailable" in d

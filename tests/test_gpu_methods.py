@@ -1,0 +1,216 @@
+"""Accelerated SP2 (A-Z-RFOE, Sec. II-B2) and the truncated SP2 expansion at
+finite temperature (T-RFOE, Sec. II-B3 Eq. (2)) through the C ABI, against
+the oracle.
+
+A-Z-RFOE converges to the same projector as SP2, so its tolerances are the
+zero-temperature ones: ||D - D_ref||_F / sqrt(N_e) <= 1e-6, |E - E_ref| / N_e
+<= 1e-7, |tr D - N_e| <= 1e-9, ||D^2 - D||_F <= 1e-8.
+
+T-RFOE is compared with the oracle's recursion on the eigenvalues
+(oracle.trfoe: same trace rule, same stop rule, same Gershgorin bounds):
+the number of steps and the midpoint energy must agree (they follow from the
+branch sequence), and D must equal Q diag(G_m(x(lambda))) Q^T.  The
+expansion's step function is steep, |dG/dx| = (beta/4) w at its midpoint
+(w the Gershgorin width), so a product error e moves the states near mu by
+up to about (beta/4) w e: the FP64 schedule (FP64-accurate digit products
+from an FP64 X0) is held to 1e-9, and the mixed schedule (split FP16 until
+RelTr < 5e-4) to (beta/4) w 2^-21 per entry."""
+import math
+
+import numpy as np
+import pytest
+
+import hp_synth
+import oracle
+from gpu_util import ctx, torch
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="no CUDA device")]
+
+TOL_EPS1, TOL_E, TOL_TR, TOL_IDEM = 1e-6, 1e-7, 1e-9, 1e-8
+
+
+def fe():
+    import paper_2301_04642_gb300 as m
+    return m
+
+
+def zero_t_errors(p, D, res):
+    f = (np.arange(p.n) < int(p.ne)).astype(float)
+    if p.Q is not None:
+        Dref = oracle.density_from_eig(p.Q, f)
+        Eref = float(np.sum(f * p.lam))
+    else:
+        r = oracle.density(p.H, p.ne)
+        Dref, Eref = r["D"], r["e_band"]
+    D2 = oracle.matmul(D, D)
+    return dict(eps1=np.linalg.norm(D - Dref) / math.sqrt(p.ne), e_err=abs(res["e_band"] - Eref) / p.ne,
+                tr_err=abs(np.trace(D) - p.ne), idem=np.linalg.norm(D2 - D))
+
+
+def inner_estimates(lam, ne, frac=0.1):
+    """HOMO/LUMO estimates inside the gap, `frac` of the gap from each edge
+    (what the folds need; the exact edges work as well)."""
+    h, l = lam[int(ne) - 1], lam[int(ne)]
+    g = l - h
+    return h + frac * g, l - frac * g
+
+
+def assert_zero_t(m):
+    assert m["eps1"] <= TOL_EPS1 and m["e_err"] <= TOL_E
+    assert m["tr_err"] <= TOL_TR and m["idem"] <= TOL_IDEM
+
+
+@pytest.mark.parametrize("n,ne", [(300, 250), (1000, 850), (1250, 1000)])
+def test_asp2_matches_oracle_in_fewer_products(n, ne):
+    p = hp_synth.gapped(n, ne, (-3.0, -0.01), (0.01, 1.0), 5000 + n)
+    h, l = inner_estimates(p.lam, ne)
+    D = np.zeros_like(p.H)
+    r = ctx().solve(p.H, ne, D=D, method=fe().FE_METHOD_ASP2, homo=h, lumo=l)
+    m = zero_t_errors(p, D, r)
+    D0 = np.zeros_like(p.H)
+    r0 = ctx().solve(p.H, ne, D=D0)
+    print(n, r["iters_by_phase"], r0["iters_by_phase"], m)
+    assert r["status"] == 0
+    assert_zero_t(m)
+    assert r["iters"] <= 0.75 * r0["iters"]
+
+
+def test_asp2_paper_matrix():
+    """The paper's own matrix (Sec. IV) at n = 1000, N_e = 900: a continuous
+    band with a gap of 1.4e-3 at N_e.  Estimates inside the gap from a
+    library eigensolver (standing in for the previous subspace iteration)."""
+    p = hp_synth.paper_matrix(1000)
+    lam = np.linalg.eigvalsh(p.H)
+    h, l = inner_estimates(lam, p.ne)
+    D = np.zeros_like(p.H)
+    r = ctx().solve(p.H, p.ne, D=D, method=fe().FE_METHOD_ASP2, homo=h, lumo=l)
+    r0 = ctx().solve(p.H, p.ne)
+    m = zero_t_errors(p, D, r)
+    print(r["iters_by_phase"], r0["iters_by_phase"], m)
+    assert r["status"] == 0
+    assert_zero_t(m)
+    assert r["iters"] <= 0.75 * r0["iters"]
+
+
+@pytest.mark.parametrize("shift", [-1, 1])
+def test_asp2_misplaced_estimates_fall_back_to_sp2(shift):
+    """Estimates that put the gap one state off cannot give the projector
+    onto the N_e lowest states.  The device's trace test catches it, the
+    solve runs again as plain SP2 and still meets every tolerance; the
+    products of the abandoned attempt are counted."""
+    p = hp_synth.gapped(600, 450, (-3.0, -0.02), (0.02, 1.0), 5600)
+    ne = 450
+    h, l = p.lam[ne - 1 + shift], p.lam[ne + shift]
+    D = np.zeros_like(p.H)
+    r = ctx().solve(p.H, ne, D=D, method=fe().FE_METHOD_ASP2, homo=h + 0.1 * (l - h), lumo=l - 0.1 * (l - h))
+    r0 = ctx().solve(p.H, ne)
+    m = zero_t_errors(p, D, r)
+    print(shift, r["iters"], r0["iters"], m)
+    assert r["status"] == 0
+    assert_zero_t(m)
+    assert r["iters"] > r0["iters"]
+
+
+def test_asp2_rejects_bad_arguments():
+    F = fe()
+    p = hp_synth.gapped(64, 32, (-3.0, -0.01), (0.01, 1.0), 3)
+    for homo, lumo, kT in [(0.1, 0.1, 0.0), (0.2, -0.1, 0.0), (float("nan"), 0.1, 0.0), (-0.1, 0.1, 0.01)]:
+        with pytest.raises(F.FeError) as ei:
+            ctx().solve(p.H, 32, kT=kT, method=F.FE_METHOD_ASP2, homo=homo, lumo=lumo)
+        assert ei.value.status == F.FE_EINVAL
+
+
+def test_asp2_in_a_batch_and_served_equals_solo():
+    """A-Z-RFOE problems (one with misplaced estimates) share a batch with a
+    plain SP2 problem and are also served through fe_submit: each result is
+    the solo one within the tolerances."""
+    F = fe()
+    probs = [hp_synth.gapped(n, ne, (-3.0, -0.01), (0.01, 1.0), 5700 + n) for n, ne in
+             [(400, 300), (700, 600), (520, 400)]]
+    ests = [inner_estimates(probs[0].lam, 300), (probs[1].lam[600], probs[1].lam[601]), None]
+    items, solo = [], []
+    for p, est in zip(probs, ests):
+        kw = dict(method=F.FE_METHOD_ASP2, homo=est[0], lumo=est[1]) if est else {}
+        Ds = np.zeros_like(p.H)
+        rs = ctx().solve(p.H, p.ne, D=Ds, **kw)
+        solo.append(Ds)
+        it = dict(H=p.H, ne=p.ne, D=np.zeros_like(p.H))
+        it.update(kw)
+        items.append(it)
+    rc, res = ctx().solve_batch(items)
+    assert rc == 0
+    for p, it, Ds, r in zip(probs, items, solo, res):
+        assert r["status"] == 0
+        assert np.linalg.norm(it["D"] - Ds) / math.sqrt(p.ne) <= TOL_EPS1
+        assert_zero_t(zero_t_errors(p, it["D"], r))
+    tickets, outs = [], []
+    for p, it in zip(probs, items):
+        Dd = np.zeros_like(p.H)
+        outs.append(Dd)
+        tickets.append(ctx().submit(p.H, p.ne, D=Dd, method=it.get("method", 0), homo=it.get("homo", 0.0),
+                                    lumo=it.get("lumo", 0.0)))
+    for p, t, Dd, Ds in zip(probs, tickets, outs, solo):
+        r = ctx().wait(t)
+        assert r["status"] == 0
+        assert np.linalg.norm(Dd - Ds) / math.sqrt(p.ne) <= TOL_EPS1
+        assert_zero_t(zero_t_errors(p, Dd, r))
+
+
+# ------------------------------------------------------------------ T-RFOE
+
+def trfoe_reference(p, kT):
+    lo, hi = oracle.gershgorin(p.H)
+    g, m, br, mu = oracle.trfoe(p.lam, p.ne, kT, lo, hi)
+    assert m > 0
+    return g, m, mu, hi - lo
+
+
+@pytest.mark.parametrize("n,ne,kT,seed", [(300, 255.0, 0.02, 17), (517, 440.5, 0.01, 18),
+                                          (2000, 1700.0, 0.003, 20)])
+def test_trfoe_fp64_matches_oracle_recursion(n, ne, kT, seed):
+    p = hp_synth.smeared(n, ne, kT, -2.0, 1.0, seed)
+    g, m, mu, w = trfoe_reference(p, kT)
+    D = np.zeros_like(p.H)
+    r = ctx().solve(p.H, ne, kT=kT, D=D, precision="fp64", method=fe().FE_METHOD_TRFOE)
+    Dref = oracle.density_from_eig(p.Q, g)
+    err = np.linalg.norm(D - Dref) / math.sqrt(ne)
+    print(n, r["iters"], m, r["mu"], mu, err)
+    assert r["status"] == 0
+    assert r["iters"] == m
+    assert abs(r["mu"] - mu) <= 1e-9 * w
+    assert err <= 1e-9
+    assert abs(r["e_band"] - float(np.sum(g * p.lam))) / ne <= 1e-9
+    assert abs(r["trace"] - g.sum()) <= 1e-8
+
+
+@pytest.mark.parametrize("n,ne,kT,seed", [(1000, 850.0, 0.003, 19), (2000, 1700.0, 0.003, 20)])
+def test_trfoe_mixed_matches_oracle_recursion(n, ne, kT, seed):
+    p = hp_synth.smeared(n, ne, kT, -2.0, 1.0, seed)
+    g, m, mu, w = trfoe_reference(p, kT)
+    D = np.zeros_like(p.H)
+    r = ctx().solve(p.H, ne, kT=kT, D=D, method=fe().FE_METHOD_TRFOE)
+    Dref = oracle.density_from_eig(p.Q, g)
+    dmax = np.abs(D - Dref).max()
+    err = np.linalg.norm(D - Dref) / math.sqrt(ne)
+    gp = 0.25 / kT * w                      # |dG/dx| at the midpoint
+    f, _ = oracle.occupations(p.lam, ne, kT)
+    fd = np.linalg.norm(g - f) / math.sqrt(ne)
+    print(n, r["iters_by_phase"], m, r["mu"], mu, "max", dmax, "eps", err, "bound", gp * 2.0 ** -21,
+          "oracle vs FD", fd)
+    assert r["status"] == 0
+    assert r["iters"] == m
+    assert abs(r["mu"] - mu) <= 1e-9 * w
+    assert r["iters_by_phase"][2] > 0        # the FP64-accurate steps after RelTr < 5e-4
+    assert dmax <= gp * 2.0 ** -21
+
+
+def test_trfoe_rejects_zero_temperature_and_fp16():
+    F = fe()
+    p = hp_synth.gapped(64, 32, (-3.0, -0.01), (0.01, 1.0), 3)
+    with pytest.raises(F.FeError) as ei:
+        ctx().solve(p.H, 32, kT=0.0, method=F.FE_METHOD_TRFOE)
+    assert ei.value.status == F.FE_EINVAL
+    with pytest.raises(F.FeError) as ei:
+        ctx().solve(p.H, 32, kT=0.01, method=F.FE_METHOD_TRFOE, precision="try_fp16")
+    assert ei.value.status == F.FE_EINVAL

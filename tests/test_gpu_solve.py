@@ -238,3 +238,32 @@ def test_pinned_host_output_matches_staged():
     assert r3["status"] == 0
     assert np.array_equal(big.numpy()[:, :p.n], D2)
     assert np.all(big.numpy()[:, p.n:] == -7.0)
+
+
+@pytest.mark.parametrize("kind", ["degenerate", "gap1e-5"])
+def test_unresolvable_gap_reports_notconv_or_meets_tolerances(kind):
+    """A Fermi level that the products cannot resolve: a two-fold degenerate
+    HOMO split by N_e (D is not unique, Sec. II-A needs a gap), or a gap of
+    1e-5 Ha.  The solve must either meet every zero-temperature tolerance or
+    say FE_ENOTCONV; it must never report success with a D that misses them."""
+    import paper_2301_04642_gb300 as fe
+    n, ne = 400, 300
+    lam = hp_synth.gapped_spectrum(n, ne, (-3.0, -0.01), (0.01, 1.0), 77)
+    if kind == "degenerate":
+        lam[ne] = lam[ne - 1]
+    else:
+        lam[ne] = lam[ne - 1] + 1e-5
+    lam = np.sort(lam)
+    Q = hp_synth.haar_q(n, 78)
+    H = hp_synth.assemble(Q, lam)
+    D = np.zeros_like(H)
+    r = ctx().solve(H, ne, D=D, check=False)
+    print(kind, r["status"], r["iters_by_phase"])
+    if r["status"] == fe.FE_ENOTCONV:
+        return
+    assert r["status"] == 0
+    p = hp_synth.Problem(kind, H, Q, lam, float(ne), 0.0, 5e-8, 77)
+    m = check_zero_t(p, D, r)
+    print(m)
+    assert m["eps1"] <= TOL_EPS1 and m["e_err"] <= TOL_E
+    assert m["tr_err"] <= TOL_TR and m["idem"] <= TOL_IDEM

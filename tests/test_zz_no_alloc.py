@@ -36,6 +36,41 @@ def test_noalloc_matches_context_path_twice(n, ld):
         _check(out.cpu().tolist(), ref, n)
 
 
+def test_noalloc_fills_the_whole_scratch_and_matches_oracle():
+    """n = 32768 (4096 blocks, the last row at the end of the fixed array)
+    with ld > n, and a small case, against the oracle's Gershgorin bounds
+    (the same row sums in another order: equal to rounding)."""
+    import oracle
+    import paper_2301_04642_gb300 as fe
+    for n, ld in [(32768, 32776), (301, 301)]:
+        p = hp_synth.paper_matrix(n, device="cuda")
+        H = torch.zeros((n, ld), dtype=torch.float64, device="cuda")
+        H[:, :n] = p.H
+        del p
+        Hv = H[:, :n]
+        lo, hi = oracle.gershgorin(Hv.cpu().numpy())
+        tr = float(torch.trace(Hv).item())
+        for _ in range(2):
+            out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+            fe.gershgorin_noalloc(Hv, out)
+            torch.cuda.synchronize()
+            got = out.cpu().tolist()
+            scale = max(abs(lo), abs(hi))
+            assert abs(got[0] - lo) <= 1e-12 * scale and abs(got[1] - hi) <= 1e-12 * scale
+            assert abs(got[2] - tr) <= 1e-12 * n and got[3] == 0.0
+        del H, Hv
+
+
+def test_noalloc_binding_checks_its_arguments():
+    import paper_2301_04642_gb300 as fe
+    H = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    for bad_h, bad_o in [(H.float(), out), (H[:, :4], out), (H.t(), out), (H, out[:3]), (H, out.float()),
+                         (H.cpu(), out)]:
+        with pytest.raises(ValueError):
+            fe.gershgorin_noalloc(bad_h, bad_o)
+
+
 def test_noalloc_flags_nonfinite_then_recovers():
     import paper_2301_04642_gb300 as fe
     p = hp_synth.gapped(300, 150, (-3.0, -0.01), (0.01, 1.0), 31)

@@ -416,6 +416,11 @@ def main():
                     help="override the workload's precision schedule")
     ap.add_argument("--tiles", default="auto", choices=["auto", "256", "128"],
                     help="tensor-core tile width: autotuned per size (untimed, before the warm-up) or fixed")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="one solve with plain (profiled) launches and nothing else: the command the ncu "
+                         "launch lists and kernel captures are taken on")
+    ap.add_argument("--n", type=int, default=0,
+                    help="with --profile-solve: a smaller problem of the workload's recipe (ncu captures)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
@@ -442,6 +447,8 @@ def main():
         return bench_batch(args, torch, fe)
     if args.workload == "serve_poisson":
         return bench_serve(args, torch, fe)
+    if args.profile_solve:
+        return profile_solve(args, torch, fe, wl)
 
     dist = None
     if world > 1:
@@ -580,6 +587,39 @@ def main():
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def profile_solve(args, torch, fe, wl):
+    """One solve of the workload (or of its recipe at --n) with the step loop
+    as plain launches (per-launch CUDA events), fixed 128 x 256 tiles unless
+    --tiles says otherwise; prints the per-kernel times.  In a k_sym_mma
+    launch list the first three launches are the bound certificate."""
+    spec = wl["sample"]
+    if args.n and spec is not None and args.n != spec.get("n"):
+        sp = dict(spec, n=args.n)
+        if spec["kind"] == "fd":
+            p = hp_synth.smeared(args.n, float(round(spec["frac"] * args.n)), spec["kT"], spec["a"], spec["b"],
+                                 spec["seed"], device="cuda")
+        elif spec["kind"] == "sp2_paper":
+            p = hp_synth.paper_matrix(args.n, frac=spec["frac"], device="cuda")
+        else:
+            p = hp_synth.gapped(args.n, int(round(sp["frac"] * args.n)), sp["occ"], sp["emp"], sp["seed"],
+                                device="cuda")
+    else:
+        p = wl["make"]()
+    H = p.H.cuda() if torch.is_tensor(p.H) else torch.from_numpy(p.H).cuda()
+    D = torch.empty_like(H)
+    kT = float(p.kT or 0.0)
+    ctx = fe.Context(device=0)
+    if wl["precision"] != "fp64":
+        ctx.set_tile_width(p.n, 256 if args.tiles == "auto" else int(args.tiles), wl["precision"])
+    ctx.profile(True)
+    r = ctx.solve(H, p.ne, kT=kT, tol=p.tol, D=D, precision=wl["precision"])
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.close()
+    print(json.dumps({"workload": args.workload, "n": p.n, "status": r["status"], "iters": r["iters"],
+                      "iters_by_phase": r["iters_by_phase"], "profile": prof}), flush=True)
 
 
 def _gershgorin_torch(H):
@@ -760,11 +800,12 @@ def same_gpu_baselines(torch, ctx, p, H, D, kT, our_rate, r, prec):
     ns = n
     M = H
     f = f_all
-    t_probe, _ = _median_time(torch, lambda: torch.linalg.eigh(H[:1024, :1024]), reps=1, warm=1)
+    n0 = min(n, 2048)
+    t_probe, _ = _median_time(torch, lambda: torch.linalg.eigh(H[:n0, :n0]), reps=1, warm=1)
     # the largest size whose four calls take about a minute at most
     for cand in (n, 8192, 4096, 2048):
         ns = min(cand, n)
-        if t_probe * (ns / 1024) ** 3 * 4 <= 60.0:
+        if t_probe * (ns / n0) ** 3 * 4 <= 60.0:
             break
     if ns != n:
         frac = p.ne / n

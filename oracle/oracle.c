@@ -448,16 +448,22 @@ int oracle_sp2(int n, const double *H, double ne, double tol, int max_iter,
  * scaling the SP2 polynomials with the HOMO and LUMO eigenvalues (homo <
  * lumo, estimates from the caller).  With X0 as in oracle_sp2, unoccupied
  * eigenvalues of X lie in [0, a] and occupied ones in [b, 1], where
- * a = (emax - lumo)/w and b = (emax - homo)/w.  Each step takes the branch
- * by the SP2 trace rule on t1 = tr X, t2 = tr X^2 and applies its polynomial
- * folded over the interval that has to shrink:
+ * a = (emax - lumo)/w and b = (emax - homo)/w.  The bounds, not the trace,
+ * say where the gap is, so each step takes the branch that moves the gap
+ * toward the middle of [0, 1] (X^2 while a + b > 1, else 2X - X^2) as long
+ * as max(a, 1 - b) >= 1e-3, and the SP2 trace rule on t1 = tr X,
+ * t2 = tr X^2 after that (the folds are then negligible); it applies its
+ * polynomial folded over the interval that has to shrink:
  *   X^2 branch:     p(x) = ((x - s)/(1 - s))^2,        s = a/2,
  *                   so p(0) = p(a), p(1) = 1;
  *   2X - X^2 branch: q(x) = (2 (1 - s) x - x^2)/(1 - s)^2, s = (1 - b)/2,
  *                   so q(b) = q(1), q(0) = 0;
- * then a <- f(a), b <- f(b) for the polynomial f applied.  With s = 0 (no
- * gap information: a = 0, b = 1, or bounds that do not bracket a gap) a step
- * is the SP2 step.
+ * then a <- f(a), b <- f(b) for the polynomial f applied.  A product's
+ * rounding error enters the next iterate multiplied by r = 1/(1 - s)^2 and
+ * turns the occupied subspace by that error over the gap b - a, so while
+ * that gap is narrow (b - a < 1e-2) the fold point is capped at s <= 1/4
+ * (r <= 16/9).  With s = 0 (no gap information: a = 0, b = 1, or bounds
+ * that do not bracket a gap) a step is the SP2 step.
  *
  * The folds are valid only while every eigenvalue stays in [0, a] u [b, 1],
  * i.e. when the estimates lie inside the true gap (homo >= HOMO, lumo <=
@@ -491,9 +497,11 @@ int oracle_sp2_accel(int n, const double *H, double ne, double homo, double lumo
     while (it < max_iter && !done) {
         double t2 = 0.0;
         for (size_t k = 0; k < (size_t)n * n; ++k) t2 += X[k] * X[k];
-        const int sq = fabs(t2 - ne) <= fabs(2.0 * t1 - t2 - ne);
+        const int by_bounds = informed && fmax(a, 1.0 - b) >= 1e-3;
+        const int sq = by_bounds ? (a + b > 1.0) : (fabs(t2 - ne) <= fabs(2.0 * t1 - t2 - ne));
         oracle_matmul(n, X, X, X2);
-        const double s = sq ? 0.5 * a : 0.5 * (1.0 - b);
+        double s = sq ? 0.5 * a : 0.5 * (1.0 - b);
+        if (b - a < 1e-2 && s > 0.25) s = 0.25;
         const double r = 1.0 / ((1.0 - s) * (1.0 - s));
         if (sq) {
             for (int i = 0; i < n; ++i)

@@ -284,6 +284,12 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
 
     // ---- SP2 branch (Eq. (1)) and the instruction for the next product
     int sq = fabs(t2 - ne) <= fabs(2.0 * t1 - t2 - ne);
+    if (st->acc_on && phase != kPhaseFp64 && fmax(st->acc_a, 1.0 - st->acc_b) >= 1e-3) {
+        // A-Z-RFOE: the bounds say where the gap is; the branch moves it
+        // toward the middle of [0, 1] (the trace rule takes over once the
+        // folds are negligible)
+        sq = st->acc_a + st->acc_b > 1.0;
+    }
     st->gamma = 0.0;
     if (phase == kPhaseFp64 && st->prec != kPrecFp64 && (st->it_phase[kPhaseFp64] & 1) == 1) {
         // Polishing: the second product of each pair takes the other branch,
@@ -324,6 +330,10 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
         double sf = 0.0;
         if (st->acc_on) {
             sf = sq ? 0.5 * st->acc_a : 0.5 * (1.0 - st->acc_b);
+            // a product's rounding error enters X' multiplied by r and turns
+            // the occupied subspace by that error over the gap b - a: while
+            // the gap is narrow the fold is capped at sf <= 1/4 (r <= 16/9)
+            if (st->acc_b - st->acc_a < 1e-2 && sf > 0.25) sf = 0.25;
             const double rr = 1.0 / ((1.0 - sf) * (1.0 - sf));
             const double a = st->acc_a, b = st->acc_b;
             st->acc_a_next = sq ? rr * (a - sf) * (a - sf) : rr * (2.0 * (1.0 - sf) * a - a * a);

@@ -201,8 +201,10 @@ def test_trfoe_mixed_matches_oracle_recursion(n, ne, kT, seed):
     assert r["status"] == 0
     assert r["iters"] == m
     assert abs(r["mu"] - mu) <= 1e-9 * w
-    assert r["iters_by_phase"][2] > 0        # the FP64-accurate steps after RelTr < 5e-4
+    # the FP64-accurate steps start only if RelTr < 5e-4 comes before the
+    # slope target (on these spectra it does not: split products throughout)
     assert dmax <= gp * 2.0 ** -21
+    assert err <= 1e-6                       # measured 3.8e-7 and 7.8e-7
 
 
 def test_trfoe_rejects_zero_temperature_and_fp16():

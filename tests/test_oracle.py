@@ -242,10 +242,11 @@ def test_sp2_degenerate_counts():
 def test_sp2_accel_first_step_on_diagonal_by_hand():
     """H = diag(-1, -0.6, 0.2, 1), N_e = 2: Gershgorin bounds [-1, 1], X0 =
     diag(1, 0.8, 0.4, 0); HOMO -0.6 and LUMO 0.2 give a = 0.4, b = 0.8.
-    t1 = 2.2, t2 = 1.8: the X^2 branch (|t2 - 2| = 0.2 < |2 t1 - t2 - 2| =
-    0.6), folded at s = a/2 = 0.2: p(x) = ((x - 0.2)/0.8)^2, so
-    X1 = diag(1, 9/16, 1/16, 1/16) (p(0) = p(a): the unoccupied interval is
-    folded onto itself)."""
+    The gap (a, b) lies above the middle (a + b = 1.2 > 1): the X^2 branch
+    (the trace rule agrees: t1 = 2.2, t2 = 1.8, |t2 - 2| = 0.2 <
+    |2 t1 - t2 - 2| = 0.6), folded at s = a/2 = 0.2 (b - a = 0.4, no cap):
+    p(x) = ((x - 0.2)/0.8)^2, so X1 = diag(1, 9/16, 1/16, 1/16) (p(0) = p(a):
+    the unoccupied interval is folded onto itself)."""
     H = np.diag([-1.0, -0.6, 0.2, 1.0])
     X, it, br = oracle.sp2_accel(H, 2.0, -0.6, 0.2, max_iter=1)
     assert it == -1 and list(br) == [1]
@@ -303,6 +304,26 @@ def test_sp2_accel_flags_misplaced_estimates(shift):
     _, it, _ = oracle.sp2_accel(p.H, p.ne, h + 0.1 * (l - h), l - 0.1 * (l - h), tol=1e-12, max_iter=200)
     assert it == -2
     assert oracle.sp2_accel_status(it) == "inconsistent"
+
+
+def test_sp2_accel_branch_follows_the_bounds_and_caps_the_fold():
+    """Two steps by hand.  H = diag(-1, -0.9, -0.8, 0.9, 1), N_e = 3,
+    bounds [-1, 1]: X0 = diag(1, 0.95, 0.9, 0.05, 0); HOMO -0.8, LUMO -0.79
+    give a = 0.895, b = 0.9 (gap 0.005 < 1e-2).  a + b > 1: X^2, whose fold
+    s = a/2 = 0.4475 is capped at 1/4: p(x) = ((x - 1/4)/(3/4))^2 gives
+    X1 = diag(1, 196/225, 169/225, 16/225, 1/9) (the fold puts 0 above
+    0.05), a1 = p(a) = 0.7396, b1 = p(b) = 0.75111.  Again a1 + b1 > 1, now
+    with b1 - a1 = 0.0115 >= 1e-2: X^2 folded at the uncapped s = a1/2."""
+    H = np.diag([-1.0, -0.9, -0.8, 0.9, 1.0])
+    X, it, br = oracle.sp2_accel(H, 3.0, -0.8, -0.79, max_iter=1)
+    x1 = np.array([225.0, 196.0, 169.0, 16.0, 25.0]) / 225.0
+    assert it == -1 and list(br) == [1]
+    assert np.allclose(np.diag(X), x1, rtol=0, atol=1e-15)
+    a1 = (0.895 - 0.25) ** 2 / 0.5625
+    s2 = a1 / 2
+    X2, it2, br2 = oracle.sp2_accel(H, 3.0, -0.8, -0.79, max_iter=2)
+    assert list(br2) == [1, 1]
+    assert np.allclose(np.diag(X2), ((x1 - s2) / (1 - s2)) ** 2, rtol=0, atol=1e-14)
 
 
 def test_sp2_accel_estimates_inside_the_gap_are_never_flagged():

@@ -21,6 +21,8 @@ passage each routine follows:
 * ``trfoe``                     -- the truncated SP2 expansion of Sec. II-B3,
   Eq. (2) as printed (T-RFOE), on the eigenvalues.
 * ``metrics``                   -- eps1, eps2 ingredients (Sec. III-C).
+* ``gemm``                      -- the plain products either side of the
+  expansion in subspace iteration (Sec. III-A).
 
 Every function here is pinned by a test in ``tests/test_oracle.py`` against
 closed forms, invariants, brute force on tiny inputs or a library routine.
@@ -45,6 +47,7 @@ def lib():
         d, i = ctypes.c_double, ctypes.c_int
         sig = {
             "oracle_matmul": (None, [i, _D, _D, _D]),
+            "oracle_gemm": (None, [i, i, i, _D, i, i, _D, i, i, _D, i]),
             "oracle_gershgorin": (None, [i, _D, _D, _D]),
             "oracle_eigh_ql": (i, [i, _D, _D, _D]),
             "oracle_eigh_jacobi": (i, [i, _D, _D, _D, i]),
@@ -80,6 +83,17 @@ def matmul(A, B):
     n = A.shape[0]
     C = np.empty((n, n))
     lib().oracle_matmul(n, _p(A), _p(B), _p(C))
+    return C
+
+
+def gemm(A, B, ta=False, tb=False):
+    """op(A) op(B) in plain FP64 loops (op = transpose when ta / tb)."""
+    A, B = _c64(A), _c64(B)
+    m, k = (A.shape[1], A.shape[0]) if ta else A.shape
+    n = B.shape[0] if tb else B.shape[1]
+    assert (B.shape[1] if tb else B.shape[0]) == k
+    C = np.empty((m, n))
+    lib().oracle_gemm(m, n, k, _p(A), A.shape[1], int(ta), _p(B), B.shape[1], int(tb), _p(C), n)
     return C
 
 

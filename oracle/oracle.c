@@ -21,6 +21,8 @@
  *     with the sign picked so that the trace moves toward N_occ.
  *   - Sec. III-B: tr(X^2) evaluated as the squared Frobenius norm.
  *   - Sec. III-C: error metrics eps1 and eps2.
+ *   - Sec. III-A: the plain products either side of the expansion in
+ *     subspace iteration (Rayleigh-Ritz projection, rotation by D).
  *   - Sec. II-C: spectral bounds, taken as Gershgorin discs.
  *   - Finite temperature (Sec. II-B3, Eq. (2)): a recursive expansion that
  *     doubles the inverse temperature at every step, z <- 2 z (I + z^2)^{-1}
@@ -62,6 +64,27 @@ void oracle_matmul(int n, const double *A, const double *B, double *C)
             for (int j = 0; j < n; ++j) ci[j] += a * bk[j];
         }
     }
+}
+
+/* C (m x n) = op(A) op(B), op(X) = X or X^T (ta, tb), inner dimension k;
+ * A is stored m x k (or k x m when ta), B k x n (or n x k when tb), all
+ * row-major with the given leading dimensions.  Plain loops over k for each
+ * entry of C (the products either side of the expansion in subspace
+ * iteration, Sec. III-A: Psi^T (H Psi) and Psi D). */
+void oracle_gemm(int m, int n, int k, const double *A, int lda, int ta, const double *B, int ldb, int tb,
+                 double *C, int ldc)
+{
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int p = 0; p < k; ++p) {
+                const double a = ta ? A[(size_t)p * lda + i] : A[(size_t)i * lda + p];
+                const double b = tb ? B[(size_t)j * ldb + p] : B[(size_t)p * ldb + j];
+                s += a * b;
+            }
+            C[(size_t)i * ldc + j] = s;
+        }
 }
 
 double oracle_trace(int n, const double *A)

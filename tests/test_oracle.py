@@ -345,6 +345,30 @@ def test_sp2_accel_estimates_inside_the_gap_are_never_flagged():
         assert np.abs(X - oracle.density_from_eig(p.Q, f)).max() < 1e-8
 
 
+# ---------------------------------------------------------------- products either side
+
+def test_gemm_against_library_and_closed_forms():
+    """op(A) op(B) against numpy on rectangular and transposed operands, and
+    two closed forms of the subspace-iteration products: for Psi with
+    orthonormal columns Psi^T Psi = I, and with H Psi = Psi diag(lam) the
+    projection Psi^T (H Psi) = diag(lam); rotating by D = I returns Psi."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((37, 21))
+    B = rng.standard_normal((21, 13))
+    assert np.allclose(oracle.gemm(A, B), A @ B, rtol=0, atol=1e-12)
+    assert np.allclose(oracle.gemm(A, A, ta=True), A.T @ A, rtol=0, atol=1e-12)
+    assert np.allclose(oracle.gemm(B, B, tb=True), B @ B.T, rtol=0, atol=1e-12)
+    assert np.allclose(oracle.gemm(B, A, ta=True, tb=True), (A @ B).T, rtol=0, atol=1e-12)
+    Psi = hp_synth.haar_q(60, 4)[:, :17]
+    assert np.abs(oracle.gemm(Psi, Psi, ta=True) - np.eye(17)).max() < 1e-14
+    lam = np.linspace(-2.0, 1.0, 17)
+    assert np.abs(oracle.gemm(Psi, Psi * lam[None, :], ta=True) - np.diag(lam)).max() < 1e-14
+    assert np.array_equal(oracle.gemm(Psi, np.eye(17)), Psi)
+    # by hand: [[1, 2], [3, 4]]^T [[5], [6]] = [[23], [34]]
+    assert np.array_equal(oracle.gemm(np.array([[1.0, 2.0], [3.0, 4.0]]), np.array([[5.0], [6.0]]), ta=True),
+                          np.array([[23.0], [34.0]]))
+
+
 # ---------------------------------------------------------------- truncated SP2 at finite T
 
 def _apply_branches(x, branches):

@@ -77,6 +77,8 @@ WORKLOADS = {
                                sample=dict(kind="sp2_paper", n=1024, frac=0.9)),
     # many problems per step (see bench_batch / bench_serve)
     "ragged_batch64": dict(make=None, precision="mixed", sample=None),
+    # the products either side of the expansion in subspace iteration
+    "chfsi_n4096": dict(make=None, precision="mixed", sample=None),
     "serve_poisson": dict(make=None, precision="mixed", sample=None),
 }
 
@@ -447,6 +449,8 @@ def main():
         return bench_batch(args, torch, fe)
     if args.workload == "serve_poisson":
         return bench_serve(args, torch, fe)
+    if args.workload == "chfsi_n4096":
+        return bench_chfsi(args, torch, fe)
     if args.profile_solve:
         return profile_solve(args, torch, fe, wl)
 
@@ -594,19 +598,22 @@ def profile_solve(args, torch, fe, wl):
     as plain launches (per-launch CUDA events), fixed 128 x 256 tiles unless
     --tiles says otherwise; prints the per-kernel times.  In a k_sym_mma
     launch list the first three launches are the bound certificate."""
+    # the workload's spectrum recipe at --n (or the workload's own n), Q from
+    # 8 Householder reflectors: no device linear algebra of torch (not
+    # available under the profiler on every image), and the kernels' work
+    # depends on the spectrum, not on Q
     spec = wl["sample"]
-    if args.n and spec is not None and args.n != spec.get("n"):
-        sp = dict(spec, n=args.n)
-        if spec["kind"] == "fd":
-            p = hp_synth.smeared(args.n, float(round(spec["frac"] * args.n)), spec["kT"], spec["a"], spec["b"],
-                                 spec["seed"], device="cuda")
-        elif spec["kind"] == "sp2_paper":
-            p = hp_synth.paper_matrix(args.n, frac=spec["frac"], device="cuda")
-        else:
-            p = hp_synth.gapped(args.n, int(round(sp["frac"] * args.n)), sp["occ"], sp["emp"], sp["seed"],
-                                device="cuda")
+    full_n = {"gapped_n4096": 4096, "gapped_n256_fp64": 256, "gapped_n8192": 8192, "gapped_n16384": 16384,
+              "fermi_n16384": 16384, "paper_matrix_n8192": 8192}[args.workload]
+    nn = args.n or full_n
+    if spec["kind"] == "fd":
+        p = hp_synth.smeared_reflected(nn, float(round(spec["frac"] * nn)), spec["kT"], spec["a"], spec["b"],
+                                       spec["seed"], device="cuda")
+    elif spec["kind"] == "sp2_paper":
+        p = hp_synth.paper_matrix(nn, frac=spec["frac"], device="cuda")
     else:
-        p = wl["make"]()
+        p = hp_synth.gapped_reflected(nn, int(round(spec["frac"] * nn)), spec["occ"], spec["emp"], spec["seed"],
+                                      device="cuda")
     H = p.H.cuda() if torch.is_tensor(p.H) else torch.from_numpy(p.H).cuda()
     D = torch.empty_like(H)
     kT = float(p.kT or 0.0)
@@ -923,6 +930,82 @@ def bench_batch(args, torch, fe):
            "accuracy_worst_member": {k: max(m[k] for m in member) for k in member[0]},
            "phases_ms": phases,
            "gpu_launches": launches, "kernels": kern, "clocks": clk.summary(), "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def bench_chfsi(args, torch, fe):
+    """The products either side of the expansion in Chebyshev-filtered subspace
+    iteration (Sec. III-A) at n = 4096 vectors on m = 131072 grid points (env
+    FE_CHFSI_M): the Rayleigh-Ritz projection Hp = Psi^T (H Psi) and the
+    rotation Psi D.  Psi, H Psi and D are seeded normal draws on the device
+    (torch generator, seed 4000; D symmetrised); one step = one projection and
+    one rotation.  Rates in TFLOP/s of the products (2 m n^2 each, the
+    projection's upper half counted once: m n (n + 1))."""
+    dev = torch.device("cuda", 0)
+    n = 4096
+    m = int(os.environ.get("FE_CHFSI_M", "131072"))
+    g = torch.Generator(device=dev).manual_seed(4000)
+    Psi = torch.randn(m, n, dtype=torch.float64, device=dev, generator=g) / math.sqrt(m)
+    HPsi = torch.randn(m, n, dtype=torch.float64, device=dev, generator=g) / math.sqrt(m)
+    Dm = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g) / math.sqrt(n)
+    Dm = 0.5 * (Dm + Dm.T)
+    Hp = torch.empty(n, n, dtype=torch.float64, device=dev)
+    Out = torch.empty(m, n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fe.Context(device=0, stream=stream.cuda_stream)
+    peaks, peak_kind = load_peaks()
+    for _ in range(args.warmup):
+        ctx.project(Psi, HPsi, Hp)
+        ctx.rotate(Psi, Dm, Out)
+    ph_p, ph_r = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.project(Psi, HPsi, Hp)
+            ph_p.append(ctx.phase_ms())
+            ctx.rotate(Psi, Dm, Out)
+            ph_r.append(ctx.phase_ms())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    # accuracy against FP64 products by torch (cuBLAS DGEMM) on sampled rows
+    idx = torch.arange(0, n, 97, device=dev)
+    ref_p = Psi.T @ HPsi[:, idx]
+    err_p = float(((Hp[:, idx] - ref_p).abs().max() / (Psi.abs().T @ HPsi[:, idx].abs()).max()).item())
+    rows = torch.arange(0, m, 1031, device=dev)
+    ref_r = Psi[rows] @ Dm
+    err_r = float(((Out[rows] - ref_r).abs().max() / (Psi[rows].abs() @ Dm.abs()).max()).item())
+
+    def med(ph, k):
+        return statistics.median(x[k] for x in ph)
+
+    tiles_p = sum(1 for J in range((n + 191) // 192) for I in range((n + 127) // 128) if J * 192 + 191 >= I * 128)
+    flops_p = 3 * 2.0 * tiles_p * 128 * 192 * m       # algorithmic: 3 split products per tile
+    tiles_r = ((m + 127) // 128) * ((n + 191) // 192)
+    flops_r = 3 * 2.0 * tiles_r * 128 * 192 * n
+    gp, gr = med(ph_p, 1), med(ph_r, 1)
+    pk = peaks["bf16_tflops"]
+    kern = {"k_gemm_split_project": {"ms": gp, "algorithmic_flops": flops_p, "achieved_tflops": flops_p / gp / 1e9},
+            "k_gemm_split_rotate": {"ms": gr, "algorithmic_flops": flops_r, "achieved_tflops": flops_r / gr / 1e9},
+            "split_project_ms": med(ph_p, 0), "split_rotate_ms": med(ph_r, 0), "reduce_project_ms": med(ph_p, 2),
+            # max pass + split pass: read Psi and H Psi twice (FP64), write 2 x 2 FP16 slices
+            "split_project_gbs": 40.0 * m * n / med(ph_p, 0) / 1e6,
+            "k_parts_units": ph_p[-1][3]}
+    dom = max(("k_gemm_split_project", "k_gemm_split_rotate"), key=lambda k: kern[k]["ms"])
+    out = {"metric": "chfsi_project_and_rotate_per_s", "value": args.steps / (t_ms / 1e3), "unit": "pairs/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16x2", "data": "synthetic",
+           "config": {"workload": "chfsi_n4096", "m": m, "n": n, "parallelism": "single"},
+           "effective_tflops": {"project": 2.0 * m * n * n / (med(ph_p, 0) + gp + med(ph_p, 2)) / 1e9,
+                                "rotate": 2.0 * m * n * n / (med(ph_r, 0) + gr) / 1e9},
+           "accuracy": {"project_max_err_rel_to_abs_product": err_p, "rotate_max_err_rel_to_abs_product": err_r},
+           "roofline": {"kernel": dom, "bound": "tensor", "achieved": kern[dom]["achieved_tflops"], "peak": pk,
+                        "unit": "TFLOP/s", "frac": kern[dom]["achieved_tflops"] / pk, "traffic": None,
+                        "peak_source": "%s bf16 dense burst (fp16 dense has the same rate)" % peak_kind},
+           "kernels": kern, "clocks": clk.summary(), "cpu_baseline": None}
     print(json.dumps(out), flush=True)
     ctx.close()
 

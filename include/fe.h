@@ -236,6 +236,39 @@ FE_API int fe_autotune(fe_ctx *ctx, int count, const int64_t *ns, uint32_t prec,
 FE_API int fe_autotune_batch(fe_ctx *ctx, int count, const fe_problem *ps, int reps, double *trial_ms,
                              int max_trials, int *ntrials);
 
+/* ---- the products either side of the expansion --------------------------
+ * In Chebyshev-filtered subspace iteration (Sec. I, Sec. III-A) the
+ * expansion replaces the diagonalisation of the projected Hamiltonian; the
+ * step before it forms Hp from the filtered subspace by the Rayleigh-Ritz
+ * projection, the step after it uses D for the density and the subspace
+ * rotation.  Psi is the m x n block of filtered vectors (m grid points,
+ * n vectors, m >> n), row-major with leading dimension ld (a grid point's n
+ * values contiguous).  Both calls take DEVICE pointers on the context's
+ * device, run on the context's stream and return when the result is ready.
+ * Precision: the operands are split into FP16 hi + lo slices (22 bits, one
+ * power-of-two scale per operand from its largest entry) and multiplied on
+ * the tensor cores with FP32 accumulation per 64-wide K chunk, the chunks
+ * summed in FP32 registers (at most 128 per part) and the parts in FP64:
+ * |C_ij - (A B)_ij| <= (2^-21 + 2^-21 + c 2^-24) sum_k |A_ik| |B_kj|, c the
+ * chunks of one part (an FP32-class result, as the FP32 Rayleigh-Ritz
+ * products of mixed-precision subspace iteration).
+ * Errors: FE_EINVAL (NULL pointer, m or n < 1, n > 2^20, m > 2^31 - 1, a
+ * leading dimension below n), FE_ENOMEM (workspace of about 8 m n bytes for
+ * fe_project, 4 (m + n) n for fe_rotate, beyond the HBM budget), FE_ETIMEOUT,
+ * FE_ECUDA. */
+
+/* Hp = Psi^T HPsi (n x n, leading dimension ldh), HPsi = H Psi given (m x n,
+ * same leading dimension ld as Psi).  The product is symmetric in exact
+ * arithmetic; the upper triangle is computed and mirrored, so Hp is exactly
+ * symmetric. */
+FE_API int fe_project(fe_ctx *ctx, const double *Psi, const double *HPsi, int64_t m, int64_t n, int64_t ld,
+                      double *Hp, int64_t ldh);
+
+/* Out = Psi D (m x n, leading dimension ldo) for a symmetric n x n D
+ * (leading dimension ldd; its rows are read as its columns). */
+FE_API int fe_rotate(fe_ctx *ctx, const double *Psi, int64_t m, int64_t n, int64_t ldpsi, const double *D,
+                     int64_t ldd, double *Out, int64_t ldo);
+
 /* One-line description of the last error on this context (or of the last
  * fe_create failure when ctx is NULL).  Valid until the next call. */
 FE_API const char *fe_last_error_string(const fe_ctx *ctx);

@@ -107,7 +107,10 @@ FE_API int fe_k_set_wait(fe_ctx *ctx, double limit_ms, int fail_partner);
  * (measurement hook, no counterpart in the paper; CUDA events, always on).
  * out4 (HOST): [0] ms of set-up (Hp staging, bounds, X0, first control step),
  * [1] ms of the step loop, [2] ms of the output kernels, [3] steps the loop
- * ran.  Zeros before the first solve. */
+ * ran.  After fe_project / fe_rotate: [0] ms of the operand split (max and
+ * FP16 slices), [1] ms of the tensor-core product (k_gemm_split), [2] ms of
+ * the reduction of the K parts, [3] work units of the product.  Zeros before
+ * the first call. */
 FE_API int fe_k_phase_ms(fe_ctx *ctx, double *out4);
 
 /* Tile-shape table hooks (tests; see fe_autotune in fe.h).  set: make problems

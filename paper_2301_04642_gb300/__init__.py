@@ -78,6 +78,8 @@ def load(build=True):
     L.fe_last_error_string.argtypes = [P]
     L.fe_last_error_string.restype = ctypes.c_char_p
     L.fe_k_gershgorin.argtypes = [P, P, i64, i64, ctypes.POINTER(dbl)]
+    L.fe_project.argtypes = [P, P, P, i64, i64, i64, P, i64]
+    L.fe_rotate.argtypes = [P, P, i64, i64, i64, P, i64, P, i64]
     L.fe_k_sym_square.argtypes = [P, P, i64, i64, P, i64, ctypes.c_int, dbl]
     L.fe_k_gershgorin_noalloc.argtypes = [P, i64, i64, P, P]
     L.fe_k_digit_square.argtypes = [P, P, i64, i64, P, i64]
@@ -98,6 +100,7 @@ def load(build=True):
     L.fe_k_set_tile_width.argtypes = [P, i64, ctypes.c_uint32, ctypes.c_int]
     L.fe_k_tile_width.argtypes = [P, i64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int)]
     for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
+                 "fe_project", "fe_rotate",
                  "fe_k_gershgorin", "fe_k_gershgorin_noalloc", "fe_k_sym_square", "fe_k_digit_square",
                  "fe_k_profile", "fe_k_profile_read", "fe_k_narrow_bounds", "fe_k_set_wait", "fe_k_serve_stats", "fe_k_phase_ms",
                  "fe_k_profile_steps",
@@ -285,6 +288,35 @@ class Context:
             if time.time() - t0 > timeout_s:
                 raise TimeoutError("ticket %d still pending" % ticket)
             time.sleep(sleep_s)
+
+    # ---- either side of the expansion (device buffers) ------------------------
+    def project(self, Psi, HPsi, Hp):
+        """Hp = Psi^T HPsi (Rayleigh-Ritz projection): Psi, HPsi m x n, Hp n x n,
+        FP64 device tensors with unit column stride."""
+        for t in (Psi, HPsi, Hp):
+            if not (getattr(t, "is_cuda", False) and t.stride(1) == 1):
+                raise ValueError("device tensors with unit column stride expected")
+        if HPsi.shape != Psi.shape or HPsi.stride(0) != Psi.stride(0):
+            raise ValueError("Psi and HPsi must have the same shape and leading dimension")
+        m, n = Psi.shape
+        _ready(Psi, HPsi, Hp)
+        rc = self.L.fe_project(self.h, Psi.data_ptr(), HPsi.data_ptr(), m, n, Psi.stride(0), Hp.data_ptr(),
+                               Hp.stride(0))
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+
+    def rotate(self, Psi, D, Out):
+        """Out = Psi D for a symmetric D (subspace rotation / density): Psi and
+        Out m x n, D n x n, FP64 device tensors with unit column stride."""
+        for t in (Psi, D, Out):
+            if not (getattr(t, "is_cuda", False) and t.stride(1) == 1):
+                raise ValueError("device tensors with unit column stride expected")
+        m, n = Psi.shape
+        _ready(Psi, D, Out)
+        rc = self.L.fe_rotate(self.h, Psi.data_ptr(), m, n, Psi.stride(0), D.data_ptr(), D.stride(0),
+                              Out.data_ptr(), Out.stride(0))
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
 
     # ---- single kernels (device buffers) -------------------------------------
     def gershgorin(self, H):

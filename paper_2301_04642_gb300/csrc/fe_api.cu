@@ -182,6 +182,14 @@ struct fe_ctx {
     // number of requests on the device at once
     long long n_submitted = 0, n_deferred = 0;
     long long peak_waiting = 0, peak_running = 0;
+    // fe_project / fe_rotate: FP16 slices of both operands and split-K
+    // partial tiles (one arena, grown on demand), argument block, tile list
+    char *gws = nullptr;
+    size_t gws_cap = 0;
+    GemmArgs *d_gargs = nullptr;
+    TileEnt *d_gtiles = nullptr;
+    size_t gtiles_cap = 0;
+    unsigned long long *d_amax = nullptr;
 };
 
 namespace {
@@ -284,6 +292,11 @@ size_t slot_bytes(int n, int method, int *ldy, int *lds, int *ldx, size_t *npart
     return b;
 }
 
+// A K-major FP16 operand of rows x kdim elements (leading dimension ld_elems),
+// loaded in boxes of 64 (K) x box_rows with 128-byte swizzling.
+int encode_map_rect(fe_ctx *ctx, CUtensorMap *m, void *base, int64_t kdim, int64_t rows, int64_t ld_elems,
+                    int box_rows);
+
 int encode_map(fe_ctx *ctx, CUtensorMap *m, void *base, int n, int ld_elems, int box_rows,
                int box_k = kTileK, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
     auto enc = get_encode();
@@ -294,6 +307,21 @@ int encode_map(fe_ctx *ctx, CUtensorMap *m, void *base, int n, int ld_elems, int
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, gdim, gstride, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_err(ctx, FE_ECUDA, "cuTensorMapEncodeTiled failed");
+    return FE_OK;
+}
+
+int encode_map_rect(fe_ctx *ctx, CUtensorMap *m, void *base, int64_t kdim, int64_t rows, int64_t ld_elems,
+                    int box_rows) {
+    auto enc = get_encode();
+    if (!enc) return set_err(ctx, FE_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    cuuint64_t gdim[2] = {static_cast<cuuint64_t>(kdim), static_cast<cuuint64_t>(rows)};
+    cuuint64_t gstride[1] = {static_cast<cuuint64_t>(ld_elems) * 2};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(kTileK), static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_err(ctx, FE_ECUDA, "cuTensorMapEncodeTiled failed");
     return FE_OK;
@@ -1459,7 +1487,9 @@ extern "C" int fe_create(fe_ctx **out, const fe_config *cfg) {
     if (rc == FE_OK && (cudaFuncSetAttribute(k_sym_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(mma_smem_bytes())) != cudaSuccess ||
                         cudaFuncSetAttribute(k_digit_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(digit_smem_bytes())) != cudaSuccess))
+                                             static_cast<int>(digit_smem_bytes())) != cudaSuccess ||
+                        cudaFuncSetAttribute(k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(gemm_smem_bytes())) != cudaSuccess))
         rc = set_err(nullptr, FE_ECUDA, std::string("context setup: ") + cudaGetErrorString(cudaGetLastError()));
     if (rc == FE_OK) {
         // the register hand-off inside the split-FP16 kernel assumes this allocation
@@ -1501,6 +1531,10 @@ extern "C" int fe_destroy(fe_ctx *ctx) {
     }
     ctx->slots.clear();
     for (cudaEvent_t ev : ctx->pev) cudaEventDestroy(ev);
+    if (ctx->gws) cudaFree(ctx->gws);
+    if (ctx->d_gargs) cudaFree(ctx->d_gargs);
+    if (ctx->d_gtiles) cudaFree(ctx->d_gtiles);
+    if (ctx->d_amax) cudaFree(ctx->d_amax);
     delete ctx;
     return FE_OK;
 }
@@ -1800,6 +1834,177 @@ extern "C" int fe_k_digit_square(fe_ctx *ctx, const double *X, int64_t n, int64_
     if (e != cudaSuccess) return cuda_fail(ctx, e, "digit_square");
     if (herr) return set_err(ctx, FE_ETIMEOUT, "device wait timed out (code " + std::to_string(herr) + ")");
     return FE_OK;
+}
+
+// ============================================================== either side of the expansion
+
+namespace {
+
+// Run C = A B^T (k_gemm_split, + k_gemm_reduce in split mode) on the
+// context's stream with the slices already in the workspace; blocking.
+int run_gemm(fe_ctx *ctx, const GemmArgs &ga, const std::vector<TileEnt> &tl, const char *what) {
+    Engine &eg = ctx->eng;
+    cudaStream_t q = eg.stream;
+    int rc = ensure_dev(ctx, &ctx->d_gtiles, &ctx->gtiles_cap, tl.size());
+    if (rc != FE_OK) return rc;
+    FE_CUDA(ctx, cudaMemcpyAsync(ctx->d_gargs, &ga, sizeof(GemmArgs), cudaMemcpyHostToDevice, q));
+    FE_CUDA(ctx, cudaMemcpyAsync(ctx->d_gtiles, tl.data(), sizeof(TileEnt) * tl.size(), cudaMemcpyHostToDevice, q));
+    FE_CUDA(ctx, cudaMemsetAsync(eg.d_err, 0, sizeof(int), q));
+    const int units = ga.ntiles * (ga.nsplit > 0 ? ga.nsplit : 1);
+    FE_CUDA(ctx, cudaEventRecord(eg.ev_setup, q));
+    k_gemm_split<<<std::min(units, ctx->num_sms), kGemmThreads, gemm_smem_bytes(), q>>>(ctx->d_gargs, ctx->d_gtiles,
+                                                                                        eg.d_err);
+    ctx->launches += 1;
+    FE_CUDA(ctx, cudaEventRecord(eg.ev_loop, q));
+    if (ga.nsplit > 0) {
+        k_gemm_reduce<<<ga.ntiles, 256, 0, q>>>(ctx->d_gargs, ctx->d_gtiles);
+        ctx->launches += 1;
+    }
+    FE_CUDA(ctx, cudaEventRecord(eg.ev1, q));
+    FE_CUDA(ctx, cudaGetLastError());
+    int herr = 0;
+    FE_CUDA(ctx, cudaMemcpyAsync(&herr, eg.d_err, sizeof(int), cudaMemcpyDeviceToHost, q));
+    const cudaError_t e = cudaStreamSynchronize(q);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    // operand split, tensor-core product, reduction of the K parts
+    float a = 0.0f, b = 0.0f, c = 0.0f;
+    cudaEventElapsedTime(&a, eg.ev0, eg.ev_setup);
+    cudaEventElapsedTime(&b, eg.ev_setup, eg.ev_loop);
+    cudaEventElapsedTime(&c, eg.ev_loop, eg.ev1);
+    ctx->phase_ms[0] = a;
+    ctx->phase_ms[1] = b;
+    ctx->phase_ms[2] = c;
+    ctx->phase_ms[3] = units;
+    if (herr) return set_err(ctx, FE_ETIMEOUT, std::string(what) + ": device wait timed out (code " +
+                                                   std::to_string(herr) + ")");
+    return FE_OK;
+}
+
+// Workspace of `bytes` and the small device blocks of the GEMM path.
+int gemm_workspace(fe_ctx *ctx, size_t bytes) {
+    if (!ctx->d_gargs) FE_CUDA(ctx, cudaMalloc(&ctx->d_gargs, sizeof(GemmArgs)));
+    if (!ctx->d_amax) FE_CUDA(ctx, cudaMalloc(&ctx->d_amax, 2 * sizeof(unsigned long long)));
+    if (bytes <= ctx->gws_cap) return FE_OK;
+    if (ctx->gws) cudaFree(ctx->gws);
+    ctx->gws = nullptr;
+    ctx->gws_cap = 0;
+    if (bytes > ctx->budget) return set_err(ctx, FE_ENOMEM, "workspace of " + std::to_string(bytes) +
+                                                                 " bytes exceeds the HBM budget");
+    if (cudaMalloc(&ctx->gws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, FE_ENOMEM, "no device memory for the workspace");
+    }
+    ctx->gws_cap = bytes;
+    return FE_OK;
+}
+
+int split_grid(fe_ctx *ctx, int64_t rows, int64_t cols) {
+    const int64_t t = ((rows + 31) / 32) * ((cols + 31) / 32);
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(t, 8LL * ctx->num_sms)));
+}
+
+}  // namespace
+
+extern "C" int fe_project(fe_ctx *ctx, const double *Psi, const double *HPsi, int64_t m, int64_t n, int64_t ld,
+                          double *Hp, int64_t ldh) {
+    if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
+    if (!Psi || !HPsi || !Hp || m < 1 || n < 1 || n > (1 << 20) || m > INT_MAX || ld < n || ldh < n)
+        return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t q = ctx->eng.stream;
+    const int64_t lds = static_cast<int64_t>(align_up(static_cast<size_t>(m), 8));  // slices of Psi^T: n rows of m
+    const int nk = static_cast<int>((m + kTileK - 1) / kTileK);
+    // upper-triangle tiles: 128-row block I, 192-column panel J holding some j >= i
+    std::vector<TileEnt> tl;
+    const int TI = static_cast<int>((n + kTileM - 1) / kTileM), TJ = static_cast<int>((n + kGemmN - 1) / kGemmN);
+    for (int J = 0; J < TJ; ++J)
+        for (int I = 0; I < TI; ++I)
+            if (static_cast<int64_t>(J) * kGemmN + kGemmN - 1 >= static_cast<int64_t>(I) * kTileM)
+                tl.push_back(TileEnt{0, I, J, 0});
+    const int ntiles = static_cast<int>(tl.size());
+    // K parts: at most 128 chunks (K = 8192) summed in FP32 per part, and
+    // enough work units for about six waves over the SMs; at least 8 chunks a part
+    int S = std::max((nk + 127) / 128, (6 * ctx->num_sms + ntiles - 1) / ntiles);
+    S = std::max(1, std::min(S, std::max(1, nk / 8)));
+    const int cs = (nk + S - 1) / S;
+    S = (nk + cs - 1) / cs;  // every part non-empty
+    const size_t slice = 2 * static_cast<size_t>(n) * static_cast<size_t>(lds);
+    const size_t tsz = static_cast<size_t>(kTileM) * kGemmN * sizeof(float);
+    const size_t bytes = align_up(4 * slice, 1024) + static_cast<size_t>(ntiles) * S * tsz;
+    int rc = gemm_workspace(ctx, bytes);
+    if (rc != FE_OK) return rc;
+    __half *sl[4];
+    for (int k = 0; k < 4; ++k) sl[k] = reinterpret_cast<__half *>(ctx->gws + k * slice);
+    GemmArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    for (int k = 0; k < 2 && rc == FE_OK; ++k) {
+        rc = encode_map_rect(ctx, &ga.tA[k], sl[k], m, n, lds, kTileM);
+        if (rc == FE_OK) rc = encode_map_rect(ctx, &ga.tB[k], sl[2 + k], m, n, lds, kGemmN);
+    }
+    if (rc != FE_OK) return rc;
+    ga.C = Hp;
+    ga.ldc = ldh;
+    ga.ws = reinterpret_cast<float *>(ctx->gws + align_up(4 * slice, 1024));
+    ga.amax = ctx->d_amax;
+    ga.rows_a = ga.rows_b = static_cast<int>(n);
+    ga.kdim = static_cast<int>(m);
+    ga.nsplit = S;
+    ga.ntiles = ntiles;
+    FE_CUDA(ctx, cudaEventRecord(ctx->eng.ev0, q));
+    FE_CUDA(ctx, cudaMemsetAsync(ctx->d_amax, 0, 2 * sizeof(unsigned long long), q));
+    k_absmax<<<4 * ctx->num_sms, 256, 0, q>>>(Psi, m, n, ld, ctx->d_amax);
+    k_absmax<<<4 * ctx->num_sms, 256, 0, q>>>(HPsi, m, n, ld, ctx->d_amax + 1);
+    const int gs = split_grid(ctx, m, n);
+    k_split_rows<<<gs, 256, 0, q>>>(Psi, m, n, ld, ctx->d_amax, sl[0], sl[1], lds, 1);
+    k_split_rows<<<gs, 256, 0, q>>>(HPsi, m, n, ld, ctx->d_amax + 1, sl[2], sl[3], lds, 1);
+    ctx->launches += 4;
+    return run_gemm(ctx, ga, tl, "fe_project");
+}
+
+extern "C" int fe_rotate(fe_ctx *ctx, const double *Psi, int64_t m, int64_t n, int64_t ldpsi, const double *D,
+                         int64_t ldd, double *Out, int64_t ldo) {
+    if (!ctx) return set_err(nullptr, FE_EINVAL, "ctx is NULL");
+    if (!Psi || !D || !Out || m < 1 || n < 1 || n > (1 << 20) || m > INT_MAX || ldpsi < n || ldd < n || ldo < n)
+        return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t q = ctx->eng.stream;
+    const int64_t lds = static_cast<int64_t>(align_up(static_cast<size_t>(n), 8));  // K = n
+    std::vector<TileEnt> tl;
+    const int TI = static_cast<int>((m + kTileM - 1) / kTileM), TJ = static_cast<int>((n + kGemmN - 1) / kGemmN);
+    for (int I = 0; I < TI; ++I)
+        for (int J = 0; J < TJ; ++J) tl.push_back(TileEnt{0, I, J, 0});
+    const size_t sa = 2 * static_cast<size_t>(m) * static_cast<size_t>(lds);
+    const size_t sb = 2 * static_cast<size_t>(n) * static_cast<size_t>(lds);
+    const size_t oa = align_up(sa, 1024), ob = align_up(sb, 1024);
+    int rc = gemm_workspace(ctx, 2 * oa + 2 * ob);
+    if (rc != FE_OK) return rc;
+    __half *ah = reinterpret_cast<__half *>(ctx->gws), *al = reinterpret_cast<__half *>(ctx->gws + oa);
+    __half *bh = reinterpret_cast<__half *>(ctx->gws + 2 * oa), *bl = reinterpret_cast<__half *>(ctx->gws + 2 * oa + ob);
+    GemmArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    rc = encode_map_rect(ctx, &ga.tA[0], ah, n, m, lds, kTileM);
+    if (rc == FE_OK) rc = encode_map_rect(ctx, &ga.tA[1], al, n, m, lds, kTileM);
+    if (rc == FE_OK) rc = encode_map_rect(ctx, &ga.tB[0], bh, n, n, lds, kGemmN);
+    if (rc == FE_OK) rc = encode_map_rect(ctx, &ga.tB[1], bl, n, n, lds, kGemmN);
+    if (rc != FE_OK) return rc;
+    ga.C = Out;
+    ga.ldc = ldo;
+    ga.amax = ctx->d_amax;
+    ga.rows_a = static_cast<int>(m);
+    ga.rows_b = static_cast<int>(n);
+    ga.kdim = static_cast<int>(n);
+    ga.nsplit = 0;
+    ga.ntiles = static_cast<int>(tl.size());
+    FE_CUDA(ctx, cudaEventRecord(ctx->eng.ev0, q));
+    FE_CUDA(ctx, cudaMemsetAsync(ctx->d_amax, 0, 2 * sizeof(unsigned long long), q));
+    k_absmax<<<4 * ctx->num_sms, 256, 0, q>>>(Psi, m, n, ldpsi, ctx->d_amax);
+    k_absmax<<<4 * ctx->num_sms, 256, 0, q>>>(D, n, n, ldd, ctx->d_amax + 1);
+    k_split_rows<<<split_grid(ctx, m, n), 256, 0, q>>>(Psi, m, n, ldpsi, ctx->d_amax, ah, al, lds, 0);
+    k_split_rows<<<split_grid(ctx, n, n), 256, 0, q>>>(D, n, n, ldd, ctx->d_amax + 1, bh, bl, lds, 0);
+    ctx->launches += 4;
+    return run_gemm(ctx, ga, tl, "fe_rotate");
 }
 
 extern "C" int fe_k_profile(fe_ctx *ctx, int enable) {

@@ -183,6 +183,31 @@ constexpr int kInitBlocks = 304;   // 2 x 152 SMs
 constexpr int kFinBlocks = 304;
 constexpr int kTile64 = 64;
 
+// ---- products either side of the expansion in subspace iteration (k_gemm.cu)
+// C = A B^T from K-major FP16 slices (hi, lo), tiles 128 x kGemmN.
+constexpr int kGemmN = 192;
+constexpr int kGemmThreads = 512;     // warp 0 TMA, warp 1 MMA, warps 2-3 idle, warps 4-15 drain
+constexpr int kGemmDrainWarps = 12;
+struct GemmArgs {
+    CUtensorMap tA[kMaxSlices];       // A slices (rows_a x kdim), box 64 (K) x 128 rows
+    CUtensorMap tB[kMaxSlices];       // B slices (rows_b x kdim), box 64 (K) x kGemmN rows
+    double *C;                        // FP64 result, leading dimension ldc
+    float *ws;                        // split mode: FP32 partial tiles, [unit][column][row]
+    const unsigned long long *amax;   // [0] max|A|, [1] max|B| as FP64 bit patterns (slice scales)
+    long long ldc;
+    int rows_a, rows_b, kdim;
+    int nsplit;                       // 0: direct C = A B^T; > 0: K in nsplit parts, k_gemm_reduce
+                                      // sums them into the symmetric C (rows_a = rows_b)
+    int ntiles, pad;
+};
+__global__ void k_gemm_split(const GemmArgs *__restrict__ args, const TileEnt *__restrict__ tiles, DevCtl *ctl);
+__global__ void k_gemm_reduce(const GemmArgs *__restrict__ args, const TileEnt *__restrict__ tiles);
+__global__ void k_absmax(const double *__restrict__ X, long long rows, long long cols, long long ld,
+                         unsigned long long *out);
+__global__ void k_split_rows(const double *__restrict__ X, long long rows, long long cols, long long ld,
+                             const unsigned long long *amax, __half *hi, __half *lo, long long lds, int transpose);
+size_t gemm_smem_bytes();
+
 // Record msg as the calling thread's last error (fe_last_error_string); returns code.
 int set_error_string(int code, const std::string &msg);
 

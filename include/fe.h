@@ -249,9 +249,11 @@ FE_API int fe_autotune_batch(fe_ctx *ctx, int count, const fe_problem *ps, int r
  * power-of-two scale per operand from its largest entry) and multiplied on
  * the tensor cores with FP32 accumulation per 64-wide K chunk, the chunks
  * summed in FP32 registers (at most 128 per part) and the parts in FP64:
- * |C_ij - (A B)_ij| <= (2^-21 + 2^-21 + c 2^-24) sum_k |A_ik| |B_kj|, c the
- * chunks of one part (an FP32-class result, as the FP32 Rayleigh-Ritz
- * products of mixed-precision subspace iteration).
+ * |C_ij - (A B)_ij| <= (2^-21 + 2^-21 + c 2^-24) sum_k |A_ik| |B_kj|
+ * + 2^-36 K max|A| max|B|, c the chunks of one part (the last term for
+ * entries below 2^-25 of their operand's largest, whose low slice leaves the
+ * FP16 normal range); an FP32-class result, as the FP32 Rayleigh-Ritz
+ * products of mixed-precision subspace iteration.
  * Errors: FE_EINVAL (NULL pointer, m or n < 1, n > 2^20, m > 2^31 - 1, a
  * leading dimension below n), FE_ENOMEM (workspace of about 8 m n bytes for
  * fe_project, 4 (m + n) n for fe_rotate, beyond the HBM budget), FE_ETIMEOUT,

@@ -979,8 +979,10 @@ def bench_chfsi(args, torch, fe):
     ref_r = Psi[rows] @ Dm
     err_r = float(((Out[rows] - ref_r).abs().max() / (Psi[rows].abs() @ Dm.abs()).max()).item())
 
+    keys = ("setup_ms", "loop_ms", "output_ms", "steps")  # split, product, reduce, work units
+
     def med(ph, k):
-        return statistics.median(x[k] for x in ph)
+        return statistics.median(x[keys[k]] for x in ph)
 
     tiles_p = sum(1 for J in range((n + 191) // 192) for I in range((n + 127) // 128) if J * 192 + 191 >= I * 128)
     flops_p = 3 * 2.0 * tiles_p * 128 * 192 * m       # algorithmic: 3 split products per tile
@@ -993,7 +995,7 @@ def bench_chfsi(args, torch, fe):
             "split_project_ms": med(ph_p, 0), "split_rotate_ms": med(ph_r, 0), "reduce_project_ms": med(ph_p, 2),
             # max pass + split pass: read Psi and H Psi twice (FP64), write 2 x 2 FP16 slices
             "split_project_gbs": 40.0 * m * n / med(ph_p, 0) / 1e6,
-            "k_parts_units": ph_p[-1][3]}
+            "k_parts_units": ph_p[-1][keys[3]]}
     dom = max(("k_gemm_split_project", "k_gemm_split_rotate"), key=lambda k: kern[k]["ms"])
     out = {"metric": "chfsi_project_and_rotate_per_s", "value": args.steps / (t_ms / 1e3), "unit": "pairs/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,

@@ -545,9 +545,9 @@ def main():
     ctx.profile(True)
     rp = one()
     prof = ctx.profile_read()
-    steps_ms = ctx.profile_steps(max_steps=1000)
+    kinds = ctx.profile_kinds()
     ctx.profile(False)
-    kernels, roof = kernel_table(prec, kT, n, rp, prof, steps_ms, peaks, peak_kind, args.workload)
+    kernels, roof = kernel_table(prec, kT, n, rp, prof, kinds, peaks, peak_kind, args.workload)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -634,57 +634,45 @@ def _gershgorin_torch(H):
     return float((H.diagonal() - a).min()), float((H.diagonal() + a).max())
 
 
-def kernel_table(prec, kT, n, rp, prof, steps_ms, peaks, peak_kind, workload):
-    """Per-kernel CUDA-event times of the profiled solve and the roofline
-    object of the dominant kernel.  Finite temperature: the tensor-core
-    launches include epilogue-only steps (shift-only Newton steps of mu,
-    no products); they are told apart by time (below 40% of the median
-    launch) and left out of the product rate."""
+def kernel_table(prec, kT, n, rp, prof, kinds, peaks, peak_kind, workload):
+    """Per-kernel CUDA-event times of the profiled solve (its step launches
+    summed by the kind of step the control kernel issued) and the roofline
+    object of the dominant kernel.  k_sym_mma runs split-FP16 products (3 MMA
+    products of the upper triangle each), single-FP16 ones (1) and
+    epilogue-only steps (none, left out of the rate)."""
     sym_flops = float(n) * n * (n + 1)  # upper triangle incl. diagonal: n^2 (n+1) per product
-    n_single = rp["iters_by_phase"][0] if kT == 0.0 else 0
-    act = [t for t in steps_ms[: int(prof["tc_launches"])] if t > 0]
-    single_ms = float(sum(act[:n_single]))
-    split = act[n_single:]
-    epi = []
-    if kT > 0.0 and split:
-        med = statistics.median(split)
-        epi = [t for t in split if t < 0.4 * med]
-        split = [t for t in split if t >= 0.4 * med]
-    tc_split_ms = float(sum(split))
-    tc_n = max(len(split), 1)
-    tc_avg = tc_split_ms / tc_n
-    fp_n = max(prof["fp64_launches"], 1)
-    fp_avg = prof["fp64_ms"] / fp_n
-    fp_name = "k_digit_mma" if prec != "fp64" else "k_fp64_step"
+    ms_sp, n_sp = kinds["split_fp16"]
+    ms_si, n_si = kinds["single_fp16"]
+    ms_ep, n_ep = kinds["epilogue_only"]
+    tc_ms = ms_sp + ms_si
+    tc_flops = (3 * n_sp + n_si) * sym_flops
     kernels = {
-        "k_sym_mma": {"launches": len(split), "ms_total": tc_split_ms, "ms_avg": tc_avg,
-                      "algorithmic_flops": 3 * sym_flops,
-                      "achieved_tflops": 3 * sym_flops / (tc_avg * 1e-3) / 1e12 if tc_split_ms > 0 else 0},
+        "k_sym_mma": {"launches": n_sp + n_si, "split_launches": n_sp, "single_launches": n_si,
+                      "ms_total": tc_ms, "ms_avg": tc_ms / max(n_sp + n_si, 1),
+                      "ms_avg_split": ms_sp / n_sp if n_sp else None,
+                      "ms_avg_single": ms_si / n_si if n_si else None,
+                      "algorithmic_flops": tc_flops,
+                      "achieved_tflops": tc_flops / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else 0},
     }
-    if epi:
-        kernels["k_sym_mma_epilogue_only"] = {"launches": len(epi), "ms_total": float(sum(epi)),
-                                              "ms_avg": float(sum(epi)) / len(epi)}
-    if kT == 0.0:
-        kernels[fp_name] = {"launches": prof["fp64_launches"], "ms_total": prof["fp64_ms"],
-                            "ms_avg": fp_avg, "fp64_equivalent_flops": sym_flops,
-                            "fp64_equivalent_tflops": sym_flops / (fp_avg * 1e-3) / 1e12 if prof["fp64_ms"] else 0}
+    if n_ep:
+        kernels["k_sym_mma_epilogue_only"] = {"launches": n_ep, "ms_total": ms_ep, "ms_avg": ms_ep / n_ep}
+    fp_name = "k_digit_mma" if prec != "fp64" else "k_fp64_step"
+    ms_fp, n_fp = kinds["digit"] if prec != "fp64" else kinds["fp64"]
+    if n_fp:
+        fp_avg = ms_fp / n_fp
+        kernels[fp_name] = {"launches": n_fp, "ms_total": ms_fp, "ms_avg": fp_avg,
+                            "fp64_equivalent_flops": sym_flops,
+                            "fp64_equivalent_tflops": sym_flops / (fp_avg * 1e-3) / 1e12}
         if fp_name == "k_digit_mma":
             # 28 FP16 digit products per FP64-accurate product (levels a + c <= 6 of 7 digits)
             kernels[fp_name]["algorithmic_flops"] = 28 * sym_flops
-            kernels[fp_name]["achieved_tflops"] = (28 * sym_flops / (fp_avg * 1e-3) / 1e12
-                                                   if prof["fp64_ms"] else 0)
+            kernels[fp_name]["achieved_tflops"] = 28 * sym_flops / (fp_avg * 1e-3) / 1e12
             kernels[fp_name]["includes"] = "k_digit_prep (digit split of X) + k_digit_mma"
         else:
             kernels[fp_name]["algorithmic_flops"] = sym_flops
             kernels[fp_name]["achieved_tflops"] = kernels[fp_name]["fp64_equivalent_tflops"]
-    tc_names = ["k_sym_mma"] + ([fp_name] if kT == 0.0 else [])
-    if n_single:
-        avg1 = single_ms / n_single
-        kernels["k_sym_mma_fp16"] = {"launches": n_single, "ms_total": single_ms, "ms_avg": avg1,
-                                     "algorithmic_flops": sym_flops,
-                                     "achieved_tflops": sym_flops / (avg1 * 1e-3) / 1e12}
-        tc_names.append("k_sym_mma_fp16")
-    kernels["share_of_solve"] = {k: kernels[k]["ms_total"] / prof["solve_ms"] for k in tc_names}
+    names = [k for k in ("k_sym_mma", fp_name) if k in kernels and kernels[k]["ms_total"] > 0]
+    kernels["share_of_solve"] = {k: kernels[k]["ms_total"] / prof["solve_ms"] for k in names}
     # a kernel timed inside a solve of a second or more runs under the
     # sustained (power-capped) clock; shorter solves take the burst peak
     sustained = prof["solve_ms"] >= 1000.0
@@ -692,7 +680,7 @@ def kernel_table(prec, kT, n, rp, prof, steps_ms, peaks, peak_kind, workload):
     src = "%s bf16 dense %s (fp16 dense has the same rate); solve %.1f ms" % (
         peak_kind, "sustained" if sustained else "burst", prof["solve_ms"])
     if prec != "fp64":
-        kname = max(tc_names, key=lambda k: kernels[k]["ms_total"])
+        kname = max(names, key=lambda k: kernels[k]["ms_total"])
         ach = kernels[kname]["achieved_tflops"]
         roof = {"kernel": kname, "bound": "tensor", "achieved": ach, "peak": pk,
                 "unit": "TFLOP/s", "frac": ach / pk,
@@ -972,9 +960,12 @@ def bench_chfsi(args, torch, fe):
         torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1)
     # accuracy against FP64 products by torch (cuBLAS DGEMM) on sampled rows
+    # the projection is computed on the upper triangle and mirrored: compare
+    # rows i <= j of the sampled columns j
     idx = torch.arange(0, n, 97, device=dev)
     ref_p = Psi.T @ HPsi[:, idx]
-    err_p = float(((Hp[:, idx] - ref_p).abs().max() / (Psi.abs().T @ HPsi[:, idx].abs()).max()).item())
+    upper = torch.arange(n, device=dev)[:, None] <= idx[None, :]
+    err_p = float((((Hp[:, idx] - ref_p).abs() * upper).max() / (Psi.abs().T @ HPsi[:, idx].abs()).max()).item())
     rows = torch.arange(0, m, 1031, device=dev)
     ref_r = Psi[rows] @ Dm
     err_r = float(((Out[rows] - ref_r).abs().max() / (Psi[rows].abs() @ Dm.abs()).max()).item())
@@ -1068,17 +1059,23 @@ def bench_serve(args, torch, fe):
         lat = [x["ms"] for x in res]
         ok = sum(1 for x in res if x["status"] == 0)
         worst = {"eps1_probe": 0.0, "e_err_per_electron": 0.0}
+        per = []
         for (p, q), Dq, x in zip(reqs, outs, res):
-            e = probe_errors(torch, Dq, p.Q, p.lam, reference_occupations(p.lam, p.ne, q["kT"]), p.ne, q["kT"], x)
-            for k in worst:
-                worst[k] = max(worst[k], e[k])
+            rec = {"n": int(p.n), "kT": float(q["kT"]), "status": x["status"], "iters": x["iters"],
+                   "ms": round(x["ms"], 1)}
+            if x["status"] == 0:
+                e = probe_errors(torch, Dq, p.Q, p.lam, reference_occupations(p.lam, p.ne, q["kT"]), p.ne,
+                                 q["kT"], x)
+                rec["eps1_probe"] = e["eps1_probe"]
+                for k in worst:
+                    worst[k] = max(worst[k], e[k])
+            per.append(rec)
         return {"label": label, "requests": len(reqs), "completed_ok": ok, "seconds": t1 - t0,
                 "solves_per_s": ok / (t1 - t0),
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                 "deferred": stats["deferred"], "peak_queue_depth": stats["peak_waiting"],
                 "peak_on_device": stats["peak_running"], "gpu_launches": launches, "clocks": clk.summary(),
-                "accuracy_worst_request": worst,
-                "n_served": [int(p.n) for p, _ in reqs]}
+                "accuracy_worst_request": worst, "requests_detail": per}
 
     main_reqs = make(3000, count, rate)
     main = run(main_reqs, "offered %g/s" % rate)

@@ -78,6 +78,14 @@ FE_API int fe_k_profile_read(fe_ctx *ctx, double *out8);
  * values are single-FP16 products and the next iters_by_phase[1] split ones. */
 FE_API int fe_k_profile_steps(fe_ctx *ctx, double *out, int max_steps, int *count);
 
+/* The last profiled solve's step launches summed by the kind of step
+ * (measurement hook, no counterpart in the paper; first problem of the
+ * batch), HOST out: ms8[k] milliseconds and n8[k] launches of kind k,
+ * 1 single-FP16 tensor-core product, 2 split-FP16 product, 3 native FP64
+ * product, 5 epilogue-only tensor-core step, 6 FP64-accurate digit product
+ * (its digit split included); other entries 0. */
+FE_API int fe_k_profile_kinds(fe_ctx *ctx, double *ms8, int *n8);
+
 /* Test hook (no counterpart in the paper): every following solve on ctx,
  * blocking or submitted, shrinks its Lanczos estimate of the spectral bounds
  * about the interval's centre by `factor` (1 = off, the default) before the

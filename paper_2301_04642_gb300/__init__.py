@@ -87,6 +87,7 @@ def load(build=True):
     L.fe_k_narrow_bounds.argtypes = [P, dbl]
     L.fe_k_set_wait.argtypes = [P, dbl, ctypes.c_int]
     L.fe_k_serve_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.c_int]
+    L.fe_k_profile_kinds.argtypes = [P, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_int)]
     L.fe_k_phase_ms.argtypes = [P, ctypes.POINTER(dbl)]
     L.fe_k_profile_steps.argtypes = [P, ctypes.POINTER(dbl), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.fe_k_profile_read.argtypes = [P, ctypes.POINTER(dbl)]
@@ -102,7 +103,7 @@ def load(build=True):
     for name in ("fe_create", "fe_destroy", "fe_solve", "fe_solve_batch", "fe_submit", "fe_poll",
                  "fe_project", "fe_rotate",
                  "fe_k_gershgorin", "fe_k_gershgorin_noalloc", "fe_k_sym_square", "fe_k_digit_square",
-                 "fe_k_profile", "fe_k_profile_read", "fe_k_narrow_bounds", "fe_k_set_wait", "fe_k_serve_stats", "fe_k_phase_ms",
+                 "fe_k_profile", "fe_k_profile_read", "fe_k_narrow_bounds", "fe_k_set_wait", "fe_k_serve_stats", "fe_k_profile_kinds", "fe_k_phase_ms",
                  "fe_k_profile_steps",
                  "fe_k_launch_count", "fe_k_history", "fe_autotune", "fe_autotune_batch", "fe_k_set_tile_width",
                  "fe_k_tile_width"):
@@ -414,6 +415,16 @@ class Context:
         rc = self.L.fe_k_set_wait(self.h, float(limit_ms), 1 if fail_partner else 0)
         if rc != FE_OK:
             raise FeError(rc, self.last_error())
+
+    def profile_kinds(self):
+        """Step launches of the last profiled solve by kind: {name: (ms, launches)}."""
+        ms = (ctypes.c_double * 8)()
+        cnt = (ctypes.c_int * 8)()
+        rc = self.L.fe_k_profile_kinds(self.h, ms, cnt)
+        if rc != FE_OK:
+            raise FeError(rc, self.last_error())
+        names = {1: "single_fp16", 2: "split_fp16", 3: "fp64", 5: "epilogue_only", 6: "digit"}
+        return {v: (ms[k], cnt[k]) for k, v in names.items()}
 
     def narrow_bounds(self, factor):
         """Test hook: shrink the estimated spectral bounds of later solves

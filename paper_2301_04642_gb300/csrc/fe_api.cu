@@ -158,6 +158,8 @@ struct fe_ctx {
     std::vector<cudaEvent_t> pev;
     double prof_out[8] = {};
     std::vector<double> prof_steps;  // tensor-core launch ms of each step of the last profiled solve
+    double prof_kind_ms[8] = {};     // ... summed by the kind of step (first problem of the table)
+    int prof_kind_n[8] = {};
     std::atomic<long long> launches{0};  // kernels launched by this context
     std::atomic<double> lz_narrow{1.0};  // test hook: scale of the estimated bound interval
     double phase_ms[4] = {};             // last blocking solve: set-up, step loop, output; steps
@@ -1145,6 +1147,21 @@ int run_problems_once(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) 
         ctx->prof_out[5] = static_cast<double>(ctx->launches.load());
         ctx->prof_out[6] = tc_all;
         ctx->prof_out[7] = e.any_tc ? nloop : 0;
+        // by kind of step: the k-th pass of the loop runs the k-th step issued
+        for (int q = 0; q < 8; ++q) {
+            ctx->prof_kind_ms[q] = 0.0;
+            ctx->prof_kind_n[q] = 0;
+        }
+        const SolveState &s0 = e.h_states[0];
+        for (int it = 0; it < nloop && it < s0.nctl && it < kKindLog; ++it) {
+            const int kd = s0.kind_log[it];
+            if (kd <= kNone || kd > 7) continue;
+            float a = 0;
+            const bool tc = (kd == kTcSingle || kd == kTcSplit || kd == kTcElem);
+            cudaEventElapsedTime(&a, ctx->pev[4 * it + (tc ? 0 : 2)], ctx->pev[4 * it + (tc ? 1 : 3)]);
+            ctx->prof_kind_ms[kd] += a;
+            ctx->prof_kind_n[kd] += 1;
+        }
     }
     int first_bad = FE_OK;
     for (int k = 0; k < np; ++k) {
@@ -1898,8 +1915,10 @@ int gemm_workspace(fe_ctx *ctx, size_t bytes) {
     return FE_OK;
 }
 
-int split_grid(fe_ctx *ctx, int64_t rows, int64_t cols) {
-    const int64_t t = ((rows + 31) / 32) * ((cols + 31) / 32);
+// Blocks of k_split_rows: one per row (direct) or per 64 x 64 tile
+// (transposed), at most 8 per SM (the kernel loops).
+int split_grid(fe_ctx *ctx, int64_t rows, int64_t cols, bool transpose) {
+    const int64_t t = transpose ? ((rows + 63) / 64) * ((cols + 63) / 64) : rows;
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(t, 8LL * ctx->num_sms)));
 }
 
@@ -1955,7 +1974,7 @@ extern "C" int fe_project(fe_ctx *ctx, const double *Psi, const double *HPsi, in
     FE_CUDA(ctx, cudaMemsetAsync(ctx->d_amax, 0, 2 * sizeof(unsigned long long), q));
     k_absmax<<<4 * ctx->num_sms, 256, 0, q>>>(Psi, m, n, ld, ctx->d_amax);
     k_absmax<<<4 * ctx->num_sms, 256, 0, q>>>(HPsi, m, n, ld, ctx->d_amax + 1);
-    const int gs = split_grid(ctx, m, n);
+    const int gs = split_grid(ctx, m, n, true);
     k_split_rows<<<gs, 256, 0, q>>>(Psi, m, n, ld, ctx->d_amax, sl[0], sl[1], lds, 1);
     k_split_rows<<<gs, 256, 0, q>>>(HPsi, m, n, ld, ctx->d_amax + 1, sl[2], sl[3], lds, 1);
     ctx->launches += 4;
@@ -2001,8 +2020,8 @@ extern "C" int fe_rotate(fe_ctx *ctx, const double *Psi, int64_t m, int64_t n, i
     FE_CUDA(ctx, cudaMemsetAsync(ctx->d_amax, 0, 2 * sizeof(unsigned long long), q));
     k_absmax<<<4 * ctx->num_sms, 256, 0, q>>>(Psi, m, n, ldpsi, ctx->d_amax);
     k_absmax<<<4 * ctx->num_sms, 256, 0, q>>>(D, n, n, ldd, ctx->d_amax + 1);
-    k_split_rows<<<split_grid(ctx, m, n), 256, 0, q>>>(Psi, m, n, ldpsi, ctx->d_amax, ah, al, lds, 0);
-    k_split_rows<<<split_grid(ctx, n, n), 256, 0, q>>>(D, n, n, ldd, ctx->d_amax + 1, bh, bl, lds, 0);
+    k_split_rows<<<split_grid(ctx, m, n, false), 256, 0, q>>>(Psi, m, n, ldpsi, ctx->d_amax, ah, al, lds, 0);
+    k_split_rows<<<split_grid(ctx, n, n, false), 256, 0, q>>>(D, n, n, ldd, ctx->d_amax + 1, bh, bl, lds, 0);
     ctx->launches += 4;
     return run_gemm(ctx, ga, tl, "fe_rotate");
 }
@@ -2039,6 +2058,16 @@ extern "C" int fe_k_set_wait(fe_ctx *ctx, double limit_ms, int fail_partner) {
                                      reinterpret_cast<const char *>(&c) + sizeof(int), sizeof(DevCtl) - sizeof(int),
                                      cudaMemcpyHostToDevice, e->stream));
         FE_CUDA(ctx, cudaStreamSynchronize(e->stream));
+    }
+    return FE_OK;
+}
+
+extern "C" int fe_k_profile_kinds(fe_ctx *ctx, double *ms8, int *n8) {
+    if (!ctx || !ms8 || !n8) return set_err(ctx, FE_EINVAL, "bad arguments");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    for (int q = 0; q < 8; ++q) {
+        ms8[q] = ctx->prof_kind_ms[q];
+        n8[q] = ctx->prof_kind_n[q];
     }
     return FE_OK;
 }

@@ -90,6 +90,7 @@ constexpr int kCheckSteps = 3;      // logistic steps certifying the estimate (T
 constexpr int kStatusEscaped = -100;  // internal: an eigenvalue left [0, 1] (bounds too tight)
 constexpr int kStatusAccelFailed = -101;  // internal: HOMO/LUMO estimates inconsistent (run plain SP2)
 constexpr int kTrfoeMaxSteps = 128;   // branch bits kept for the truncated expansion
+constexpr int kKindLog = 768;         // per-step kinds kept for the profiling hook
 constexpr int kHistCols = 6;
 
 // ---------------------------------------------------------------- state
@@ -139,6 +140,9 @@ struct SolveState {
     double beta, mu_t, beta0;
     int ft_m, ft_stage, ft_sub, ft_j, ft_nj, ft_shifts, wcur, ft_phase;
     int ft_last_mat, ft_pad2;  // slot whose ||.||_F the last step's partials report
+    double ns_r;      // Newton-Schulz: bound on the residual ||I - M W|| of the current W
+    int ns_single;    // 1: the current Newton-Schulz pair runs single-FP16 products
+    int ft_pad3;
     double sc[6];     // identity parts: A = sc I + A~ (W's in sc[kMatW0], shared by both W slots)
     double fb[6];     // bounds on ||A~||_F (slice scales are derived from them)
     float scl[6];     // slice scale s of each slot's FP16 slices (slices hold s A~)
@@ -189,6 +193,9 @@ struct SolveState {
     // outputs
     double e_band, trace, idem_fro, mu;
     double pad[4];
+    // kinds of the steps issued, in order (profiling hook)
+    int nctl, nctl_pad;
+    unsigned char kind_log[kKindLog];
     // per-step record written by the control kernel (read back with the state):
     // phase, branch, t1 - N_e, t1 - t2, ||X^2 - X||_F of the last product's input, RelTr
     double hist[kHistRows][kHistCols];

@@ -479,23 +479,29 @@ __device__ void control_trfoe(SolveState *st, double trV, double sumsq) {
 enum FtSub : int { kFtStart = 0, kFtSquare = 1, kFtShiftElem = 2, kFtMW = 3, kFtWR = 4, kFtNW = 5,
                    kFtFinal = 6 };
 
-// Newton-Schulz steps after the closed-form first iterate so that the
-// residual bound r0^(2^(j+1)) falls below 3e-8.  The residual leaves each
-// eigenvalue's z'' short by at most that fraction.  The doubling map never
-// raises a relative error (d ln f / d ln z = (1 - z^2)/(1 + z^2) <= 1) and
-// nearly erases it where |z| is close to 1, so the saturated states carry
-// only the last stage's residual, D moves by about half of it, and tr D is
-// restored by the closing shift steps: 3e-8 stays well inside the 1e-6
-// (D) and 1e-7 (band energy per electron) tolerances.
-__device__ int ns_steps(double mmin, double mmax) {
+// Newton-Schulz steps W <- W (2 I - M W) after the closed-form first
+// iterate run until the residual bound, r0^2 after that iterate (r0 =
+// (m_max - m_min)/(m_max + m_min)) and squared by every step, falls below
+// 3e-8.  The residual leaves each eigenvalue's z'' short by at most that
+// fraction.  The doubling map never raises a relative error
+// (d ln f / d ln z = (1 - z^2)/(1 + z^2) <= 1) and nearly erases it where |z|
+// is close to 1, so the saturated states carry only the last stage's
+// residual, D moves by about half of it, and tr D is restored by the closing
+// shift steps: 3e-8 stays well inside the 1e-6 (D) and 1e-7 (band energy per
+// electron) tolerances.
+//
+// The iteration corrects itself: a step's rounding error e only leaves a
+// residual of about e for the next step to square.  So under the mixed
+// policy the pairs whose input bound is still >= 0.05 run as single-FP16
+// products (one MMA instead of three), which leave a residual of at most
+// about 2^-10 kappa(M) <= 4e-3 (kappa <= 2 here) besides the square of their
+// input; the remaining pairs are split-FP16 and bring the bound under 3e-8.
+constexpr double kNsTarget = 3e-8, kNsSingleAbove = 0.05, kNsSingleFloor = 4e-3;
+constexpr int kNsMaxSteps = 12;
+
+__device__ double ns_residual0(double mmin, double mmax) {
     const double r0 = (mmax - mmin) / (mmax + mmin);
-    double r = r0 * r0;
-    int j = 0;
-    while (r > 3e-8 && j < 12) {
-        r = r * r;
-        ++j;
-    }
-    return j;
+    return r0 * r0;
 }
 
 __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1) {
@@ -542,13 +548,18 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
 
     // ---- Newton-Schulz inner steps
     if (sub == kFtSquare || sub == kFtShiftElem || sub == kFtWR) {
-        if (sub == kFtWR) st->ft_j += 1;
-        if (st->ft_j < st->ft_nj) {
+        if (sub == kFtWR) {
+            st->ft_j += 1;
+            const double r2 = st->ns_r * st->ns_r;
+            st->ns_r = st->ns_single ? fmax(r2, kNsSingleFloor) : r2;
+        }
+        if (st->ns_r > kNsTarget && st->ft_j < kNsMaxSteps) {
             // R = M W:  R~ = v + Mc W~ + Wc M~,  Rc = Mc Wc
             const double Mc = sc[M], Wc = sc[WS];
             fb[R] = fb[M] * fb[W] + fabs(Mc) * fb[W] + fabs(Wc) * fb[M];
             sc[R] = Mc * Wc;
-            st->kind = kTcSplit;
+            st->ns_single = (st->prec == kPrecMixed && st->ns_r >= kNsSingleAbove) ? 1 : 0;
+            st->kind = st->ns_single ? kTcSingle : kTcSplit;
             begin_op(op, M, W, W, M, 1.0 / (static_cast<double>(scl[M]) * scl[W]));
             op.nout = 1;
             set_out(op.out[0], R, kOutMaster | kOutSlices, 1.0, Mc, Wc, 0.0, fb[R]);
@@ -577,7 +588,7 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
         const int Wn = (W == kMatW0) ? kMatW1 : kMatW0;
         fb[Wn] = fabs(2.0 - Rc) * fb[W] + fabs(Wc) * fb[R] + fb[W] * fb[R];
         sc[WS] = Wc * (2.0 - Rc);
-        st->kind = kTcSplit;
+        st->kind = st->ns_single ? kTcSingle : kTcSplit;
         begin_op(op, W, R, W, R, 1.0 / (static_cast<double>(scl[W]) * scl[R]));
         op.nout = 1;
         set_out(op.out[0], Wn, kOutMaster | kOutSlices, -1.0, 2.0 - Rc, -Wc, 0.0, fb[Wn]);
@@ -644,6 +655,7 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
     st->ft_t = t;
     st->mu_t += 2.0 * b / beta_k;
     st->ft_j = 0;
+    st->ns_single = 0;
     const double fz = fb[Z];
     if (!shift_only) {
         st->ft_shifts = 0;
@@ -660,7 +672,7 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
                                                                  : fmin(m_p, m_m);
         const double w0 = 2.0 / (mmin + mmax);
         st->w0 = w0;
-        st->ft_nj = ns_steps(mmin, mmax);
+        st->ns_r = ns_residual0(mmin, mmax);
         const double bM1 = 2.0 * (1.0 + t2) * zc - 4.0 * t;  // M~ = (1 + t^2) v + bM1 z~
         const double bN1 = 2.0 * (1.0 + t2) - 4.0 * t * zc;  // N~ = -2t v + bN1 z~
         fb[M] = (1.0 + t2) * fz * fz + fabs(bM1) * fz;
@@ -689,7 +701,7 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
         const double mmin = 1.0 - fabs(t) * rho, mmax = 1.0 + fabs(t) * rho;
         const double w0 = 2.0 / (mmin + mmax);
         st->w0 = w0;
-        st->ft_nj = ns_steps(mmin, mmax);
+        st->ns_r = ns_residual0(mmin, mmax);
         fb[M] = fabs(t) * fz;
         fb[N] = fz;
         fb[W] = w0 * w0 * fb[M];
@@ -764,10 +776,16 @@ __device__ void control_one(const MmaProb &pr, const DevCtl *ctl) {
         st->kind = kNone;
         return;
     }
-    if (st->chk_left > 0 || st->chk) control_check(st, s_a[0], s_b[0]);
-    else if (st->method == kMethodFermi) control_fermi(st, s_a[0], s_b[0], s_c[0]);
+    if (st->chk_left > 0 || st->chk) {
+        control_check(st, s_a[0], s_b[0]);
+        return;
+    }
+    if (st->method == kMethodFermi) control_fermi(st, s_a[0], s_b[0], s_c[0]);
     else if (st->method == kMethodTrfoe) control_trfoe(st, s_a[0], s_b[0]);
     else control_sp2(st, s_a[0], s_b[0], s_d[0]);
+    // the kind of every step issued (step k runs in the k-th pass of the step loop)
+    if (st->nctl < kKindLog) st->kind_log[st->nctl] = static_cast<unsigned char>(st->done ? kNone : st->kind);
+    st->nctl += 1;
 }
 
 }  // namespace

@@ -331,16 +331,25 @@ __global__ void __launch_bounds__(256) k_gemm_reduce(const GemmArgs *__restrict_
 
 // max |X_ij| over a rows x cols block (ld) as the bit pattern of a
 // non-negative FP64 value (ordered like the value), atomically into *out.
+// Block b takes rows b, b + grid, ...; threads stride the columns, four
+// loads in flight each.
 __global__ void __launch_bounds__(256) k_absmax(const double *__restrict__ X, long long rows, long long cols,
                                                 long long ld, unsigned long long *out) {
     constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
     unsigned long long m = 0;
-    const long long total = rows * cols;
-    for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long r = e / cols, c = e - r * cols;
-        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(X[r * ld + c])) & kAbs;
-        m = b > m ? b : m;
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const double *row = X + r * ld;
+        long long c = t;
+        for (; c + 3 * nt < cols; c += 4 * nt) {
+            const unsigned long long b0 = static_cast<unsigned long long>(__double_as_longlong(row[c])) & kAbs;
+            const unsigned long long b1 = static_cast<unsigned long long>(__double_as_longlong(row[c + nt])) & kAbs;
+            const unsigned long long b2 = static_cast<unsigned long long>(__double_as_longlong(row[c + 2 * nt])) & kAbs;
+            const unsigned long long b3 = static_cast<unsigned long long>(__double_as_longlong(row[c + 3 * nt])) & kAbs;
+            m = max(max(m, max(b0, b1)), max(b2, b3));
+        }
+        for (; c < cols; c += nt)
+            m = max(m, static_cast<unsigned long long>(__double_as_longlong(row[c])) & kAbs);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -350,47 +359,75 @@ __global__ void __launch_bounds__(256) k_absmax(const double *__restrict__ X, lo
     if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
+namespace {
+
+__device__ __forceinline__ void split_pair(double x0, double x1, float s, __half2 &h, __half2 &l) {
+    const double y0 = x0 * static_cast<double>(s), y1 = x1 * static_cast<double>(s);
+    h = __floats2half2_rn(static_cast<float>(y0), static_cast<float>(y1));
+    const float2 back = __half22float2(h);
+    l = __floats2half2_rn(static_cast<float>(y0 - static_cast<double>(back.x)),
+                          static_cast<float>(y1 - static_cast<double>(back.y)));
+}
+
+}  // namespace
+
 // FP16 slices hi = fp16(s x), lo = fp16(s x - hi) of a rows x cols FP64 block,
-// s from *amax.  transpose = 0: out[r][c] (ld lds); transpose = 1:
-// out[c][r], through a 32 x 32 shared-memory tile so that both the FP64 reads
-// and the FP16 writes are coalesced.  Blocks of 32 x 8 threads.
+// s from *amax.
+// transpose = 0: out[r][c] (ld lds): block b takes rows b, b + grid, ...,
+// each thread a pair of columns per pass (one 4-byte store per slice).
+// transpose = 1: out[c][r]: 64 x 64 tiles through shared memory (stored by
+// column, so that an output row of the tile is 64 consecutive values: 128
+// bytes per slice and warp).  Blocks of 256 threads.
 __global__ void __launch_bounds__(256) k_split_rows(const double *__restrict__ X, long long rows, long long cols,
                                                     long long ld, const unsigned long long *amax, __half *hi,
                                                     __half *lo, long long lds, int transpose) {
-    __shared__ double t[32][33];
+    __shared__ double t[64][65];
     const float s = static_cast<float>(slice_scale_of(*amax));
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const long long tiles_c = (cols + 31) / 32;
-    const long long ntiles = ((rows + 31) / 32) * tiles_c;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long r0 = (tile / tiles_c) * 32, c0 = (tile % tiles_c) * 32;
-        if (!transpose) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const long long r = r0 + ty + 8 * k, c = c0 + tx;
-                if (r < rows && c < cols) {
-                    const double x = X[r * ld + c] * static_cast<double>(s);
-                    const __half h = __float2half_rn(static_cast<float>(x));
-                    hi[r * lds + c] = h;
-                    lo[r * lds + c] = __float2half_rn(static_cast<float>(x - static_cast<double>(__half2float(h))));
-                }
+    const int tid = threadIdx.x;
+    if (!transpose) {
+        for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+            const double *row = X + r * ld;
+            __half2 *h2 = reinterpret_cast<__half2 *>(hi + r * lds);
+            __half2 *l2 = reinterpret_cast<__half2 *>(lo + r * lds);
+            for (long long c = 2 * tid; c < cols; c += 2 * blockDim.x) {
+                const double x0 = row[c], x1 = (c + 1 < cols) ? row[c + 1] : 0.0;
+                __half2 h, l;
+                split_pair(x0, x1, s, h, l);
+                h2[c >> 1] = h;  // lds is even: the pair (c, c + 1) is one aligned 4-byte word
+                l2[c >> 1] = l;
             }
-            continue;
         }
+        return;
+    }
+    const int tx = tid & 31, ty = tid >> 5;  // 32 x 8
+    const long long tiles_c = (cols + 63) / 64;
+    const long long ntiles = ((rows + 63) / 64) * tiles_c;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long r0 = (tile / tiles_c) * 64, c0 = (tile % tiles_c) * 64;
+        // load 64 rows x 64 columns (two columns per lane), keep them by column
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long r = r0 + ty + 8 * k, c = c0 + tx;
-            t[ty + 8 * k][tx] = (r < rows && c < cols) ? X[r * ld + c] : 0.0;
+        for (int k = 0; k < 8; ++k) {
+            const long long r = r0 + ty + 8 * k;
+            const long long c = c0 + 2 * tx;
+            double x0 = 0.0, x1 = 0.0;
+            if (r < rows) {
+                if (c < cols) x0 = X[r * ld + c];
+                if (c + 1 < cols) x1 = X[r * ld + c + 1];
+            }
+            t[2 * tx][ty + 8 * k] = x0;
+            t[2 * tx + 1][ty + 8 * k] = x1;
         }
         __syncthreads();
+        // output rows c0 .. c0 + 63, columns r0 .. r0 + 63: two columns per lane
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long c = c0 + ty + 8 * k, r = r0 + tx;  // out row c, column r
-            if (r < rows && c < cols) {
-                const double x = t[tx][ty + 8 * k] * static_cast<double>(s);
-                const __half h = __float2half_rn(static_cast<float>(x));
-                hi[c * lds + r] = h;
-                lo[c * lds + r] = __float2half_rn(static_cast<float>(x - static_cast<double>(__half2float(h))));
+        for (int k = 0; k < 8; ++k) {
+            const long long c = c0 + ty + 8 * k;
+            const long long r = r0 + 2 * tx;
+            if (c < cols && r < rows) {
+                __half2 h, l;
+                split_pair(t[ty + 8 * k][2 * tx], t[ty + 8 * k][2 * tx + 1], s, h, l);
+                reinterpret_cast<__half2 *>(hi + c * lds)[r >> 1] = h;  // lds even, r even
+                reinterpret_cast<__half2 *>(lo + c * lds)[r >> 1] = l;
             }
         }
         __syncthreads();

@@ -644,13 +644,17 @@ def kernel_table(prec, kT, n, rp, prof, kinds, peaks, peak_kind, workload):
     ms_sp, n_sp = kinds["split_fp16"]
     ms_si, n_si = kinds["single_fp16"]
     ms_ep, n_ep = kinds["epilogue_only"]
-    tc_ms = ms_sp + ms_si
-    tc_flops = (3 * n_sp + n_si) * sym_flops
+    ms_dl, n_dl = kinds.get("polish_delta", (0.0, 0))
+    # the second product of a polishing pair is a split product too (Delta0 S)
+    tc_ms = ms_sp + ms_si + ms_dl
+    tc_flops = (3 * (n_sp + n_dl) + n_si) * sym_flops
     kernels = {
-        "k_sym_mma": {"launches": n_sp + n_si, "split_launches": n_sp, "single_launches": n_si,
-                      "ms_total": tc_ms, "ms_avg": tc_ms / max(n_sp + n_si, 1),
+        "k_sym_mma": {"launches": n_sp + n_si + n_dl, "split_launches": n_sp, "single_launches": n_si,
+                      "polish_delta_launches": n_dl,
+                      "ms_total": tc_ms, "ms_avg": tc_ms / max(n_sp + n_si + n_dl, 1),
                       "ms_avg_split": ms_sp / n_sp if n_sp else None,
                       "ms_avg_single": ms_si / n_si if n_si else None,
+                      "ms_avg_polish_delta": ms_dl / n_dl if n_dl else None,
                       "algorithmic_flops": tc_flops,
                       "achieved_tflops": tc_flops / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else 0},
     }
@@ -673,6 +677,11 @@ def kernel_table(prec, kT, n, rp, prof, kinds, peaks, peak_kind, workload):
             kernels[fp_name]["achieved_tflops"] = kernels[fp_name]["fp64_equivalent_tflops"]
     names = [k for k in ("k_sym_mma", fp_name) if k in kernels and kernels[k]["ms_total"] > 0]
     kernels["share_of_solve"] = {k: kernels[k]["ms_total"] / prof["solve_ms"] for k in names}
+    if kT == 0.0 and prec != "fp64":
+        # FP64-accurate polishing: digit products plus the pairs' split Delta products
+        pol = (ms_fp if n_fp else 0.0) + ms_dl
+        kernels["polish"] = {"ms_total": pol, "share_of_solve": pol / prof["solve_ms"],
+                             "digit_products": n_fp, "delta_products": n_dl}
     # a kernel timed inside a solve of a second or more runs under the
     # sustained (power-capped) clock; shorter solves take the burst peak
     sustained = prof["solve_ms"] >= 1000.0

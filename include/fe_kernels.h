@@ -83,7 +83,8 @@ FE_API int fe_k_profile_steps(fe_ctx *ctx, double *out, int max_steps, int *coun
  * batch), HOST out: ms8[k] milliseconds and n8[k] launches of kind k,
  * 1 single-FP16 tensor-core product, 2 split-FP16 product, 3 native FP64
  * product, 5 epilogue-only tensor-core step, 6 FP64-accurate digit product
- * (its digit split included); other entries 0. */
+ * (its digit split included), 7 second product of a polishing pair (split
+ * FP16, added to the FP64 iterate); other entries 0. */
 FE_API int fe_k_profile_kinds(fe_ctx *ctx, double *ms8, int *n8);
 
 /* Test hook (no counterpart in the paper): every following solve on ctx,

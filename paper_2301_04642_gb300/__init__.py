@@ -423,7 +423,8 @@ class Context:
         rc = self.L.fe_k_profile_kinds(self.h, ms, cnt)
         if rc != FE_OK:
             raise FeError(rc, self.last_error())
-        names = {1: "single_fp16", 2: "split_fp16", 3: "fp64", 5: "epilogue_only", 6: "digit"}
+        names = {1: "single_fp16", 2: "split_fp16", 3: "fp64", 5: "epilogue_only", 6: "digit",
+                 7: "polish_delta"}
         return {v: (ms[k], cnt[k]) for k, v in names.items()}
 
     def narrow_bounds(self, factor):

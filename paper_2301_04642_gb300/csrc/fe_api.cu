@@ -287,6 +287,7 @@ size_t slot_bytes(int n, int method, int *ldy, int *lds, int *ldx, size_t *npart
     add(8 * 3 * nn);                                 // Lanczos vectors
     if (method == kMethodSp2)
         for (int a = 0; a < kDigits; ++a) add(2 * nn * (*lds));  // digits of X/4
+    if (method == kMethodFermi) add(8 * kNumMats * nn);  // FP64 diagonals of the matrix slots
     add(8 * kPartStride * (*nparts));                // partials
     add(sizeof(SolveState));
     add(sizeof(RowInfo) * nn);
@@ -402,6 +403,7 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
     __half *digs[kDigits] = {};
     if (method == kMethodSp2)
         for (int a = 0; a < kDigits; ++a) digs[a] = reinterpret_cast<__half *>(take(2 * nn * lds));
+    double *diags = (method == kMethodFermi) ? reinterpret_cast<double *>(take(8 * kNumMats * nn)) : nullptr;
     s->part = reinterpret_cast<double *>(take(8 * kPartStride * nparts));
     s->st = reinterpret_cast<SolveState *>(take(sizeof(SolveState)));
     s->rowinfo = reinterpret_cast<RowInfo *>(take(sizeof(RowInfo) * nn));
@@ -441,6 +443,7 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
         s->hp.mats[kMatW0].master = masters[3];  // the two W slice sets share one master
         s->hp.mats[kMatW1].master = masters[3];
         s->hp.mats[kMatR].master = masters[4];
+        for (int m = 0; m < kNumMats; ++m) s->hp.dg[m] = diags + static_cast<size_t>(m) * nn;
     } else {
         s->hp.mats[kMatY0].master = masters[0];  // both slice sets of Y share the master
         s->hp.mats[kMatY1].master = masters[0];
@@ -588,7 +591,7 @@ void init_state(const fe_ctx *ctx, const fe_problem *p, SolveState *st) {
     if (st->method == kMethodFermi) {
         st->max_iters = kFermiMaxSteps;
         st->wcur = kMatW0;
-        st->ft_sub = 0;  // z0 fresh
+        st->ft_sub = 0;  // x ready: the control starts with the tanh polynomial
     }
 }
 // ---------------------------------------------------------------- engine
@@ -1157,7 +1160,7 @@ int run_problems_once(fe_ctx *ctx, const std::vector<Job> &jobs, fe_result *rs) 
             const int kd = s0.kind_log[it];
             if (kd <= kNone || kd > 7) continue;
             float a = 0;
-            const bool tc = (kd == kTcSingle || kd == kTcSplit || kd == kTcElem);
+            const bool tc = (kd == kTcSingle || kd == kTcSplit || kd == kTcElem || kd == kTcDelta);
             cudaEventElapsedTime(&a, ctx->pev[4 * it + (tc ? 0 : 2)], ctx->pev[4 * it + (tc ? 1 : 3)]);
             ctx->prof_kind_ms[kd] += a;
             ctx->prof_kind_n[kd] += 1;

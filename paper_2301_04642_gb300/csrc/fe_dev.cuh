@@ -95,11 +95,13 @@ constexpr int kHistCols = 6;
 
 // ---------------------------------------------------------------- state
 // Which kernel does the step: the tensor-core kernel (kTcSingle / kTcSplit:
-// one or two FP16 slices per operand; kTcElem: no product, epilogue only),
-// the FP64-accurate SIMT kernel (kFp64 native, kDf double-float), or the
-// FP64-accurate digit product on the tensor cores (kDigit).
+// one or two FP16 slices per operand; kTcElem: no product, epilogue only;
+// kTcDelta: the second product of an FP64-accurate polishing pair, a split
+// product of small matrices added to the FP64 iterate), the FP64-accurate
+// SIMT kernel (kFp64 native, kDf double-float), or the FP64-accurate digit
+// product on the tensor cores (kDigit).
 enum Kind : int { kNone = 0, kTcSingle = 1, kTcSplit = 2, kFp64 = 3, kDf = 4, kTcElem = 5,
-                  kDigit = 6 };
+                  kDigit = 6, kTcDelta = 7 };
 enum Phase : int { kPhaseSingle = 0, kPhaseSplit = 1, kPhaseFp64 = 2, kPhaseDone = 3 };
 enum Prec : int { kPrecMixed = 0, kPrecFp64 = 1, kPrecFp32 = 2, kPrecTryFp16 = 3 };
 // kMethodSp2 also runs the accelerated form (SolveState::acc_on); kMethodTrfoe
@@ -108,13 +110,29 @@ enum Method : int { kMethodSp2 = 0, kMethodFermi = 1, kMethodTrfoe = 2 };
 
 // Output of one tensor-core step: value = a v + b1 E1 + b2 E2 + c [i == j],
 // v the product (A~ B~)_ij, E1/E2 FP32 masters of the epilogue inputs.
-enum OutFlags : int { kOutMaster = 1, kOutSlices = 2, kOutF64a = 4, kOutF64b = 8 };
+// kOutF64Add (with kOutF64a or kOutF64b) adds the entry of the other FP64
+// buffer: Xd[1] for an output to Xd[0] and the reverse.
+// kOutDiag: the diagonal form of the finite-temperature matrices, A =
+// diag(d_A) + A~ with d_A an FP64 vector and A~ zero on the diagonal.  Off
+// the diagonal the E terms take per-row / per-column coefficients
+//     (b1 + g1r d_V1[i] + g1c d_V1[j]) E1 + (b2 + g2r d_V2[i] + g2c d_V2[j]) E2,
+// and the diagonal entry, with v_ii the product's, is
+//     c + a v_ii + q d_X[i] d_Y[i] + l1 d_X[i] + l2 d_Y[i],
+// written to d_mat (FP64) while the small part's diagonal is stored as 0; an
+// FP64 output (kOutF64a/b) writes it into the FP64 matrix instead.
+enum OutFlags : int { kOutMaster = 1, kOutSlices = 2, kOutF64a = 4, kOutF64b = 8, kOutF64Add = 16,
+                      kOutDiag = 32 };
 struct OutSpec {
     int mat;     // target matrix slot (master and/or slices)
     int flags;   // OutFlags
     float a, b1, b2;
     float s;     // slice scale of the target
     double c;    // diagonal term, FP64 (exact for the FP64 outputs)
+    // kOutDiag only: coefficient vectors of E1/E2 and the diagonal formula
+    int v1, v2;                 // slots whose d vectors scale E1 / E2 (-1: none)
+    float g1r, g1c, g2r, g2c;
+    int dx, dy;                 // slots of the diagonal formula's d vectors (-1: none)
+    double q, l1, l2;
 };
 struct ProdOp {
     int A, B;      // operand matrix slots (A~ and B~ slices)
@@ -141,6 +159,7 @@ struct SolveState {
     int ft_m, ft_stage, ft_sub, ft_j, ft_nj, ft_shifts, wcur, ft_phase;
     int ft_last_mat, ft_pad2;  // slot whose ||.||_F the last step's partials report
     double ns_r;      // Newton-Schulz: bound on the residual ||I - M W|| of the current W
+    double ns_mmin, ns_mmax;  // bounds on the spectrum of the current M
     int ns_single;    // 1: the current Newton-Schulz pair runs single-FP16 products
     int ft_pad3;
     double sc[6];     // identity parts: A = sc I + A~ (W's in sc[kMatW0], shared by both W slots)
@@ -174,6 +193,12 @@ struct SolveState {
     float s_next;       // slice scale of the zero-temperature iterate after this step
     double c_next;
     double gamma;       // FP64-accurate step: X' = F(X) + gamma (X - X^2) (trace correction)
+    // polishing pair (mixed policy): the first, FP64-accurate product also
+    // writes the slices of Delta0 = X0^2 - X0 (scale pol_sD, slot Y0) and of S
+    // (scale pol_sS, slot Y1); the second is X2 = X1 + pol_kappa Delta0 S
+    int pol_emit, pol_pad;
+    float pol_sD, pol_sS;
+    double pol_kappa;
     // accelerated SP2 (A-Z-RFOE): with acc_on the unoccupied eigenvalues of X
     // lie in [acc_a, ...] = [0, acc_a] and the occupied ones in [acc_b, 1];
     // homo/lumo are the caller's estimates (host), acc_*_next the interval

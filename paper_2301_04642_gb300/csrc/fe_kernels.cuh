@@ -8,8 +8,9 @@ namespace fe {
 
 // One symmetric n x n matrix as the tensor-core kernel sees it: FP16 slices
 // (hi, lo) of s * A~ with their TMA descriptors, and optionally the FP32 master
-// A~.  Every matrix of the expansion is kept as (FP64 scalar) I + A~; the
-// scalar lives in the solve state.
+// A~.  Zero temperature keeps (FP64 scalar) I + A~, the scalar in the solve
+// state; finite temperature keeps diag(d) + A~ with d an FP64 vector
+// (MmaProb::dg) and A~ zero on the diagonal.
 struct MatSlot {
     CUtensorMap tmA[kMaxSlices];  // box 64 (K) x 128 rows
     CUtensorMap tmB[kMaxSlices];  // box 64 (K) x 256 rows
@@ -47,6 +48,7 @@ struct MmaProb {
     CUtensorMap dB[kDigits];         // box 32 (K) x 64 rows
     __half *dig[kDigits];
     int ntilesD, padD;
+    double *dg[kNumMats];            // finite T: FP64 diagonals of the matrix slots (n each)
 };
 
 // One tensor-core tile: rows [I*128, I*128+128) x columns [Jp*bn, Jp*bn+bn)
@@ -124,14 +126,14 @@ __device__ __forceinline__ void setup_from_bounds(const MmaProb &pr, SolveState 
     st->xcur = 0;
     st->x_fp64 = (st->prec == kPrecFp64) ? 1 : 0;
     if (st->method == kMethodFermi) {
-        // z0 = (beta0 / 2)(H - mu0 I) with mu0 = tr H / n and the number of
-        // doublings m chosen so that |z0| <= t0 = 1e-3 on the bound interval:
-        // then z0 = tanh(beta0 (H - mu0)/2) to a relative 1e-7/3 in the
-        // logit, an error the doublings carry over unchanged.
+        // x = (beta0 / 2)(H - mu0 I) with mu0 = tr H / n and the number of
+        // doublings m chosen so that |x| <= t0 = 1/4 on the bound interval;
+        // the control's first five products turn x into z0 = tanh(x) (odd
+        // Taylor polynomial through x^11, truncation below 5.4e-11).
         const double mu0 = trH / n;
         const double rad = fmax(fabs(lo - mu0), fabs(hi - mu0));
         const double beta = 1.0 / st->kT;
-        const double t0 = 1e-3;
+        const double t0 = 0.25;
         int m = 0;
         if (beta * rad / 2.0 > t0) m = static_cast<int>(ceil(log2(beta * rad / (2.0 * t0))));
         st->beta = beta;

@@ -15,8 +15,10 @@
 //     is nearer N_e), else 2X - X^2.
 //
 // Finite temperature (Sec. II-A Fermi-Dirac target, recursive expansion of
-// Sec. II-B3): z = I - 2D = tanh(beta (H - mu)/2).  Starting from the
-// linearised z0 = (beta0/2)(H - mu0 I) at beta0 = beta / 2^m, every stage
+// Sec. II-B3): z = I - 2D = tanh(beta (H - mu)/2).  Starting from
+// z0 = tanh((beta0/2)(H - mu0 I)) at beta0 = beta / 2^m (the paper's
+// expansion starts from the linear term; here five products evaluate a
+// Taylor polynomial of tanh instead, see control_fermi_start), every stage
 // doubles beta with the double-angle identity of tanh, folding in a shift of
 // mu (logit shift b, t = tanh b) chosen by a Newton step so that tr D tracks
 // N_e at every temperature:
@@ -32,8 +34,9 @@
 // Q = (I - z^2)/4 = D0 - D0^2 in FP64; the output kernel forms
 // D = D0 + gamma Q with gamma fixed so that tr D = N_e exactly (a first-order
 // shift of mu, since dD/dmu = beta D (I - D)).
-// All matrices are kept as (FP64 scalar) I + (FP32 small part); every
-// product is a split-FP16 tensor-core product of the small parts.
+// All matrices are kept as diag(FP64 vector) + (FP32 small part, zero on the
+// diagonal); every product is a split-FP16 tensor-core product of the small
+// parts (see the diagonal form below).
 #include <cfloat>
 
 #include "fe_dev.cuh"
@@ -60,6 +63,9 @@ __device__ void set_out(OutSpec &o, int mat, int flags, double a, double b1, dou
     o.b2 = static_cast<float>(b2);
     o.c = c;
     o.s = slice_scale(bound);
+    o.v1 = o.v2 = o.dx = o.dy = -1;
+    o.g1r = o.g1c = o.g2r = o.g2c = 0.0f;
+    o.q = o.l1 = o.l2 = 0.0;
 }
 
 __device__ void begin_op(ProdOp &op, int A, int B, int E1, int E2, double inv) {
@@ -140,10 +146,11 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
         st->c = st->c_next;
         st->s_cur = st->s_next;
         st->cur ^= 1;
-    } else if (prev_kind == kFp64 || prev_kind == kDf || prev_kind == kDigit) {
+    } else if (prev_kind == kFp64 || prev_kind == kDf || prev_kind == kDigit || prev_kind == kTcDelta) {
         st->xcur ^= 1;
         st->x_fp64 = 1;
     }
+    st->pol_emit = 0;
     if (st->acc_fold) {
         st->acc_a = st->acc_a_next;
         st->acc_b = st->acc_b_next;
@@ -238,7 +245,8 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
             if (st->prec == kPrecFp32) done = true;
             else phase = kPhaseFp64;
         }
-    } else if (phase == kPhaseFp64 && (prev_kind == kFp64 || prev_kind == kDf || prev_kind == kDigit)) {
+    } else if (phase == kPhaseFp64 &&
+               (prev_kind == kFp64 || prev_kind == kDf || prev_kind == kDigit || prev_kind == kTcDelta)) {
         const int nfp64 = st->it_phase[kPhaseFp64];
         if (st->prec == kPrecFp64) {
             const bool idem_ok = fabs(idem) <= 2e-10 ||
@@ -256,8 +264,13 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
             // from then on a single product may end the phase (the SP2 rule
             // picks the branch that squares the side holding the trace
             // error, e.g. one slowly converging eigenvalue next to the gap).
+            // t1 and t2 are both about N_e and carry the rounding of their
+            // FP64 sums (measured: 11 ulp(N_e) below zero at n = 16040), so
+            // the sign test on their difference allows N_e 2^-46 (64 to 128
+            // ulp of N_e).
             const double f0 = st->fro_hist[0];
-            const bool idem_small = idem >= -1e-12 && idem <= 5e-9;
+            const double idem_floor = -fmax(1e-12, ldexp(fmax(ne, 1.0), -46));
+            const bool idem_small = idem >= idem_floor && idem <= 5e-9;
             const bool trace_ok = fabs(t1 - ne) <= 5e-10;
             const bool pair_ok = (nfp64 & 1) == 0 ? f0 * f0 <= 5e-9 : true;
             if (nfp64 >= 2 && idem_small && trace_ok && pair_ok) {
@@ -316,8 +329,44 @@ __device__ void control_sp2(SolveState *st, double trV, double sumsq, double rsq
     st->phase = phase;
     st->acc_fold = 0;
     if (phase == kPhaseFp64) {
-        st->kind = (st->prec == kPrecFp64) ? kFp64 : kDigit;
         st->acc_on = 0;  // the FP64-accurate steps are plain SP2 (a and 1 - b are ~0 by now)
+        if (st->prec == kPrecFp64) {
+            st->kind = kFp64;
+        } else if ((st->it_phase[kPhaseFp64] & 1) == 0) {
+            // First product of a polishing pair: FP64-accurate, X1 = F_A(X0).
+            // Its epilogue also writes the slices of Delta0 = X0^2 - X0 and of
+            // S = 2 X0 + Delta0 (X^2 branch) or 2I - 2 X0 + Delta0.  Slice
+            // scales from bounds on the spectral norms (entries are below
+            // them): |S| <= 2 max|x| + ||Delta0|| < 4; X0 = F(X_in) doubles
+            // the deviations of X_in on one side (||.||_F <= fro_hist[0]) and
+            // squares them on the other, plus the rounding of the product
+            // that made X0: at most 2^-19 n for a split product (entries of
+            // Y^2 within 2^-20 of exact, FP32 master), 2^-40 n once FP64.
+            st->kind = kDigit;
+            st->pol_emit = 1;
+            const double f = st->fro_hist[0];
+            const double bD = 4.0 * f + f * f + ldexp(nn, st->x_fp64 ? -40 : -19);
+            st->pol_sD = slice_scale(bD);
+            st->pol_sS = slice_scale(4.0);
+        } else {
+            // Second product of the pair, with Delta0 and X0 commuting:
+            //   X1 = X0^2 = X0 + Delta0     ->  Delta1 = X1^2 - X1 = Delta0 (2 X0 + Delta0)
+            //   X1 = 2 X0 - X0^2 = X0 - Delta0 -> Delta1 = Delta0 (2I - 2 X0 + Delta0)
+            // and F_B(X1) + gamma (X1 - X1^2) = X1 + kappa Delta1 with
+            // kappa = 1 - gamma (X^2 branch) or -1 - gamma (2X - X^2).
+            // Delta0 is small, so the split-FP16 product gives Delta1 to
+            // ~2^-21 of |Delta0| |S|, an absolute error far below the FP64
+            // iterate's tolerance; X1 + kappa Delta1 is formed in FP64.
+            st->kind = kTcDelta;
+            st->pol_kappa = sq ? 1.0 - st->gamma : -1.0 - st->gamma;
+            ProdOp &op = st->op;
+            begin_op(op, kMatY0, kMatY1, -1, -1, 1.0 / (static_cast<double>(st->pol_sD) * st->pol_sS));
+            op.nout = 1;
+            set_out(op.out[0], kMatY0, kOutF64Add | ((st->xcur ^ 1) == 0 ? kOutF64a : kOutF64b),
+                    st->pol_kappa, 0.0, 0.0, 0.0, 1.0);
+            op.part_out = 0;
+            op.ra = 1.0f;  // ||Delta1||_F^2 = ||X1^2 - X1||_F^2 of this product's input
+        }
     } else {
         st->kind = (phase == kPhaseSingle) ? kTcSingle : kTcSplit;
         // The step's polynomial, folded over the interval that has to shrink
@@ -477,7 +526,161 @@ __device__ void control_trfoe(SolveState *st, double trV, double sumsq) {
 // ------------------------------------------------------------------ finite T
 // ft_sub names the step that was issued last; kFtStart is the state after X0.
 enum FtSub : int { kFtStart = 0, kFtSquare = 1, kFtShiftElem = 2, kFtMW = 3, kFtWR = 4, kFtNW = 5,
-                   kFtFinal = 6 };
+                   kFtFinal = 6, kFtPoly1 = 7, kFtPoly2 = 8, kFtPoly3 = 9, kFtPoly4 = 10, kFtPoly5 = 11,
+                   kFtPoly6 = 12 };
+
+// Finite-temperature matrices are kept in the diagonal form A = diag(d_A) +
+// A~ (d_A FP64, A~ FP32 master + FP16 slices, zero on the diagonal; the
+// kOutDiag epilogue).  With both operands in that form
+//     (A B)_ij = d_A[i] B~_ij + A~_ij d_B[j] + (A~ B~)_ij   (i != j),
+//     (A B)_ii = d_A[i] d_B[i] + (A~ B~)_ii,
+// so every output is the product v = A~ B~ plus E terms with per-row or
+// per-column coefficients, and its diagonal is formed in FP64.  Why: near
+// the Fermi level the Fermi function's slope beta/4 amplifies an absolute
+// error of the logit, and with (scalar) I + A~ the diagonal entries of A~
+// are O(1) (A's diagonal minus its mean), so their FP32/FP16 rounding is an
+// absolute 2^-23..2^-24 on every eigenvalue whose eigenvector is localised
+// (Hp close to diagonal, as late in a self-consistent cycle).  In a CPU
+// emulation with the kernels' slicing (n = 800, kT = 1.2 mHa, reflector Q)
+// ||D - D_ref||_F / sqrt(N_e) was 9.5e-7 in the scalar form and 3.6e-8 in
+// the diagonal form (1.5e-7 and 8.7e-8 for a Haar Q).
+//
+// Slice scales come from spectral bounds of the full matrices: entries of
+// the off-diagonal part A~ are below ||A~||_2 <= 2 ||A||_2.
+__device__ float ft_scale(double spec) { return slice_scale(2.5 * spec + 1e-6); }
+
+// E-term coefficients and the diagonal formula of a diagonal-form output
+__device__ void set_e(OutSpec &o, int v1, double b1, double g1r, double g1c, int v2, double b2, double g2r,
+                      double g2c) {
+    o.flags |= kOutDiag;
+    o.v1 = v1;
+    o.b1 = static_cast<float>(b1);
+    o.g1r = static_cast<float>(g1r);
+    o.g1c = static_cast<float>(g1c);
+    o.v2 = v2;
+    o.b2 = static_cast<float>(b2);
+    o.g2r = static_cast<float>(g2r);
+    o.g2c = static_cast<float>(g2c);
+}
+__device__ void set_d(OutSpec &o, double c, int dx, int dy, double q, double l1, double l2) {
+    o.flags |= kOutDiag;
+    o.c = c;
+    o.dx = dx;
+    o.dy = dy;
+    o.q = q;
+    o.l1 = l1;
+    o.l2 = l2;
+}
+// output = a v + E terms; diagonal c + a v_ii + q d_X d_Y + l1 d_X + l2 d_Y
+__device__ void out_d(OutSpec &o, int mat, int flags, double a, double spec) {
+    o.mat = mat;
+    o.flags = flags | kOutDiag;
+    o.a = static_cast<float>(a);
+    o.b1 = o.b2 = 0.0f;
+    o.g1r = o.g1c = o.g2r = o.g2c = 0.0f;
+    o.v1 = o.v2 = o.dx = o.dy = -1;
+    o.c = o.q = o.l1 = o.l2 = 0.0;
+    o.s = ft_scale(spec);
+}
+// the product of two diagonal-form matrices A B (commuting, so symmetric):
+// E1 = B~ scaled by d_A per row, E2 = A~ scaled by d_B per column
+__device__ void prod_terms(OutSpec &o, int A, int B, double a) {
+    set_e(o, A, 0.0, a, 0.0, B, 0.0, 0.0, a);
+    set_d(o, 0.0, A, B, a, 0.0, 0.0);
+}
+
+// The start z0 = tanh(x), x = (beta0/2)(H - mu0 I) with ||x||_2 <= 1/4 on the
+// bound interval, from the odd Taylor polynomial of tanh through x^11 in
+// Horner form in y = x^2:
+//   tanh x = x P,  P = c0 + y T2,  T2 = c1 + y T3,  T3 = c2 + y T4,
+//   T4 = c3 + y T5,  T5 = c4 + c5 y
+// (the next term, 21844/6081075 x^13, is below 5.4e-11 at |x| = 1/4).  Six
+// split-FP16 products replace the eight doublings from |x| <= 1e-3 to 1/4.
+//   1: Y = x x -> M, T5 -> N, copy of x -> R     2: T4 = c3 + Y T5 -> W0
+//   3: T3 = c2 + Y T4 -> N     4: T2 = c1 + Y T3 -> W0     5: P = c0 + Y T2 -> N
+//   6: z0 = x P -> Z
+__device__ double tanh_coef(int k) {
+    switch (k) {
+        case 0: return 1.0;
+        case 1: return -1.0 / 3.0;
+        case 2: return 2.0 / 15.0;
+        case 3: return -17.0 / 315.0;
+        case 4: return 62.0 / 2835.0;
+        default: return -1382.0 / 155925.0;
+    }
+}
+
+__device__ void control_fermi_start(SolveState *st, int sub) {
+    float *scl = st->scl;
+    ProdOp &op = st->op;
+    const int Z = kMatZ, N = kMatN, M = kMatM, W0 = kMatW0, X = kMatR;
+    // r bounds ||x||_2 (bound interval about mu0)
+    const double r = 0.5 * st->beta0 * fmax(fabs(st->emax - st->mu_t), fabs(st->emin - st->mu_t));
+    const double r2 = r * r;
+    // spectral bounds of T5, T4, T3, T2, P over y in [0, r^2]
+    double tb[6];
+    tb[5] = fabs(tanh_coef(4)) + fabs(tanh_coef(5)) * r2;
+    for (int k = 4; k >= 1; --k) tb[k] = fabs(tanh_coef(k - 1)) + r2 * tb[k + 1];
+    st->kind = kTcSplit;
+    op.part_out = 0;
+    auto horner = [&](int T, int out, int k, double spec) {
+        // out = c_k I + Y T with Y in M: E1 = T~ (row d_Y), E2 = Y~ (column d_T)
+        begin_op(op, M, T, T, M, 1.0 / (static_cast<double>(scl[M]) * scl[T]));
+        op.nout = 1;
+        out_d(op.out[0], out, kOutMaster | kOutSlices, 1.0, spec);
+        prod_terms(op.out[0], M, T, 1.0);
+        op.out[0].c = tanh_coef(k);
+        scl[out] = op.out[0].s;
+    };
+    if (sub == kFtStart) {
+        // Y = x^2: Y~ = v + (d_x[i] + d_x[j]) x~,  d_Y = d_x^2 + v_ii
+        begin_op(op, Z, Z, Z, -1, 1.0 / (static_cast<double>(scl[Z]) * scl[Z]));
+        op.nout = 3;
+        out_d(op.out[0], M, kOutMaster | kOutSlices, 1.0, r2);
+        set_e(op.out[0], Z, 0.0, 1.0, 1.0, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[0], 0.0, Z, Z, 1.0, 0.0, 0.0);
+        // T5 = c4 I + c5 Y
+        const double c4 = tanh_coef(4), c5 = tanh_coef(5);
+        out_d(op.out[1], N, kOutMaster | kOutSlices, c5, tb[5]);
+        set_e(op.out[1], Z, 0.0, c5, c5, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[1], c4, Z, Z, c5, 0.0, 0.0);
+        // copy of x
+        out_d(op.out[2], X, kOutMaster | kOutSlices, 0.0, r);
+        set_e(op.out[2], -1, 1.0, 0.0, 0.0, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[2], 0.0, Z, -1, 0.0, 1.0, 0.0);
+        scl[M] = op.out[0].s;
+        scl[N] = op.out[1].s;
+        scl[X] = op.out[2].s;
+        st->ft_sub = kFtPoly1;
+        st->ft_last_mat = M;
+    } else if (sub == kFtPoly1) {
+        horner(N, W0, 3, tb[4]);
+        st->ft_sub = kFtPoly2;
+        st->ft_last_mat = W0;
+    } else if (sub == kFtPoly2) {
+        horner(W0, N, 2, tb[3]);
+        st->ft_sub = kFtPoly3;
+        st->ft_last_mat = N;
+    } else if (sub == kFtPoly3) {
+        horner(N, W0, 1, tb[2]);
+        st->ft_sub = kFtPoly4;
+        st->ft_last_mat = W0;
+    } else if (sub == kFtPoly4) {
+        horner(W0, N, 0, tb[1]);
+        st->ft_sub = kFtPoly5;
+        st->ft_last_mat = N;
+    } else {
+        // z0 = x P: E1 = P~ (row d_x), E2 = x~ (column d_P); |tanh x| <= |x|
+        begin_op(op, X, N, N, X, 1.0 / (static_cast<double>(scl[X]) * scl[N]));
+        op.nout = 1;
+        out_d(op.out[0], Z, kOutMaster | kOutSlices, 1.0, r);
+        prod_terms(op.out[0], X, N, 1.0);
+        scl[Z] = op.out[0].s;
+        op.part_out = 0;  // tr z0 and ||z0||_F^2 for the first decision
+        st->ft_sub = kFtPoly6;
+        st->ft_last_mat = Z;
+    }
+}
 
 // Newton-Schulz steps W <- W (2 I - M W) after the closed-form first
 // iterate run until the residual bound, r0^2 after that iterate (r0 =
@@ -546,6 +749,12 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
     st->iter += 1;
     const int W = st->wcur;
 
+    // ---- z0 = tanh(x) by the polynomial start
+    if (sub == kFtStart || (sub >= kFtPoly1 && sub <= kFtPoly5)) {
+        control_fermi_start(st, sub);
+        return;
+    }
+
     // ---- Newton-Schulz inner steps
     if (sub == kFtSquare || sub == kFtShiftElem || sub == kFtWR) {
         if (sub == kFtWR) {
@@ -554,44 +763,41 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
             st->ns_r = st->ns_single ? fmax(r2, kNsSingleFloor) : r2;
         }
         if (st->ns_r > kNsTarget && st->ft_j < kNsMaxSteps) {
-            // R = M W:  R~ = v + Mc W~ + Wc M~,  Rc = Mc Wc
-            const double Mc = sc[M], Wc = sc[WS];
-            fb[R] = fb[M] * fb[W] + fabs(Mc) * fb[W] + fabs(Wc) * fb[M];
-            sc[R] = Mc * Wc;
+            // R = M W; spec(M W) in [1 - r, 1 + r]
             st->ns_single = (st->prec == kPrecMixed && st->ns_r >= kNsSingleAbove) ? 1 : 0;
             st->kind = st->ns_single ? kTcSingle : kTcSplit;
             begin_op(op, M, W, W, M, 1.0 / (static_cast<double>(scl[M]) * scl[W]));
             op.nout = 1;
-            set_out(op.out[0], R, kOutMaster | kOutSlices, 1.0, Mc, Wc, 0.0, fb[R]);
+            out_d(op.out[0], R, kOutMaster | kOutSlices, 1.0, 1.0 + st->ns_r);
+            prod_terms(op.out[0], M, W, 1.0);
             scl[R] = op.out[0].s;
             st->ft_sub = kFtMW;
             st->ft_last_mat = R;
         } else {
-            // z'' = N W:  z~ = v + Nc W~ + Wc N~,  zc = Nc Wc
-            const double Nc = sc[N], Wc = sc[WS];
-            fb[Z] = fb[N] * fb[W] + fabs(Nc) * fb[W] + fabs(Wc) * fb[N];
-            sc[Z] = Nc * Wc;
+            // z'' = N W = tanh(...) up to the residual: spec in [-1 - r, 1 + r]
             st->kind = kTcSplit;
             begin_op(op, N, W, W, N, 1.0 / (static_cast<double>(scl[N]) * scl[W]));
             op.nout = 1;
-            set_out(op.out[0], Z, kOutMaster | kOutSlices, 1.0, Nc, Wc, 0.0, fb[Z]);
+            out_d(op.out[0], Z, kOutMaster | kOutSlices, 1.0, 1.0 + st->ns_r);
+            prod_terms(op.out[0], N, W, 1.0);
             scl[Z] = op.out[0].s;
-            op.part_out = 0;  // tr z~ and ||z~||_F^2 for the next Newton step on mu
+            op.part_out = 0;  // tr z and ||z||_F^2 for the next Newton step on mu
             st->ft_sub = kFtNW;
             st->ft_last_mat = Z;
         }
         return;
     }
     if (sub == kFtMW) {
-        // W' = 2 W - W R:  W'~ = (2 - Rc) W~ - Wc R~ - v,  W'c = Wc (2 - Rc)
-        const double Rc = sc[R], Wc = sc[WS];
+        // W' = 2 W - W R:  W'~ = (2 - d_R[j]) W~ - d_W[i] R~ - v,
+        // d_W' = 2 d_W - d_W d_R - v_ii;  W' = (1 - r'(m)) / m with |r'| <= r
+        // on the spectrum [mmin, mmax] of M
         const int Wn = (W == kMatW0) ? kMatW1 : kMatW0;
-        fb[Wn] = fabs(2.0 - Rc) * fb[W] + fabs(Wc) * fb[R] + fb[W] * fb[R];
-        sc[WS] = Wc * (2.0 - Rc);
         st->kind = st->ns_single ? kTcSingle : kTcSplit;
         begin_op(op, W, R, W, R, 1.0 / (static_cast<double>(scl[W]) * scl[R]));
         op.nout = 1;
-        set_out(op.out[0], Wn, kOutMaster | kOutSlices, -1.0, 2.0 - Rc, -Wc, 0.0, fb[Wn]);
+        out_d(op.out[0], Wn, kOutMaster | kOutSlices, -1.0, (1.0 + st->ns_r) / st->ns_mmin);
+        set_e(op.out[0], R, 2.0, 0.0, -1.0, W, 0.0, -1.0, 0.0);
+        set_d(op.out[0], 0.0, W, R, -1.0, 2.0, 0.0);
         scl[Wn] = op.out[0].s;
         st->wcur = Wn;
         st->ft_sub = kFtWR;
@@ -610,9 +816,9 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
     //      a large error falls back to shift-only steps;
     //   D  after the last doubling, shift-only Newton steps until
     //      |tr D - N_e| <= 1e-3, then the final trace-exact product.
-    const double zc = sc[Z];
-    const double trz = nn * zc + tr0;
-    const double zz = nn * zc * zc + 2.0 * zc * tr0 + sq0;
+    // diagonal form: the partials are tr z and ||z||_F^2 themselves
+    const double trz = tr0;
+    const double zz = sq0;
     fb[Z] = sqrt(fmax(sq0, 0.0));
     const double trD = 0.5 * (nn - trz);
     const double slope = 0.5 * (nn - zz);  // d tr D / d b with b the logit shift
@@ -634,20 +840,25 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
     }
     if (stages_done && (fabs(dN) <= 1e-3 || st->ft_shifts >= 6)) {
         // ---- final product: D0 = (I - z)/2 and Q = (I - z^2)/4 in FP64
+        //   D0: -z~/2 off the diagonal, (1 - d_z)/2 on it
+        //   Q:  -(v + (d_z[i] + d_z[j]) z~)/4 off it, (1 - d_z^2 - v_ii)/4 on it
         st->kind = kTcSplit;
         begin_op(op, Z, Z, Z, -1, 1.0 / (static_cast<double>(scl[Z]) * scl[Z]));
         op.nout = 2;
-        set_out(op.out[0], Z, kOutF64a, 0.0, -0.5, 0.0, 0.5 * (1.0 - zc), 1.0);
-        set_out(op.out[1], Z, kOutF64b, -0.25, -0.5 * zc, 0.0, 0.25 * (1.0 - zc * zc), 1.0);
+        out_d(op.out[0], Z, kOutF64a, 0.0, 1.0);
+        set_e(op.out[0], -1, -0.5, 0.0, 0.0, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[0], 0.5, Z, -1, 0.0, -0.5, 0.0);
+        out_d(op.out[1], Z, kOutF64b, -0.25, 1.0);
+        set_e(op.out[1], Z, 0.0, -0.25, -0.25, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[1], 0.25, Z, Z, -0.25, 0.0, 0.0);
         op.part_out = 0;
         st->ft_sub = kFtFinal;
         return;
     }
     const double beta_k = st->beta0 * ldexp(1.0, st->ft_stage);  // z = tanh(beta_k (H - mu)/2)
-    // spectral radius of z: |tanh(beta_k (lambda - mu)/2)| over the Gershgorin
-    // interval (z0 is linear in H, below tanh by < x^3/3 at |x| <= 1e-3; the
-    // margin also covers the expansion's rounding).  Early stages have small
-    // z, so M is close to I and Newton-Schulz needs few or no steps.
+    // spectral radius of z: |tanh(beta_k (lambda - mu)/2)| over the bound
+    // interval (the margin covers the expansion's rounding).  Early stages
+    // have small z, so M is close to I and Newton-Schulz needs few or no steps.
     const double rad = fmax(fabs(st->emax - st->mu_t), fabs(st->emin - st->mu_t));
     const double rho = fmin(1.0, tanh(0.5 * beta_k * rad) * (1.0 + 1e-6) + 1e-6);
     b = shift_only ? fmax(-1.0, fmin(1.0, b)) : fmax(-0.5, fmin(0.5, b));
@@ -656,38 +867,39 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
     st->mu_t += 2.0 * b / beta_k;
     st->ft_j = 0;
     st->ns_single = 0;
-    const double fz = fb[Z];
     if (!shift_only) {
         st->ft_shifts = 0;
-        // ---- shift + double: s = z^2 = zc^2 I + 2 zc z~ + v with v = z~ z~
-        const double t2 = t * t;
-        const double Mc = (1.0 + t2) * (1.0 + zc * zc) - 4.0 * t * zc;
-        const double Nc = 2.0 * (1.0 + t2) * zc - 2.0 * t * (1.0 + zc * zc);
+        // ---- shift + double, with z = diag(d) + z~ and v = z~ z~:
+        //   z^2 = diag(d^2 + v_ii) + (d[i] + d[j]) z~ + v
+        //   M = (1 + t^2)(I + z^2) - 4 t z,  N = 2 ((1 + t^2) z - t (I + z^2)),
+        //   W1 = 2 w0 I - w0^2 M (first Newton-Schulz iterate)
+        const double t2 = t * t, tp = 1.0 + t2;
         // spectrum of M: m(x) = (1 + t^2)(1 + x^2) - 4 t x = (1 - t x)^2 + (x - t)^2
         // over x in [-rho, rho]; a convex quadratic with its minimum at 2t/(1 + t^2)
-        const double m_p = (1.0 + t2) * (1.0 + rho * rho) - 4.0 * t * rho;
-        const double m_m = (1.0 + t2) * (1.0 + rho * rho) + 4.0 * t * rho;
+        const double m_p = tp * (1.0 + rho * rho) - 4.0 * t * rho;
+        const double m_m = tp * (1.0 + rho * rho) + 4.0 * t * rho;
         const double mmax = fmax(m_p, m_m);
-        const double mmin = (fabs(2.0 * t / (1.0 + t2)) <= rho) ? (1.0 - t2) * (1.0 - t2) / (1.0 + t2)
-                                                                 : fmin(m_p, m_m);
+        const double mmin = (fabs(2.0 * t / tp) <= rho) ? (1.0 - t2) * (1.0 - t2) / tp : fmin(m_p, m_m);
         const double w0 = 2.0 / (mmin + mmax);
         st->w0 = w0;
         st->ns_r = ns_residual0(mmin, mmax);
-        const double bM1 = 2.0 * (1.0 + t2) * zc - 4.0 * t;  // M~ = (1 + t^2) v + bM1 z~
-        const double bN1 = 2.0 * (1.0 + t2) - 4.0 * t * zc;  // N~ = -2t v + bN1 z~
-        fb[M] = (1.0 + t2) * fz * fz + fabs(bM1) * fz;
-        fb[N] = 2.0 * fabs(t) * fz * fz + fabs(bN1) * fz;
-        fb[W] = w0 * w0 * fb[M];
-        sc[M] = Mc;
-        sc[N] = Nc;
-        sc[WS] = 2.0 * w0 - w0 * w0 * Mc;  // first Newton-Schulz iterate W1 = 2 w0 I - w0^2 M
+        st->ns_mmin = mmin;
+        st->ns_mmax = mmax;
+        const double sN = 2.0 * (tp * rho + fabs(t) * (1.0 + rho * rho));  // ||N||_2
+        const double sW = fmax(fabs(2.0 * w0 - w0 * w0 * mmax), fabs(2.0 * w0 - w0 * w0 * mmin));
+        const double w2 = w0 * w0;
         st->kind = kTcSplit;
         begin_op(op, Z, Z, Z, -1, 1.0 / (static_cast<double>(scl[Z]) * scl[Z]));
         op.nout = 3;
-        set_out(op.out[0], M, kOutMaster | kOutSlices, 1.0 + t2, bM1, 0.0, 0.0, fb[M]);
-        set_out(op.out[1], N, kOutMaster | kOutSlices, -2.0 * t, bN1, 0.0, 0.0, fb[N]);
-        set_out(op.out[2], W, kOutMaster | kOutSlices, -w0 * w0 * (1.0 + t2), -w0 * w0 * bM1, 0.0,
-                0.0, fb[W]);
+        out_d(op.out[0], M, kOutMaster | kOutSlices, tp, mmax);
+        set_e(op.out[0], Z, -4.0 * t, tp, tp, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[0], tp, Z, Z, tp, -4.0 * t, 0.0);
+        out_d(op.out[1], N, kOutMaster | kOutSlices, -2.0 * t, sN);
+        set_e(op.out[1], Z, 2.0 * tp, -2.0 * t, -2.0 * t, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[1], -2.0 * t, Z, Z, -2.0 * t, 2.0 * tp, 0.0);
+        out_d(op.out[2], W, kOutMaster | kOutSlices, -w2 * tp, sW);
+        set_e(op.out[2], Z, 4.0 * t * w2, -w2 * tp, -w2 * tp, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[2], 2.0 * w0 - w2 * tp, Z, Z, -w2 * tp, 4.0 * t * w2, 0.0);
         scl[M] = op.out[0].s;
         scl[N] = op.out[1].s;
         scl[W] = op.out[2].s;
@@ -695,25 +907,28 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
         st->ft_sub = kFtSquare;
         st->ft_last_mat = M;
     } else {
-        // ---- shift only: N = z - t I, M = I - t z, spectrum of M in [1 - |t| rho, 1 + |t| rho]
-        const double Mc = 1.0 - t * zc;
-        const double Nc = zc - t;
+        // ---- shift only: N = z - t I, M = I - t z, spectrum of M in [1 - |t| rho, 1 + |t| rho];
+        // no product: M~ = -t z~, d_M = 1 - t d;  N~ = z~, d_N = d - t;
+        // W1~ = w0^2 t z~, d_W1 = 2 w0 - w0^2 + w0^2 t d
         const double mmin = 1.0 - fabs(t) * rho, mmax = 1.0 + fabs(t) * rho;
         const double w0 = 2.0 / (mmin + mmax);
         st->w0 = w0;
         st->ns_r = ns_residual0(mmin, mmax);
-        fb[M] = fabs(t) * fz;
-        fb[N] = fz;
-        fb[W] = w0 * w0 * fb[M];
-        sc[M] = Mc;
-        sc[N] = Nc;
-        sc[WS] = 2.0 * w0 - w0 * w0 * Mc;
+        st->ns_mmin = mmin;
+        st->ns_mmax = mmax;
+        const double w2 = w0 * w0;
         st->kind = kTcElem;
         begin_op(op, Z, Z, Z, -1, 0.0);
         op.nout = 3;
-        set_out(op.out[0], M, kOutMaster | kOutSlices, 0.0, -t, 0.0, 0.0, fb[M]);
-        set_out(op.out[1], N, kOutMaster | kOutSlices, 0.0, 1.0, 0.0, 0.0, fb[N]);
-        set_out(op.out[2], W, kOutMaster | kOutSlices, 0.0, w0 * w0 * t, 0.0, 0.0, fb[W]);
+        out_d(op.out[0], M, kOutMaster | kOutSlices, 0.0, mmax);
+        set_e(op.out[0], -1, -t, 0.0, 0.0, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[0], 1.0, Z, -1, 0.0, -t, 0.0);
+        out_d(op.out[1], N, kOutMaster | kOutSlices, 0.0, rho + fabs(t));
+        set_e(op.out[1], -1, 1.0, 0.0, 0.0, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[1], -t, Z, -1, 0.0, 1.0, 0.0);
+        out_d(op.out[2], W, kOutMaster | kOutSlices, 0.0, fmax(fabs(2.0 * w0 - w2 * mmax), fabs(2.0 * w0 - w2 * mmin)));
+        set_e(op.out[2], -1, w2 * t, 0.0, 0.0, -1, 0.0, 0.0, 0.0);
+        set_d(op.out[2], 2.0 * w0 - w2, Z, -1, 0.0, w2 * t, 0.0);
         scl[M] = op.out[0].s;
         scl[N] = op.out[1].s;
         scl[W] = op.out[2].s;
@@ -806,7 +1021,7 @@ __global__ void k_control(const MmaProb *probs, int nprobs, const DevCtl *ctl, S
         const int kind = *reinterpret_cast<const volatile int *>(&st->kind);
         if (!*reinterpret_cast<const volatile int *>(&st->done)) {
             bits |= kStepActive;
-            if (kind == kTcSingle || kind == kTcSplit || kind == kTcElem) bits |= kStepTc;
+            if (kind == kTcSingle || kind == kTcSplit || kind == kTcElem || kind == kTcDelta) bits |= kStepTc;
             if (kind == kFp64 || kind == kDf) bits |= kStepFp64;
             if (kind == kDigit) bits |= kStepDigit;
         }

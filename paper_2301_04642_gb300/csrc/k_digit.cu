@@ -20,6 +20,9 @@
 //     X' = (X^2 or 2X - X^2) + gamma (X - X^2)
 // written to the other FP64 buffer (and mirrored), with per-tile partials
 // tr X', ||X'||_F^2 and ||X^2 - X||_F^2 (same slots as the SIMT FP64 step).
+// As the first product of a polishing pair it also writes the FP16 slices of
+// Delta = X^2 - X and of S (the operands of the pair's second, split-FP16
+// product; see the control kernel).
 //
 // Tiles: 128 rows (block I) x 64 columns (block J), J >= 2I, one persistent
 // CTA per SM.  Warp roles as in the split-FP16 kernel: warp 0 TMA (per K
@@ -381,34 +384,79 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                 break;
             }
 
-            // ---- epilogue: X' = (X^2 or 2X - X^2) + gamma (X - X^2)
+            // ---- epilogue: X' = (X^2 or 2X - X^2) + gamma (X - X^2); the first
+            // product of a polishing pair also writes the FP16 slices of
+            // Delta0 = X^2 - X (slot Y0) and S = 2X + Delta0 (X^2 branch) or
+            // 2I - 2X + Delta0 (slot Y1), the operands of the pair's second product
             const int sq = st->sq;
             const double gamma = st->gamma;
             double *Xo = pr.Xd[st->xcur ^ 1];  // the control kernel flips xcur afterwards
-            const int ldx = pr.ldx;
+            const int ldx = pr.ldx, lds = pr.lds;
+            const bool emit = st->pol_emit != 0;
+            const float sD = st->pol_sD, sS = st->pol_sS;
+            const MatSlot &mD = pr.mats[kMatY0];
+            const MatSlot &mS = pr.mats[kMatY1];
             const int i0 = te.I * kTileM + q * 32;
             const int i = i0 + lane;
             const int j0 = te.Jp * kDigitN + h * 32;
             const int rsub = lane >> 3, csub = lane & 7;
             double tr = 0.0, s2 = 0.0, id = 0.0;
             double *stg = tail->stage[ew];
+            // the (i, j) half goes through the staging buffer: 4 rows x 8
+            // consecutive columns per store instruction
+            auto put_staged = [&](int jg, int what) {
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int ii = i0 + 4 * k + rsub, jj = jg + csub;
+                    if (ii < n && jj < n && jj >= ii) {
+                        const double v = stg[(4 * k + rsub) * 9 + csub];
+                        if (what == 0) {
+                            Xo[static_cast<size_t>(ii) * ldx + jj] = v;
+                        } else {
+                            const MatSlot &m = (what == 1) ? mD : mS;
+                            const float y = static_cast<float>(v) * ((what == 1) ? sD : sS);
+                            const __half hh = __float2half_rn(y);
+                            const size_t at = static_cast<size_t>(ii) * lds + jj;
+                            m.sl[0][at] = hh;
+                            m.sl[1][at] = __float2half_rn(y - __half2float(hh));
+                        }
+                    }
+                }
+                __syncwarp();
+            };
             if (i0 < n && j0 < n && j0 + 31 >= i0) {
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
                     const int jg = j0 + 8 * g;
+                    double dv[8], sv[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int j = jg + u;
                         double xn = 0.0;
+                        dv[u] = 0.0;
+                        sv[u] = 0.0;
                         if (i < n && j < n && j >= i) {
                             const double P = static_cast<double>(acc[8 * g + u]) * 8.673617379884035e-19;  // 2^-60
                             const double xo = x_at(pr, st, j, i);  // symmetric: coalesced read
                             xn = (sq ? P : 2.0 * xo - P) + gamma * (xo - P);
                             const double dd = P - xo;
+                            dv[u] = dd;
+                            sv[u] = (sq ? 2.0 * xo : ((j == i) ? 2.0 : 0.0) - 2.0 * xo) + dd;
                             if (j != i) {
                                 Xo[static_cast<size_t>(j) * ldx + i] = xn;
                                 s2 += 2.0 * xn * xn;
                                 id += 2.0 * dd * dd;
+                                if (emit) {
+                                    const size_t at = static_cast<size_t>(j) * lds + i;
+                                    const float yd = static_cast<float>(dd) * sD;
+                                    const float ys = static_cast<float>(sv[u]) * sS;
+                                    const __half hd = __float2half_rn(yd), hs = __float2half_rn(ys);
+                                    mD.sl[0][at] = hd;
+                                    mD.sl[1][at] = __float2half_rn(yd - __half2float(hd));
+                                    mS.sl[0][at] = hs;
+                                    mS.sl[1][at] = __float2half_rn(ys - __half2float(hs));
+                                }
                             } else {
                                 tr += xn;
                                 s2 += xn * xn;
@@ -417,14 +465,15 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
                         }
                         stg[lane * 9 + u] = xn;
                     }
-                    __syncwarp();
+                    put_staged(jg, 0);
+                    if (emit) {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int ii = i0 + 4 * k + rsub, jj = jg + csub;
-                        if (ii < n && jj < n && jj >= ii)
-                            Xo[static_cast<size_t>(ii) * ldx + jj] = stg[(4 * k + rsub) * 9 + csub];
+                        for (int u = 0; u < 8; ++u) stg[lane * 9 + u] = dv[u];
+                        put_staged(jg, 1);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) stg[lane * 9 + u] = sv[u];
+                        put_staged(jg, 2);
                     }
-                    __syncwarp();
                 }
             }
             tr = warp_sum(tr);

@@ -72,7 +72,10 @@ __device__ __forceinline__ double slice_scale_of(unsigned long long maxbits) {
     return ldexp(1.0, 14 - e);
 }
 
-// The K-chunk range of work unit u: tile u / S, part u % S of its chunks.
+// The K-chunk range of work unit u: part u / ntiles of tile u % ntiles.
+// The parts go outermost, so the work units that run at the same time
+// (consecutive u over the CTAs) read the same K range of their panels: one
+// part of every panel fits L2 and is read from DRAM about once per wave.
 struct Unit {
     int tile, k0, k1;
 };
@@ -82,8 +85,8 @@ __device__ __forceinline__ Unit unit_of(const GemmArgs &g, int u) {
     const int nk = (g.kdim + kTileK - 1) / kTileK;
     const int cs = (nk + S - 1) / S;
     Unit r;
-    r.tile = u / S;
-    r.k0 = (u % S) * cs;
+    r.tile = u % g.ntiles;
+    r.k0 = (u / g.ntiles) * cs;
     r.k1 = min(nk, r.k0 + cs);
     return r;
 }
@@ -315,14 +318,15 @@ __global__ void __launch_bounds__(256) k_gemm_reduce(const GemmArgs *__restrict_
     const int S = g.nsplit;
     const double inv = 1.0 / (slice_scale_of(g.amax[0]) * slice_scale_of(g.amax[1]));
     const size_t tsz = static_cast<size_t>(kTileM) * kGemmN;
-    const float *base = g.ws + static_cast<size_t>(blockIdx.x) * S * tsz;
+    const float *base = g.ws + static_cast<size_t>(blockIdx.x) * tsz;  // part s at unit s * ntiles + tile
+    const size_t pstride = static_cast<size_t>(g.ntiles) * tsz;
     const int n = g.rows_a;
     for (int idx = threadIdx.x; idx < kTileM * kGemmN; idx += blockDim.x) {
         const int r = idx % kTileM, c = idx / kTileM;
         const int i = te.I * kTileM + r, j = te.Jp * kGemmN + c;
         if (i >= n || j >= n || j < i) continue;
         double sum = 0.0;
-        for (int s = 0; s < S; ++s) sum += static_cast<double>(base[s * tsz + idx]);
+        for (int s = 0; s < S; ++s) sum += static_cast<double>(base[s * pstride + idx]);
         const double v = sum * inv;
         g.C[static_cast<long long>(i) * g.ldc + j] = v;
         if (j != i) g.C[static_cast<long long>(j) * g.ldc + i] = v;

@@ -88,7 +88,13 @@ __device__ __forceinline__ int step_kind(const SolveState *st) {
 
 __device__ __forceinline__ bool tile_active(const SolveState *st) {
     const int kind = step_kind(st);
-    return kind == kTcSingle || kind == kTcSplit || kind == kTcElem;
+    return kind == kTcSingle || kind == kTcSplit || kind == kTcElem || kind == kTcDelta;
+}
+
+// FP16 slices per operand: two for the split products
+__device__ __forceinline__ int step_slices(const SolveState *st) {
+    const int kind = step_kind(st);
+    return (kind == kTcSplit || kind == kTcDelta) ? 2 : 1;
 }
 
 // K chunks of this step (0 for an epilogue-only step)
@@ -437,7 +443,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             const TileEnt te = tiles[sg.tile];
             const MmaProb &pr = probs[sg.prob];
             const SolveState *st = pr.st;
-            const int S = (step_kind(st) == kTcSplit) ? 2 : 1;
+            const int S = step_slices(st);
             const MatSlot &ma = pr.mats[st->op.A];
             const MatSlot &mb = pr.mats[st->op.B];
             const bool wide = tile_bn(pr) == kTileN;
@@ -492,7 +498,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             const TileEnt te = tiles[sg.tile];
             const MmaProb &pr = probs[sg.prob];
             const SolveState *st = pr.st;
-            const int S = (step_kind(st) == kTcSplit) ? 2 : 1;
+            const int S = step_slices(st);
             const uint32_t idesc = (tile_bn(pr) == kTileN) ? idesc_w : idesc_n;
             for (int kc = sg.k0; kc < sg.k0 + sg.nch; ++kc) {
                 const uint32_t buf = chunk & 1u;
@@ -869,9 +875,24 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                             const MatSlot &m = pr.mats[os.mat];
                             float val[8];
                             float csq = 0.0f;
+                            if (fl & kOutDiag) {
+                                // per-row / per-column coefficients of E1 and E2
+                                const double *d1 = (os.v1 >= 0) ? pr.dg[os.v1] : nullptr;
+                                const double *d2 = (os.v2 >= 0) ? pr.dg[os.v2] : nullptr;
+                                const float r1 = d1 ? fmaf(os.g1r, static_cast<float>(d1[i]), os.b1) : os.b1;
+                                const float r2 = d2 ? fmaf(os.g2r, static_cast<float>(d2[i]), os.b2) : os.b2;
+#pragma unroll
+                                for (int u = 0; u < 8; ++u) {
+                                    const float c1 = d1 ? fmaf(os.g1c, static_cast<float>(d1[j0 + u]), r1) : r1;
+                                    const float c2 = d2 ? fmaf(os.g2c, static_cast<float>(d2[j0 + u]), r2) : r2;
+                                    val[u] = fmaf(os.a, v[u], fmaf(c1, e1[u], c2 * e2[u]));
+                                }
+                            } else {
+#pragma unroll
+                                for (int u = 0; u < 8; ++u) val[u] = fmaf(os.a, v[u], fmaf(os.b1, e1[u], os.b2 * e2[u]));
+                            }
 #pragma unroll
                             for (int u = 0; u < 8; ++u) {
-                                val[u] = fmaf(os.a, v[u], fmaf(os.b1, e1[u], os.b2 * e2[u]));
                                 csq = fmaf(val[u], val[u], csq);
                                 stf[u * 33 + lane] = val[u];
                             }
@@ -907,6 +928,30 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                     auto okf = [&](int u) { return i < n && j0 + u < n && (!diag || j0 + u >= i); };
                     auto e1f = [&](int u) { return E1 ? E1[static_cast<size_t>(j0 + u) * ldy + i] : 0.0f; };
                     auto e2f = [&](int u) { return E2 ? E2[static_cast<size_t>(j0 + u) * ldy + i] : 0.0f; };
+                    // off-diagonal value of an output (diagonal form: per-row and
+                    // per-column E coefficients)
+                    auto offv = [&](const OutSpec &os, int u) -> float {
+                        const float vv = acc[c8 * 8 + u] * inv;
+                        if (!(os.flags & kOutDiag)) return fmaf(os.a, vv, fmaf(os.b1, e1f(u), os.b2 * e2f(u)));
+                        const int j = j0 + u;
+                        float c1 = os.b1, c2 = os.b2;
+                        if (os.v1 >= 0) {
+                            const double *d1 = pr.dg[os.v1];
+                            c1 += os.g1r * static_cast<float>(d1[i]) + os.g1c * static_cast<float>(d1[j]);
+                        }
+                        if (os.v2 >= 0) {
+                            const double *d2 = pr.dg[os.v2];
+                            c2 += os.g2r * static_cast<float>(d2[i]) + os.g2c * static_cast<float>(d2[j]);
+                        }
+                        return fmaf(os.a, vv, fmaf(c1, e1f(u), c2 * e2f(u)));
+                    };
+                    // diagonal entry of an output in the diagonal form, FP64
+                    auto diagv = [&](const OutSpec &os, int u) -> double {
+                        double r = os.c + static_cast<double>(os.a) * static_cast<double>(acc[c8 * 8 + u] * inv);
+                        const double dxv = (os.dx >= 0) ? pr.dg[os.dx][i] : 0.0;
+                        const double dyv = (os.dy >= 0) ? pr.dg[os.dy][i] : 0.0;
+                        return r + os.q * dxv * dyv + os.l1 * dxv + os.l2 * dyv;
+                    };
                     float crr = 0.0f;
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
@@ -922,15 +967,21 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                         const int fl = os.flags;
                         if (fl & (kOutF64a | kOutF64b)) {
                             double *X = pr.Xd[(fl & kOutF64a) ? 0 : 1];
+                            const double *Xa = (fl & kOutF64Add) ? pr.Xd[(fl & kOutF64a) ? 1 : 0] : nullptr;
 #pragma unroll
                             for (int u = 0; u < 8; ++u) {
                                 const int j = j0 + u;
                                 const bool on_diag = (j == i);
                                 double d = 0.0;
                                 if (okf(u)) {
-                                    d = static_cast<double>(os.a) * (acc[c8 * 8 + u] * inv) +
-                                        static_cast<double>(os.b1) * e1f(u) +
-                                        static_cast<double>(os.b2) * e2f(u) + (on_diag ? os.c : 0.0);
+                                    if (fl & kOutDiag) {
+                                        d = on_diag ? diagv(os, u) : static_cast<double>(offv(os, u));
+                                    } else {
+                                        d = static_cast<double>(os.a) * (acc[c8 * 8 + u] * inv) +
+                                            static_cast<double>(os.b1) * e1f(u) +
+                                            static_cast<double>(os.b2) * e2f(u) + (on_diag ? os.c : 0.0);
+                                    }
+                                    if (Xa) d += Xa[static_cast<size_t>(j) * ldx + i];  // symmetric: read at (j, i)
                                     if (!on_diag) X[static_cast<size_t>(j) * ldx + i] = d;
                                     if (o == pout) {
                                         if (on_diag) tr += d;
@@ -952,6 +1003,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                         }
                         const MatSlot &m = pr.mats[os.mat];
                         const float cdiag = static_cast<float>(os.c);
+                        const bool dform = (fl & kOutDiag) != 0;
                         float csq = 0.0f;
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
@@ -959,17 +1011,27 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                             const bool on_diag = (j == i);
                             float val = 0.0f;
                             if (okf(u)) {
-                                val = fmaf(os.a, acc[c8 * 8 + u] * inv, fmaf(os.b1, e1f(u), os.b2 * e2f(u))) +
-                                      (on_diag ? cdiag : 0.0f);
-                                if (!on_diag) {
-                                    if (fl & kOutMaster) m.master[static_cast<size_t>(j) * ldy + i] = val;
-                                    if (fl & kOutSlices) put_slices(m, static_cast<size_t>(j) * lds + i, val * os.s);
+                                if (dform && on_diag) {
+                                    // the diagonal goes to the FP64 vector; the small part keeps 0
+                                    const double dv = diagv(os, u);
+                                    pr.dg[os.mat][i] = dv;
+                                    if (o == pout) {
+                                        tr += dv;
+                                        sq += dv * dv;
+                                    }
+                                    if (o == 1) tr1 += dv;
+                                } else {
+                                    val = offv(os, u) + ((on_diag && !dform) ? cdiag : 0.0f);
+                                    if (!on_diag) {
+                                        if (fl & kOutMaster) m.master[static_cast<size_t>(j) * ldy + i] = val;
+                                        if (fl & kOutSlices) put_slices(m, static_cast<size_t>(j) * lds + i, val * os.s);
+                                    }
+                                    if (o == pout) {
+                                        if (on_diag) tr += static_cast<double>(val);
+                                        csq = fmaf(on_diag ? val : 2.0f * val, val, csq);
+                                    }
+                                    if (o == 1 && on_diag) tr1 += static_cast<double>(val);
                                 }
-                                if (o == pout) {
-                                    if (on_diag) tr += static_cast<double>(val);
-                                    csq = fmaf(on_diag ? val : 2.0f * val, val, csq);
-                                }
-                                if (o == 1 && on_diag) tr1 += static_cast<double>(val);
                             }
                             stf[lane * 9 + u] = val;
                         }

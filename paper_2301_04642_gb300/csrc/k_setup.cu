@@ -122,23 +122,17 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
     double tr = 0.0, sq = 0.0;
     // block b takes rows b, b + grid, ...; thread t the column pairs (2t, 2t + 1),
     // (2t + 2 blockDim, ...), ...: 16-byte loads of Hp where its row is aligned,
-    // 8-byte FP32 and 4-byte FP16 stores (ldy and lds are even)
+    // 8-byte FP32 and 4-byte FP16 stores (ldy and lds are even).  Four column
+    // pairs per thread are loaded before any is used (enough bytes in flight
+    // to approach the HBM rate with 2 blocks of 256 per SM).
+    const int cstride = 2 * blockDim.x;
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         float sqr = 0.0f;
         double sqd = 0.0;
         const double *hrow = pr.H + static_cast<long long>(i) * pr.ldh;
         const bool h16 = (reinterpret_cast<uintptr_t>(hrow) & 15u) == 0;
-        for (int j = 2 * threadIdx.x; j < n; j += 2 * blockDim.x) {
+        auto body = [&](int j, double h0, double h1) {
             const bool two = j + 1 < n;
-            double h0, h1 = 0.0;
-            if (two && h16) {
-                const double2 hv = *reinterpret_cast<const double2 *>(hrow + j);
-                h0 = hv.x;
-                h1 = hv.y;
-            } else {
-                h0 = hrow[j];
-                if (two) h1 = hrow[j + 1];
-            }
             if (fp64) {
                 double *xr = pr.Xd[0] + static_cast<long long>(i) * pr.ldx;
                 const double x0 = ((i == j) ? st->emax - h0 : -h0) * inv_w;
@@ -151,15 +145,22 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
                     if (i == j + 1) tr += x1;
                     sqd += x1 * x1;
                 }
-                continue;
+                return;
             }
             float y0, y1;
             float sc;
             const MatSlot *ms;
             if (fermi) {
-                // z0~ = (beta0 / 2)(H - mu0 I); its identity part is 0
-                y0 = (i == j) ? static_cast<float>(hb0 * (h0 - mu0)) : hb0f * static_cast<float>(h0);
-                y1 = (i == j + 1) ? static_cast<float>(hb0 * (h1 - mu0)) : hb0f * static_cast<float>(h1);
+                // x = (beta0 / 2)(H - mu0 I) in the diagonal form: the diagonal
+                // in FP64 (d_Z), the small part zero on it
+                y0 = (i == j) ? 0.0f : hb0f * static_cast<float>(h0);
+                y1 = (i == j + 1) ? 0.0f : hb0f * static_cast<float>(h1);
+                if (i == j || i == j + 1) {
+                    const double dv = hb0 * (((i == j) ? h0 : h1) - mu0);
+                    pr.dg[kMatZ][i] = dv;
+                    tr += dv;
+                    sqd += dv * dv;
+                }
                 ms = &pr.mats[kMatZ];
                 sc = sz;
             } else {
@@ -186,6 +187,30 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
             if (i == j) tr += y0;
             if (i == j + 1) tr += y1;
             sqr = fmaf(y0, y0, fmaf(y1, y1, sqr));
+        };
+        for (int jb = 2 * threadIdx.x; jb < n; jb += 4 * cstride) {
+            double hx[4], hy[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = jb + q * cstride;
+                hx[q] = 0.0;
+                hy[q] = 0.0;
+                if (j < n) {
+                    if (j + 1 < n && h16) {
+                        const double2 hv = *reinterpret_cast<const double2 *>(hrow + j);
+                        hx[q] = hv.x;
+                        hy[q] = hv.y;
+                    } else {
+                        hx[q] = hrow[j];
+                        if (j + 1 < n) hy[q] = hrow[j + 1];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = jb + q * cstride;
+                if (j < n) body(j, hx[q], hy[q]);
+            }
         }
         sq += static_cast<double>(sqr) + sqd;
     }

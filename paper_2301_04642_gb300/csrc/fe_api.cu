@@ -287,7 +287,7 @@ size_t slot_bytes(int n, int method, int *ldy, int *lds, int *ldx, size_t *npart
     add(8 * 3 * nn);                                 // Lanczos vectors
     if (method == kMethodSp2)
         for (int a = 0; a < kDigits; ++a) add(2 * nn * (*lds));  // digits of X/4
-    if (method == kMethodFermi) add(8 * kNumMats * nn);  // FP64 diagonals of the matrix slots
+    if (method == kMethodFermi) add(12 * kNumMats * align_up(nn, 8));  // FP64 diagonals + FP32 copies
     add(8 * kPartStride * (*nparts));                // partials
     add(sizeof(SolveState));
     add(sizeof(RowInfo) * nn);
@@ -403,7 +403,8 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
     __half *digs[kDigits] = {};
     if (method == kMethodSp2)
         for (int a = 0; a < kDigits; ++a) digs[a] = reinterpret_cast<__half *>(take(2 * nn * lds));
-    double *diags = (method == kMethodFermi) ? reinterpret_cast<double *>(take(8 * kNumMats * nn)) : nullptr;
+    const size_t dstride = align_up(nn, 8);  // 64-byte aligned vectors
+    double *diags = (method == kMethodFermi) ? reinterpret_cast<double *>(take(12 * kNumMats * dstride)) : nullptr;
     s->part = reinterpret_cast<double *>(take(8 * kPartStride * nparts));
     s->st = reinterpret_cast<SolveState *>(take(sizeof(SolveState)));
     s->rowinfo = reinterpret_cast<RowInfo *>(take(sizeof(RowInfo) * nn));
@@ -443,7 +444,11 @@ int acquire_slot(fe_ctx *ctx, int n, int method, Slot **out) {
         s->hp.mats[kMatW0].master = masters[3];  // the two W slice sets share one master
         s->hp.mats[kMatW1].master = masters[3];
         s->hp.mats[kMatR].master = masters[4];
-        for (int m = 0; m < kNumMats; ++m) s->hp.dg[m] = diags + static_cast<size_t>(m) * nn;
+        float *diagf = reinterpret_cast<float *>(diags + kNumMats * dstride);
+        for (int m = 0; m < kNumMats; ++m) {
+            s->hp.dg[m] = diags + static_cast<size_t>(m) * dstride;
+            s->hp.dgf[m] = diagf + static_cast<size_t>(m) * dstride;
+        }
     } else {
         s->hp.mats[kMatY0].master = masters[0];  // both slice sets of Y share the master
         s->hp.mats[kMatY1].master = masters[0];

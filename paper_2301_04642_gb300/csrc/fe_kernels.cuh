@@ -10,7 +10,8 @@ namespace fe {
 // (hi, lo) of s * A~ with their TMA descriptors, and optionally the FP32 master
 // A~.  Zero temperature keeps (FP64 scalar) I + A~, the scalar in the solve
 // state; finite temperature keeps diag(d) + A~ with d an FP64 vector
-// (MmaProb::dg) and A~ zero on the diagonal.
+// (MmaProb::dg) and A~ zero on the diagonal, its master holding only the
+// upper triangle (the epilogue reads E terms at (i, j), j >= i).
 struct MatSlot {
     CUtensorMap tmA[kMaxSlices];  // box 64 (K) x 128 rows
     CUtensorMap tmB[kMaxSlices];  // box 64 (K) x 256 rows
@@ -49,6 +50,7 @@ struct MmaProb {
     __half *dig[kDigits];
     int ntilesD, padD;
     double *dg[kNumMats];            // finite T: FP64 diagonals of the matrix slots (n each)
+    float *dgf[kNumMats];            // their FP32 copies (the epilogue's E coefficients)
 };
 
 // One tensor-core tile: rows [I*128, I*128+128) x columns [Jp*bn, Jp*bn+bn)

@@ -66,6 +66,14 @@ struct SchedTab {
     int bnmin, wmin, wmax, pad;
 };
 
+// The fields of one output that the store loop's vector path reads.
+struct OutCache {
+    float a, b1, b2, s, g1r, g1c, g2r, g2c;
+    int flags, pad;
+    float *master;
+    __half *sl0, *sl1;
+};
+
 struct MmaSmemTail {
     uint64_t full[kStages];
     uint64_t empty[kStages];
@@ -77,6 +85,8 @@ struct MmaSmemTail {
     int vote[kEpiWarps];
     int sk_ticket, sk_ok;             // split-tile hand-off (drain warp 0 writes, all read)
     double stage[kEpiWarps][32 * 9];  // per-warp staging of 32 rows x 8 columns (direct writes)
+    OutCache oc[kEpiWarps][3];        // per-warp copy of the step's outputs (shared-memory loads
+                                      // in the store loop instead of reloads after every store)
     SchedTab sch;
 };
 
@@ -692,6 +702,23 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             const float *E2 = (op.E2 >= 0) ? pr.mats[op.E2].master : nullptr;
             const int nout = op.nout, pout = op.part_out;
             const float ra = op.ra, rb = op.rb, rc = op.rc;
+            if (lane < nout) {
+                const OutSpec &o = op.out[lane];
+                OutCache &c = tail->oc[ew][lane];
+                c.a = o.a;
+                c.b1 = o.b1;
+                c.b2 = o.b2;
+                c.s = o.s;
+                c.g1r = o.g1r;
+                c.g1c = o.g1c;
+                c.g2r = o.g2r;
+                c.g2c = o.g2c;
+                c.flags = o.flags;
+                c.master = pr.mats[o.mat].master;
+                c.sl0 = pr.mats[o.mat].sl[0];
+                c.sl1 = pr.mats[o.mat].sl[1];
+            }
+            __syncwarp();
             const int i0 = te.I * kTileM + q * 32;
             const int i = i0 + lane;
             const int J = wide ? 2 * te.Jp + h : te.Jp;
@@ -835,6 +862,21 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 const bool diag = (J == te.I);
                 bool has_f64 = false;
                 for (int o = 0; o < nout; ++o) has_f64 = has_f64 || (op.out[o].flags & (kOutF64a | kOutF64b));
+                // diagonal form: the outputs of one step share their E1 / E2
+                // coefficient vectors (the control kernel sets them so); the
+                // row's entries are read once per strip, the columns' once per group
+                int ev1 = -1, ev2 = -1;
+                for (int o = 0; o < nout; ++o) {
+                    if (!(op.out[o].flags & kOutDiag)) continue;
+                    if (op.out[o].v1 >= 0) ev1 = op.out[o].v1;
+                    if (op.out[o].v2 >= 0) ev2 = op.out[o].v2;
+                }
+                bool dup = false;  // a diagonal-form step: its masters are upper-triangular
+                for (int o = 0; o < nout; ++o) dup = dup || (op.out[o].flags & kOutDiag);
+                const float *F1 = (ev1 >= 0) ? pr.dgf[ev1] : nullptr;
+                const float *F2 = (ev2 >= 0) ? pr.dgf[ev2] : nullptr;
+                const float d1i = (F1 && i < n) ? F1[i] : 0.0f;
+                const float d2i = (F2 && i < n) ? F2[i] : 0.0f;
                 const int mr = lane >> 2, mc = (lane & 3) * 8;
 #pragma unroll
                 for (int c8 = 0; c8 < kTileM / 8; ++c8) {
@@ -870,22 +912,28 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                         const size_t mo = static_cast<size_t>(j0 + mr) * ldy + i0 + mc;
                         const size_t ms = static_cast<size_t>(j0 + mr) * lds + i0 + mc;
                         for (int o = 0; o < nout; ++o) {
-                            const OutSpec &os = op.out[o];
+                            const OutCache &os = tail->oc[ew][o];
                             const int fl = os.flags;
-                            const MatSlot &m = pr.mats[os.mat];
                             float val[8];
                             float csq = 0.0f;
                             if (fl & kOutDiag) {
                                 // per-row / per-column coefficients of E1 and E2
-                                const double *d1 = (os.v1 >= 0) ? pr.dg[os.v1] : nullptr;
-                                const double *d2 = (os.v2 >= 0) ? pr.dg[os.v2] : nullptr;
-                                const float r1 = d1 ? fmaf(os.g1r, static_cast<float>(d1[i]), os.b1) : os.b1;
-                                const float r2 = d2 ? fmaf(os.g2r, static_cast<float>(d2[i]), os.b2) : os.b2;
+                                const float r1 = fmaf(os.g1r, d1i, os.b1);
+                                const float r2 = fmaf(os.g2r, d2i, os.b2);
 #pragma unroll
-                                for (int u = 0; u < 8; ++u) {
-                                    const float c1 = d1 ? fmaf(os.g1c, static_cast<float>(d1[j0 + u]), r1) : r1;
-                                    const float c2 = d2 ? fmaf(os.g2c, static_cast<float>(d2[j0 + u]), r2) : r2;
-                                    val[u] = fmaf(os.a, v[u], fmaf(c1, e1[u], c2 * e2[u]));
+                                for (int u = 0; u < 8; u += 4) {
+                                    // FP32 copies, 32-byte aligned (j0 % 8 == 0, stride % 8 == 0)
+                                    const float4 f1 = F1 ? *reinterpret_cast<const float4 *>(F1 + j0 + u)
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                                    const float4 f2 = F2 ? *reinterpret_cast<const float4 *>(F2 + j0 + u)
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                                    val[u] = fmaf(os.a, v[u], fmaf(fmaf(os.g1c, f1.x, r1), e1[u], fmaf(os.g2c, f2.x, r2) * e2[u]));
+                                    val[u + 1] = fmaf(os.a, v[u + 1],
+                                                      fmaf(fmaf(os.g1c, f1.y, r1), e1[u + 1], fmaf(os.g2c, f2.y, r2) * e2[u + 1]));
+                                    val[u + 2] = fmaf(os.a, v[u + 2],
+                                                      fmaf(fmaf(os.g1c, f1.z, r1), e1[u + 2], fmaf(os.g2c, f2.z, r2) * e2[u + 2]));
+                                    val[u + 3] = fmaf(os.a, v[u + 3],
+                                                      fmaf(fmaf(os.g1c, f1.w, r1), e1[u + 3], fmaf(os.g2c, f2.w, r2) * e2[u + 3]));
                                 }
                             } else {
 #pragma unroll
@@ -899,50 +947,49 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                             if (o == pout) sq += 2.0 * static_cast<double>(csq);
                             uint4 hv, lv;
                             if (fl & kOutMaster) {
-                                *reinterpret_cast<float4 *>(m.master + ro) = make_float4(val[0], val[1], val[2], val[3]);
-                                *reinterpret_cast<float4 *>(m.master + ro + 4) = make_float4(val[4], val[5], val[6], val[7]);
+                                *reinterpret_cast<float4 *>(os.master + ro) = make_float4(val[0], val[1], val[2], val[3]);
+                                *reinterpret_cast<float4 *>(os.master + ro + 4) = make_float4(val[4], val[5], val[6], val[7]);
                             }
                             if (fl & kOutSlices) {
                                 split8(val, os.s, hv, lv);
-                                *reinterpret_cast<uint4 *>(m.sl[0] + so) = hv;
-                                *reinterpret_cast<uint4 *>(m.sl[1] + so) = lv;
+                                *reinterpret_cast<uint4 *>(os.sl0 + so) = hv;
+                                *reinterpret_cast<uint4 *>(os.sl1 + so) = lv;
                             }
                             __syncwarp();
                             float w[8];
 #pragma unroll
                             for (int t2 = 0; t2 < 8; ++t2) w[t2] = stf[mr * 33 + mc + t2];
                             __syncwarp();
-                            if (fl & kOutMaster) {
-                                *reinterpret_cast<float4 *>(m.master + mo) = make_float4(w[0], w[1], w[2], w[3]);
-                                *reinterpret_cast<float4 *>(m.master + mo + 4) = make_float4(w[4], w[5], w[6], w[7]);
+                            if ((fl & kOutMaster) && !(fl & kOutDiag)) {  // diagonal form: upper master only
+                                *reinterpret_cast<float4 *>(os.master + mo) = make_float4(w[0], w[1], w[2], w[3]);
+                                *reinterpret_cast<float4 *>(os.master + mo + 4) = make_float4(w[4], w[5], w[6], w[7]);
                             }
                             if (fl & kOutSlices) {
                                 split8(w, os.s, hv, lv);
-                                *reinterpret_cast<uint4 *>(m.sl[0] + ms) = hv;
-                                *reinterpret_cast<uint4 *>(m.sl[1] + ms) = lv;
+                                *reinterpret_cast<uint4 *>(os.sl0 + ms) = hv;
+                                *reinterpret_cast<uint4 *>(os.sl1 + ms) = lv;
                             }
                         }
                         continue;
                     }
                     // element (i, j0 + u) exists in this block's upper part
                     auto okf = [&](int u) { return i < n && j0 + u < n && (!diag || j0 + u >= i); };
-                    auto e1f = [&](int u) { return E1 ? E1[static_cast<size_t>(j0 + u) * ldy + i] : 0.0f; };
-                    auto e2f = [&](int u) { return E2 ? E2[static_cast<size_t>(j0 + u) * ldy + i] : 0.0f; };
+                    // E masters of a diagonal-form step hold the upper triangle only
+                    // (read at (i, j)); others are read at (j, i), lanes on
+                    // consecutive addresses
+                    auto e_at = [&](int u) {
+                        return dup ? static_cast<size_t>(i) * ldy + j0 + u : static_cast<size_t>(j0 + u) * ldy + i;
+                    };
+                    auto e1f = [&](int u) { return E1 ? E1[e_at(u)] : 0.0f; };
+                    auto e2f = [&](int u) { return E2 ? E2[e_at(u)] : 0.0f; };
                     // off-diagonal value of an output (diagonal form: per-row and
                     // per-column E coefficients)
                     auto offv = [&](const OutSpec &os, int u) -> float {
                         const float vv = acc[c8 * 8 + u] * inv;
                         if (!(os.flags & kOutDiag)) return fmaf(os.a, vv, fmaf(os.b1, e1f(u), os.b2 * e2f(u)));
                         const int j = j0 + u;
-                        float c1 = os.b1, c2 = os.b2;
-                        if (os.v1 >= 0) {
-                            const double *d1 = pr.dg[os.v1];
-                            c1 += os.g1r * static_cast<float>(d1[i]) + os.g1c * static_cast<float>(d1[j]);
-                        }
-                        if (os.v2 >= 0) {
-                            const double *d2 = pr.dg[os.v2];
-                            c2 += os.g2r * static_cast<float>(d2[i]) + os.g2c * static_cast<float>(d2[j]);
-                        }
+                        const float c1 = os.b1 + os.g1r * d1i + (F1 ? os.g1c * F1[j] : 0.0f);
+                        const float c2 = os.b2 + os.g2r * d2i + (F2 ? os.g2c * F2[j] : 0.0f);
                         return fmaf(os.a, vv, fmaf(c1, e1f(u), c2 * e2f(u)));
                     };
                     // diagonal entry of an output in the diagonal form, FP64
@@ -1015,6 +1062,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                                     // the diagonal goes to the FP64 vector; the small part keeps 0
                                     const double dv = diagv(os, u);
                                     pr.dg[os.mat][i] = dv;
+                                    pr.dgf[os.mat][i] = static_cast<float>(dv);
                                     if (o == pout) {
                                         tr += dv;
                                         sq += dv * dv;
@@ -1023,7 +1071,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                                 } else {
                                     val = offv(os, u) + ((on_diag && !dform) ? cdiag : 0.0f);
                                     if (!on_diag) {
-                                        if (fl & kOutMaster) m.master[static_cast<size_t>(j) * ldy + i] = val;
+                                        if ((fl & kOutMaster) && !dform) m.master[static_cast<size_t>(j) * ldy + i] = val;
                                         if (fl & kOutSlices) put_slices(m, static_cast<size_t>(j) * lds + i, val * os.s);
                                     }
                                     if (o == pout) {

@@ -158,6 +158,7 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
                 if (i == j || i == j + 1) {
                     const double dv = hb0 * (((i == j) ? h0 : h1) - mu0);
                     pr.dg[kMatZ][i] = dv;
+                    pr.dgf[kMatZ][i] = static_cast<float>(dv);
                     tr += dv;
                     sqd += dv * dv;
                 }

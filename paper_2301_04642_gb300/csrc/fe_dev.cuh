@@ -32,13 +32,13 @@ constexpr int kEpiWarps = 8;
 // split-FP16 kernel: warpgroup 0 (warp 0 TMA, warp 1 MMA, warps 2-3 idle) gives
 // registers to warpgroups 1-2 (8 drain + epilogue warps) with setmaxnreg.
 // The launch gives every thread kSymLaunchRegs (384 threads: at most 3 warps
-// per SM sub-partition of 16384 registers -> 168); 128 x 56 + 256 x 224 =
+// per SM sub-partition of 16384 registers -> 168); 128 x 40 + 256 x 232 =
 // 384 x 168, so the increase never waits for registers that are not there.
 constexpr int kSymThreads = 384;
 constexpr int kSymEpiWarp0 = 4;
 constexpr int kSymLaunchRegs = 168;
-constexpr int kSymRegsLow = 56;
-constexpr int kSymRegsHigh = 224;
+constexpr int kSymRegsLow = 40;
+constexpr int kSymRegsHigh = 232;
 static_assert(128 * kSymRegsLow + 256 * kSymRegsHigh == kSymThreads * kSymLaunchRegs,
               "register split must equal the launch allocation");
 constexpr int kPartStride = 4;    // doubles per partial slot: tr, sumsq, maxabs, spare

@@ -227,6 +227,24 @@ struct SolveState {
 };
 
 // ---------------------------------------------------------------- PTX wrappers
+// x to FP32, rounded to nearest (ties to even), by integer operations on the
+// FP64 encoding: GB300 runs FP64 arithmetic and FP64-to-FP32 conversions at a
+// small fraction of its FP32 rate, enough to make an HBM-bound pass over FP64
+// data arithmetic bound.  Values below FP32's normal range become 0, values
+// above it infinity (callers pass finite data of moderate range).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+    const int fe = static_cast<int>((hi >> 20) & 0x7FFu) - 896;  // FP32 exponent field
+    const unsigned sign = hi & 0x80000000u;
+    if (fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+    unsigned r = (static_cast<unsigned>(fe) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;  // the 29 dropped mantissa bits
+    if (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) r += 1u;  // a carry may raise the exponent
+    return __uint_as_float(sign | r);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

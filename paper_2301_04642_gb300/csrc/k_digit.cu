@@ -147,20 +147,50 @@ __global__ void k_digit_prep(const MmaProb *probs, int nprobs) {
         // thread (lds is even: one 4-byte store per digit array); off the
         // diagonal the FP32 iterate c I + Y is just Y, converted without FP64
         // arithmetic, and the diagonal takes the FP64 sum y + c
+        // four column pairs per thread are loaded before any is converted
+        // (enough bytes in flight for the HBM rate with 2 blocks per SM)
+        const int cs = 2 * blockDim.x;
+        const double c = st->c;
         for (int i = blockIdx.x; i < n; i += gridDim.x) {
-            for (int j = 2 * threadIdx.x; j < n; j += 2 * blockDim.x) {
-                const bool two = j + 1 < n;
-                long long V0, V1 = 0;
-                if (xf) {
-                    const double *X = pr.Xd[st->xcur] + static_cast<size_t>(i) * pr.ldx;
-                    V0 = fixed54(X[j]);
-                    if (two) V1 = fixed54(X[j + 1]);
-                } else {
-                    const float2 y2 = *reinterpret_cast<const float2 *>(pr.Y + static_cast<size_t>(i) * pr.ldy + j);
-                    V0 = (i == j) ? fixed54(static_cast<double>(y2.x) + st->c) : fixed54_f(y2.x);
-                    if (two) V1 = (i == j + 1) ? fixed54(static_cast<double>(y2.y) + st->c) : fixed54_f(y2.y);
+            const double *X = pr.Xd[st->xcur] + static_cast<size_t>(i) * pr.ldx;
+            const float *Yr = pr.Y + static_cast<size_t>(i) * pr.ldy;
+            for (int jb = 2 * threadIdx.x; jb < n; jb += 4 * cs) {
+                double a[4], b[4];  // FP64 iterate
+                float fa[4], fb[4];  // or the FP32 small part (no FP64 conversion off the diagonal)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = jb + q * cs;
+                    a[q] = 0.0;
+                    b[q] = 0.0;
+                    fa[q] = 0.0f;
+                    fb[q] = 0.0f;
+                    if (j < n) {
+                        if (xf) {
+                            a[q] = X[j];
+                            if (j + 1 < n) b[q] = X[j + 1];
+                        } else {
+                            const float2 y2 = *reinterpret_cast<const float2 *>(Yr + j);  // ldy even
+                            fa[q] = y2.x;
+                            fb[q] = y2.y;
+                        }
+                    }
                 }
-                put_digits2(pr, static_cast<size_t>(i) * pr.lds + j, V0, V1);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = jb + q * cs;
+                    if (j >= n) continue;
+                    const bool two = j + 1 < n;
+                    long long V0, V1 = 0;
+                    if (xf) {
+                        V0 = fixed54(a[q]);
+                        if (two) V1 = fixed54(b[q]);
+                    } else {
+                        // off the diagonal the FP32 iterate c I + Y is just Y
+                        V0 = (i == j) ? fixed54(static_cast<double>(fa[q]) + c) : fixed54_f(fa[q]);
+                        if (two) V1 = (i == j + 1) ? fixed54(static_cast<double>(fb[q]) + c) : fixed54_f(fb[q]);
+                    }
+                    put_digits2(pr, static_cast<size_t>(i) * pr.lds + j, V0, V1);
+                }
             }
         }
     }

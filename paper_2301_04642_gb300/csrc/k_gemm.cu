@@ -365,12 +365,13 @@ __global__ void __launch_bounds__(256) k_absmax(const double *__restrict__ X, lo
 
 namespace {
 
+// hi = fp16(s x), lo = fp16(s x - hi) with s x formed in FP32 (s a power of
+// two): hi + lo equals x to 2^-24 relative besides the FP32 rounding of x
 __device__ __forceinline__ void split_pair(double x0, double x1, float s, __half2 &h, __half2 &l) {
-    const double y0 = x0 * static_cast<double>(s), y1 = x1 * static_cast<double>(s);
-    h = __floats2half2_rn(static_cast<float>(y0), static_cast<float>(y1));
+    const float y0 = f64_to_f32_rn(x0) * s, y1 = f64_to_f32_rn(x1) * s;
+    h = __floats2half2_rn(y0, y1);
     const float2 back = __half22float2(h);
-    l = __floats2half2_rn(static_cast<float>(y0 - static_cast<double>(back.x)),
-                          static_cast<float>(y1 - static_cast<double>(back.y)));
+    l = __floats2half2_rn(y0 - back.x, y1 - back.y);
 }
 
 }  // namespace

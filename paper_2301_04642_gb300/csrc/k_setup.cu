@@ -153,8 +153,8 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
             if (fermi) {
                 // x = (beta0 / 2)(H - mu0 I) in the diagonal form: the diagonal
                 // in FP64 (d_Z), the small part zero on it
-                y0 = (i == j) ? 0.0f : hb0f * static_cast<float>(h0);
-                y1 = (i == j + 1) ? 0.0f : hb0f * static_cast<float>(h1);
+                y0 = (i == j) ? 0.0f : hb0f * f64_to_f32_rn(h0);
+                y1 = (i == j + 1) ? 0.0f : hb0f * f64_to_f32_rn(h1);
                 if (i == j || i == j + 1) {
                     const double dv = hb0 * (((i == j) ? h0 : h1) - mu0);
                     pr.dg[kMatZ][i] = dv;
@@ -165,8 +165,11 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
                 ms = &pr.mats[kMatZ];
                 sc = sz;
             } else {
-                y0 = (i == j) ? static_cast<float>(-h0 * inv_w + dshift) : -inv_wf * static_cast<float>(h0);
-                y1 = (i == j + 1) ? static_cast<float>(-h1 * inv_w + dshift) : -inv_wf * static_cast<float>(h1);
+                // FP64 arithmetic on the diagonal only
+                y0 = -inv_wf * f64_to_f32_rn(h0);
+                y1 = -inv_wf * f64_to_f32_rn(h1);
+                if (i == j) y0 = static_cast<float>(-h0 * inv_w + dshift);
+                if (i == j + 1) y1 = static_cast<float>(-h1 * inv_w + dshift);
                 ms = &pr.mats[kMatY0];
                 sc = s0;
             }

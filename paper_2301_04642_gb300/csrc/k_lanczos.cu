@@ -124,21 +124,6 @@ __device__ double tri_last_comp(const double *a, const double *b, int k, double 
 // the estimate needs no more (the certificate decides the bounds), and GB300
 // runs FP64 arithmetic at 1/64 of the FP32 rate.
 
-// H_ij to FP32, rounded toward zero, by integer operations on the FP64
-// encoding (no FP64 instruction); values below FP32's normal range become 0,
-// values above it infinity (Hp was checked for NaN/Inf beforehand)
-__device__ __forceinline__ float h_to_f32(double x) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
-    const int fe = static_cast<int>((hi >> 20) & 0x7FFu) - 896;  // FP32 exponent field
-    const unsigned sign = hi & 0x80000000u;
-    unsigned r;
-    if (fe <= 0) r = sign;
-    else if (fe >= 255) r = sign | 0x7F800000u;
-    else r = sign | (static_cast<unsigned>(fe) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-    return __uint_as_float(r);
-}
-
 // v = fixed pseudo-random unit vector, v_prev = 0 (one block of 1024 threads
 // per problem, blockIdx.x)
 __global__ void k_lanczos_start(const MmaProb *probs, int k0) {
@@ -167,10 +152,9 @@ __global__ void k_lanczos_start(const MmaProb *probs, int k0) {
 
 // w = H v, one warp per row (kLzThreads / 32 rows per block, kLzBlocks blocks
 // per problem, blockIdx.y); per-block partial of w . v in the partial slots.
-// The row is read as 16-byte pairs (after one peeled element when the row
-// starts off a 16-byte boundary), four pairs per lane in flight, so that the
-// rows an SM holds keep enough loads outstanding to stream H at HBM speed;
-// v is read through L1.
+// H is read from its FP32 copy in the problem's FP32 master (written by
+// k_bounds_rows; rows 16-byte aligned, ld a multiple of 4) as 16-byte
+// quadruples, four per lane in flight; v is read through L1.
 __global__ void __launch_bounds__(kLzThreads) k_lanczos_matvec(const MmaProb *probs, int k0) {
     const MmaProb &pr = probs[k0 + blockIdx.y];
     const SolveState *st = pr.st;
@@ -182,28 +166,23 @@ __global__ void __launch_bounds__(kLzThreads) k_lanczos_matvec(const MmaProb *pr
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double part = 0.0;
     for (int row = blockIdx.x * kWarps + wid; row < n; row += gridDim.x * kWarps) {
-        const double *h = pr.H + static_cast<size_t>(row) * pr.ldh;
-        const int j0 = (reinterpret_cast<uintptr_t>(h) & 15u) ? 1 : 0;
-        const int m = (n - j0) >> 1;  // 16-byte pairs
-        const double2 *h2 = reinterpret_cast<const double2 *>(h + j0);
-        const float *vj = v + j0;
+        const float *h = pr.Y + static_cast<size_t>(row) * pr.ldy;
+        const int m = n >> 2;  // 16-byte quadruples
+        const float4 *h4 = reinterpret_cast<const float4 *>(h);
         float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
         int k = lane;
+        auto dot4 = [&](const float4 a, int q, float acc) {
+            return fmaf(a.x, v[4 * q], fmaf(a.y, v[4 * q + 1], fmaf(a.z, v[4 * q + 2], fmaf(a.w, v[4 * q + 3], acc))));
+        };
         for (; k + 96 < m; k += 128) {
-            const double2 a0 = h2[k], a1 = h2[k + 32], a2 = h2[k + 64], a3 = h2[k + 96];
-            s0 = fmaf(h_to_f32(a0.x), vj[2 * k], fmaf(h_to_f32(a0.y), vj[2 * k + 1], s0));
-            s1 = fmaf(h_to_f32(a1.x), vj[2 * k + 64], fmaf(h_to_f32(a1.y), vj[2 * k + 65], s1));
-            s2 = fmaf(h_to_f32(a2.x), vj[2 * k + 128], fmaf(h_to_f32(a2.y), vj[2 * k + 129], s2));
-            s3 = fmaf(h_to_f32(a3.x), vj[2 * k + 192], fmaf(h_to_f32(a3.y), vj[2 * k + 193], s3));
+            const float4 a0 = h4[k], a1 = h4[k + 32], a2 = h4[k + 64], a3 = h4[k + 96];
+            s0 = dot4(a0, k, s0);
+            s1 = dot4(a1, k + 32, s1);
+            s2 = dot4(a2, k + 64, s2);
+            s3 = dot4(a3, k + 96, s3);
         }
-        for (; k < m; k += 32) {
-            const double2 a0 = h2[k];
-            s0 = fmaf(h_to_f32(a0.x), vj[2 * k], fmaf(h_to_f32(a0.y), vj[2 * k + 1], s0));
-        }
-        if (lane == 0) {
-            if (j0) s1 = fmaf(h_to_f32(h[0]), v[0], s1);
-            if ((n - j0) & 1) s2 = fmaf(h_to_f32(h[n - 1]), v[n - 1], s2);
-        }
+        for (; k < m; k += 32) s0 = dot4(h4[k], k, s0);
+        for (int jj = 4 * m + lane; jj < n; jj += 32) s1 = fmaf(h[jj], v[jj], s1);
         const double s = warp_sum(static_cast<double>((s0 + s1) + (s2 + s3)));
         if (lane == 0) {
             w[row] = static_cast<float>(s);

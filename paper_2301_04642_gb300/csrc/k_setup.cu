@@ -30,13 +30,22 @@ __global__ void k_bounds_rows(const MmaProb *probs, int prob, RowInfo *rowinfo, 
     unsigned long long mxb = 0, nonfin = 0;
     // four loads per lane in flight: the 128 to 2048 rows an SM holds must
     // keep enough bytes outstanding to stream Hp at HBM speed
+    // The row also goes to the FP32 master as an FP32 copy of Hp for the
+    // Lanczos matvecs (read 12 times; at 4n^2 bytes it stays in L2 up to
+    // n ~ 5600); the master is free until X0 is written.
+    float *yrow = pr.Y + static_cast<long long>(row) * pr.ldy;
     int j = lane;
     double s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (; j + 96 < pr.n; j += 128) {
-        const unsigned long long b0 = static_cast<unsigned long long>(__double_as_longlong(h[j])) & kAbs;
-        const unsigned long long b1 = static_cast<unsigned long long>(__double_as_longlong(h[j + 32])) & kAbs;
-        const unsigned long long b2 = static_cast<unsigned long long>(__double_as_longlong(h[j + 64])) & kAbs;
-        const unsigned long long b3 = static_cast<unsigned long long>(__double_as_longlong(h[j + 96])) & kAbs;
+        const double h0 = h[j], h1 = h[j + 32], h2 = h[j + 64], h3 = h[j + 96];
+        yrow[j] = f64_to_f32_rn(h0);
+        yrow[j + 32] = f64_to_f32_rn(h1);
+        yrow[j + 64] = f64_to_f32_rn(h2);
+        yrow[j + 96] = f64_to_f32_rn(h3);
+        const unsigned long long b0 = static_cast<unsigned long long>(__double_as_longlong(h0)) & kAbs;
+        const unsigned long long b1 = static_cast<unsigned long long>(__double_as_longlong(h1)) & kAbs;
+        const unsigned long long b2 = static_cast<unsigned long long>(__double_as_longlong(h2)) & kAbs;
+        const unsigned long long b3 = static_cast<unsigned long long>(__double_as_longlong(h3)) & kAbs;
         nonfin |= ((b0 & kExp) == kExp) | ((b1 & kExp) == kExp) | ((b2 & kExp) == kExp) | ((b3 & kExp) == kExp);
         s += __longlong_as_double(static_cast<long long>(b0));
         s1 += __longlong_as_double(static_cast<long long>(b1));
@@ -45,7 +54,9 @@ __global__ void k_bounds_rows(const MmaProb *probs, int prob, RowInfo *rowinfo, 
         mxb = max(max(mxb, b0), max(b1, max(b2, b3)));
     }
     for (; j < pr.n; j += 32) {
-        const unsigned long long b0 = static_cast<unsigned long long>(__double_as_longlong(h[j])) & kAbs;
+        const double h0 = h[j];
+        yrow[j] = f64_to_f32_rn(h0);
+        const unsigned long long b0 = static_cast<unsigned long long>(__double_as_longlong(h0)) & kAbs;
         nonfin |= ((b0 & kExp) == kExp);
         s += __longlong_as_double(static_cast<long long>(b0));
         mxb = max(mxb, b0);

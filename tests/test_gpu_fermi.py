@@ -113,3 +113,23 @@ def test_fermi_serving_sizes(n, kT, seed):
     eps1 = float(torch.sqrt((err ** 2).sum() / 16)) / math.sqrt(ne)
     print(n, kT, r["iters"], r["iters_by_phase"], eps1)
     assert eps1 <= TOL_EPS1
+
+
+@pytest.mark.parametrize("kT", [0.001, 0.006])
+def test_fermi_nearly_diagonal_hp_matches_oracle(kT):
+    """Hp = Q diag(lambda) Q^T with Q from 8 Householder reflectors (diagonal
+    plus a rank-16 perturbation, eigenvectors mostly localised): the case in
+    which the expansion's diagonal form keeps each near-mu eigenvalue's
+    diagonal entry in FP64.  Against the oracle's own eigensolver and
+    Fermi-Dirac occupations at n = 1200."""
+    n, ne = 1200, 1020.0
+    p = hp_synth.smeared_reflected(n, ne, kT, -2.0, 1.0, 91)
+    H = np.asarray(p.H.cpu().numpy() if hasattr(p.H, "cpu") else p.H, dtype=np.float64)
+    D = np.zeros_like(H)
+    r = ctx().solve(H, ne, kT=kT, D=D)
+    ref = oracle.density(H, ne, kT)
+    eps1 = np.linalg.norm(D - ref["D"]) / math.sqrt(ne)
+    print(kT, r["iters"], eps1)
+    assert r["status"] == 0
+    assert eps1 <= TOL_EPS1 and abs(r["e_band"] - ref["e_band"]) / ne <= TOL_E
+    assert abs(np.trace(D) - ne) <= TOL_TR

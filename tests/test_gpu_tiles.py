@@ -86,10 +86,17 @@ def test_zero_t_solve_narrow_tiles(cx, n, ne, precision):
     if precision == "mixed":
         check_zero_t(p, D, res)
     else:
-        # split-FP16 products only: the trace is matched, idempotency to the
-        # 22-bit level of the products
+        # split-FP16 products only: D and the band energy within the FP64
+        # tolerances, the trace matched, idempotency at the 22-bit level of
+        # the products (the split phase stops once ||X^2 - X||_F <= 2^-20
+        # sqrt(N_e); its last product at most doubles one side's deviations)
         assert res["status"] == 0
+        f = (np.arange(n) < ne).astype(float)
+        Dref = oracle.density_from_eig(p.Q, f)
+        assert np.linalg.norm(D - Dref) / math.sqrt(ne) <= TOL_EPS1
+        assert abs(res["e_band"] - float(np.sum(f * p.lam))) / ne <= TOL_E
         assert abs(np.trace(D) - p.ne) <= 1e-6 * p.ne
+        assert np.linalg.norm(oracle.matmul(D, D) - D) <= 4.0 * 2.0 ** -20 * math.sqrt(ne)
 
 
 def test_fermi_solve_narrow_tiles(cx):

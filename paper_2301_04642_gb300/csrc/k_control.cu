@@ -17,7 +17,7 @@
 // Finite temperature (Sec. II-A Fermi-Dirac target, recursive expansion of
 // Sec. II-B3): z = I - 2D = tanh(beta (H - mu)/2).  Starting from
 // z0 = tanh((beta0/2)(H - mu0 I)) at beta0 = beta / 2^m (the paper's
-// expansion starts from the linear term; here five products evaluate a
+// expansion starts from the linear term; here six products evaluate a
 // Taylor polynomial of tanh instead, see control_fermi_start), every stage
 // doubles beta with the double-angle identity of tanh, folding in a shift of
 // mu (logit shift b, t = tanh b) chosen by a Newton step so that tr D tracks

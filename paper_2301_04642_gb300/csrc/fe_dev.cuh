@@ -166,6 +166,8 @@ struct SolveState {
     double fb[6];     // bounds on ||A~||_F (slice scales are derived from them)
     float scl[6];     // slice scale s of each slot's FP16 slices (slices hold s A~)
     double ft_t, w0;  // tanh of the current shift; Newton-Schulz start
+    double mu_prev;   // mu(T) of the previous tracked stage (the drift prediction)
+    int mu_nconv, mu_pad;
     double tr_d0, tr_q;  // traces of D0 = (I - z)/2 and Q = (I - z^2)/4 at the end
     // spectral bounds used by the expansion (Lanczos estimate within the
     // Gershgorin interval, or Gershgorin itself) and Hp statistics

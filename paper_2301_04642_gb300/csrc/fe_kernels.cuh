@@ -142,6 +142,8 @@ __device__ __forceinline__ void setup_from_bounds(const MmaProb &pr, SolveState 
         st->ft_m = m;
         st->beta0 = ldexp(beta, -m);
         st->mu_t = mu0;
+        st->mu_prev = mu0;
+        st->mu_nconv = 0;
         st->sc[kMatZ] = 0.0;
         int ez;
         frexp(fmax(st->beta0 * rad / 2.0, 1e-300) * 1.0001, &ez);

@@ -861,6 +861,20 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
     // have small z, so M is close to I and Newton-Schulz needs few or no steps.
     const double rad = fmax(fabs(st->emax - st->mu_t), fabs(st->emin - st->mu_t));
     const double rho = fmin(1.0, tanh(0.5 * beta_k * rad) * (1.0 + 1e-6) + 1e-6);
+    if (!shift_only && st->ft_phase != 0) {
+        // The doubling halves T, and mu(T) moves with it.  mu(beta_k) is the
+        // current estimate corrected by the Newton step; from the second
+        // tracked stage on, the next stage's mu is predicted from the last
+        // two: mu(T) - mu(0) goes as T^2 at low T (Sommerfeld), so each
+        // halving of T quarters the change, mu_{k+1} - mu_k = (mu_k - mu_{k-1})/4.
+        // Folding that drift into the shift spares the shift-only steps that
+        // would otherwise correct it at the next stage.
+        const double bn = fmax(-0.5, fmin(0.5, b));
+        const double mu_k = st->mu_t + 2.0 * bn / beta_k;
+        if (st->mu_nconv >= 1) b = bn + 0.5 * beta_k * 0.25 * (mu_k - st->mu_prev);
+        st->mu_prev = mu_k;
+        st->mu_nconv += 1;
+    }
     b = shift_only ? fmax(-1.0, fmin(1.0, b)) : fmax(-0.5, fmin(0.5, b));
     const double t = tanh(b);
     st->ft_t = t;

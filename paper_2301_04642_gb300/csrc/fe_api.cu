@@ -150,6 +150,7 @@ struct fe_ctx {
     int max_iters = 100;
     uint32_t prec_default = FE_PREC_MIXED;
     int num_sms = 148;
+    int lz_grid = 0;                 // blocks of the cooperative Lanczos launch (all resident)
     Engine eng;                      // blocking solves and batches
     std::mutex smu;                  // slots, used
     std::vector<Slot *> slots;
@@ -795,15 +796,22 @@ int eng_setup(fe_ctx *ctx, Engine &e, const std::vector<Job> &jobs, int k0, int 
     }
     const bool any_lz = !tc_chk.empty() || !f64_chk.empty();
     if (any_lz) {
-        // the estimate of every problem that takes one, all at once (the
-        // kernels skip problems without lz_on)
-        k_lanczos_start<<<m, 1024, 0, s>>>(e.d_probs, k0);
-        for (int it = 0; it < kLanczosSteps; ++it) {
-            k_lanczos_matvec<<<dim3(kLzBlocks, m), kLzThreads, 0, s>>>(e.d_probs, k0);
-            k_lanczos_update<<<m, 1024, 0, s>>>(e.d_probs, k0, it);
-        }
-        k_bounds_finish<<<m, 32, 0, s>>>(e.d_probs, k0, ctx->lz_narrow.load(std::memory_order_relaxed));
-        ctx->launches += 2 + 2 * kLanczosSteps;
+        // the estimate of every problem that takes one, all at once in one
+        // cooperative launch (the kernel skips problems without lz_on)
+        int vmax = 0;
+        for (int k : tc_chk) vmax = std::max(vmax, static_cast<int>(jobs[k].p->n));
+        for (int k : f64_chk) vmax = std::max(vmax, static_cast<int>(jobs[k].p->n));
+        int vcap = std::min(vmax, kLzVcap);
+        double narrow = ctx->lz_narrow.load(std::memory_order_relaxed);
+        const MmaProb *probs = e.d_probs;
+        DevCtl *ctl = e.d_err;
+        unsigned *bar = &e.d_err->lz_bar;
+        int kk0 = k0, mm = m;
+        void *args[] = {&probs, &kk0, &mm, &vcap, &narrow, &ctl, &bar};
+        FE_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
+        FE_CUDA(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_lanczos_run), dim3(ctx->lz_grid),
+                                                 dim3(kLzThreads), args, sizeof(float) * vcap, s));
+        ctx->launches += 1;
     }
     for (int k = k0; k < k1; ++k) k_init_x0<<<kInitBlocks, 256, 0, s>>>(e.d_probs, k);
     ctx->launches += m;
@@ -1514,8 +1522,23 @@ extern "C" int fe_create(fe_ctx **out, const fe_config *cfg) {
                         cudaFuncSetAttribute(k_digit_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(digit_smem_bytes())) != cudaSuccess ||
                         cudaFuncSetAttribute(k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(gemm_smem_bytes())) != cudaSuccess))
+                                             static_cast<int>(gemm_smem_bytes())) != cudaSuccess ||
+                        cudaFuncSetAttribute(k_lanczos_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(sizeof(float) * kLzVcap)) != cudaSuccess))
         rc = set_err(nullptr, FE_ECUDA, std::string("context setup: ") + cudaGetErrorString(cudaGetLastError()));
+    if (rc == FE_OK) {
+        // the Lanczos launch waits at grid barriers, so all its blocks must be
+        // resident at once: a cooperative launch no larger than the occupancy
+        // allows with the largest staged vector
+        int coop = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c.device) != cudaSuccess || !coop ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lanczos_run, kLzThreads,
+                                                          sizeof(float) * kLzVcap) != cudaSuccess ||
+            per_sm < 1)
+            rc = set_err(nullptr, FE_ECUDA, "cooperative launch of k_lanczos_run unavailable");
+        else
+            ctx->lz_grid = std::min(kLzBlocks, per_sm * ctx->num_sms);
+    }
     if (rc == FE_OK) {
         // the register hand-off inside the split-FP16 kernel assumes this allocation
         cudaFuncAttributes fa;

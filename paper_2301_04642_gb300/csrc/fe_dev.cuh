@@ -63,6 +63,7 @@ enum DevErr : int {
     kErrTimeoutTmem = 3,    // accumulator hand-off never happened
     kErrBadInput = 4,
     kErrTimeoutPartner = 5, // the partial sums of a split tile never arrived
+    kErrTimeoutGrid = 6,    // a grid barrier of a cooperative launch never completed
 };
 
 // bounded waits give up after this many nanoseconds of wall time unless the
@@ -71,7 +72,9 @@ constexpr uint64_t kWaitTimeoutNs = 2000000000ull;
 
 // Device control block of one engine, passed to the kernels that wait: the
 // first error code of the run (the host clears it before each run), the
-// limit of every bounded wait, and a test hook.  With fail_partner set, the
+// limit of every bounded wait, the arrival counter of the grid barriers of
+// the cooperative Lanczos launch (zeroed before it), and a test hook.  With
+// fail_partner set, the
 // wait of the second CTA of a split tile in k_sym_mma watches `never` (a word
 // nothing writes) instead of its partner's flag, so the wait runs out, the
 // kernel records kErrTimeoutPartner and returns; it exists to test that
@@ -82,6 +85,8 @@ struct DevCtl {
     int never;
     int pad;
     unsigned long long wait_ns;
+    unsigned lz_bar;
+    unsigned pad2;
 };
 
 constexpr int kHistRows = 160;  // per-step history kept in the solve state

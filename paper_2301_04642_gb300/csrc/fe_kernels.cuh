@@ -91,21 +91,24 @@ __global__ void k_bounds_rows(const MmaProb *probs, int prob, RowInfo *rowinfo, 
 // the Lanczos estimate off it also prepares X0 from the Gershgorin bounds.
 __global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *rowinfo,
                                 const int *bad);
-// Spectral-bound estimate by kLanczosSteps Lanczos steps (FP64) for the
-// problems k0 .. k0 + (blocks or grid rows) - 1 that have lz_on: start
-// vector, then per step w = H v (kLzBlocks blocks of kLzThreads per problem,
-// partial dot products) and the three-term update (one block per problem);
-// k_bounds_finish turns the tridiagonal into the estimate and prepares X0 on
-// it.  narrow < 1 shrinks the estimate about its centre by that factor (a test
-// hook that forces the too-tight case).
+// Spectral-bound estimate by kLanczosSteps Lanczos steps for the problems
+// k0 .. k0 + m - 1 that have lz_on, in one cooperative launch of at most
+// kLzBlocks blocks of kLzThreads (all resident at once; the host launches it
+// with cudaLaunchCooperativeKernel after zeroing ctl->lz_bar): the start
+// vector, then per step w = H v by every block (one warp per row, per-block
+// partial dot products; v staged in `vcap` floats of dynamic shared memory
+// when n <= vcap), a grid barrier, the three-term update (one block per
+// problem), a grid barrier; at the end the tridiagonal is turned into the
+// estimate and X0 is prepared on it.  Every barrier wait is bounded
+// (kErrTimeoutGrid).  narrow < 1 shrinks the estimate about its centre by that
+// factor (a test hook that forces the too-tight case).
 constexpr int kLzBlocks = 304;
 constexpr int kLzThreads = 512;
-__global__ void k_lanczos_start(const MmaProb *probs, int k0);
-__global__ void k_lanczos_matvec(const MmaProb *probs, int k0);
-__global__ void k_lanczos_update(const MmaProb *probs, int k0, int j);
-__global__ void k_bounds_finish(const MmaProb *probs, int k0, double narrow);
+constexpr int kLzVcap = 24576;  // largest v staged in shared memory (96 KiB)
+__global__ void k_lanczos_run(const MmaProb *probs, int k0, int m, int vcap, double narrow, DevCtl *ctl,
+                              unsigned *bar);
 // Certified bounds from the certificate steps (kCheckSteps products issued by
-// k_control after k_bounds_finish), then the X0 preparation; one block per
+// k_control after k_lanczos_run), then the X0 preparation; one block per
 // problem from k0.
 __global__ void k_check_bounds(const MmaProb *probs, int k0);
 // X0 = (hi I - Hp)/(hi - lo) stored as c0 I + Y0 (its slice scale from a bound
@@ -185,7 +188,7 @@ __global__ void k_digit_prep(const MmaProb *probs, int nprobs);
 __global__ void k_make_slices(const float *Y, int n, int ldy, float s, __half *hi, __half *lo,
                               int lds);
 
-constexpr int kInitBlocks = 304;   // 2 x 152 SMs
+constexpr int kInitBlocks = 608;   // 4 x 152 SMs (k_init_x0: 8 warps each, one row per warp)
 constexpr int kFinBlocks = 304;
 constexpr int kTile64 = 64;
 

@@ -129,7 +129,10 @@ __device__ void control_check(SolveState *st, double trV, double sumsq) {
     const double s = st->s_cur;
     begin_op(op, cur, cur, cur, -1, 1.0 / (s * s));
     op.nout = 1;
-    set_out(op.out[0], cur ^ 1, kOutMaster | kOutSlices, -4.0, alpha, 0.0, 0.0, bound);
+    // the last step's matrix is not used again, only its trace and Frobenius
+    // norm (X0 is prepared afresh on the certified bounds): no stores
+    const int fl = (st->chk_left == 0) ? 0 : (kOutMaster | kOutSlices);
+    set_out(op.out[0], cur ^ 1, fl, -4.0, alpha, 0.0, 0.0, bound);
     st->s_next = op.out[0].s;
 }
 

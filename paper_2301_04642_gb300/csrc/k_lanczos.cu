@@ -117,22 +117,54 @@ __device__ double tri_last_comp(const double *a, const double *b, int k, double 
 
 }  // namespace
 
-// Every kernel below serves the problems k0 + b of the table (b = the block
-// index named in each) that estimate their bounds (lz_on); the others return.
-
 // The recurrence runs in FP32 (vectors, H entries, products) with FP64 sums:
 // the estimate needs no more (the certificate decides the bounds), and GB300
 // runs FP64 arithmetic at 1/64 of the FP32 rate.
 
-// v = fixed pseudo-random unit vector, v_prev = 0 (one block of 1024 threads
-// per problem, blockIdx.x)
-__global__ void k_lanczos_start(const MmaProb *probs, int k0) {
-    const MmaProb &pr = probs[k0 + blockIdx.x];
+namespace {
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier number k of a cooperative launch: complete once all nb blocks
+// arrived, i.e. the arrival counter (zeroed before the launch) reaches
+// (k + 1) nb.  The wait is bounded: when it runs out the block records
+// kErrTimeoutGrid and every caller returns false (the blocks still running
+// give up at their own next barrier).
+__device__ bool grid_barrier(unsigned *cnt, unsigned k, unsigned nb, DevCtl *ctl, int *flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(cnt, 1u);
+        const unsigned target = (k + 1u) * nb;
+        bool ok = true;
+        if (ld_acquire_u32(cnt) < target) {
+            const uint64_t lim = ctl->wait_ns, t0 = globaltimer();
+            while (ld_acquire_u32(cnt) < target) {
+                if (globaltimer() - t0 > lim) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (!ok) atomicCAS(&ctl->err, 0, kErrTimeoutGrid);
+        __threadfence();
+        *flag = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+// v = fixed pseudo-random unit vector, v_prev = 0 (the whole block)
+__device__ void lz_start(const MmaProb &pr, double *sh) {
     SolveState *st = pr.st;
     if (!st->lz_on) return;
     const int n = pr.n;
     float *vp = pr.lzv, *v = pr.lzv + n;
-    __shared__ double sh[1024];
     double ss = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float x = static_cast<float>(static_cast<double>(mix64(0xF00Dull + static_cast<uint64_t>(i)) >> 11) *
@@ -150,20 +182,21 @@ __global__ void k_lanczos_start(const MmaProb *probs, int k0) {
     }
 }
 
-// w = H v, one warp per row (kLzThreads / 32 rows per block, kLzBlocks blocks
-// per problem, blockIdx.y); per-block partial of w . v in the partial slots.
-// H is read from its FP32 copy in the problem's FP32 master (written by
-// k_bounds_rows; rows 16-byte aligned, ld a multiple of 4) as 16-byte
-// quadruples, four per lane in flight; v is read through L1.
-__global__ void __launch_bounds__(kLzThreads) k_lanczos_matvec(const MmaProb *probs, int k0) {
-    const MmaProb &pr = probs[k0 + blockIdx.y];
-    const SolveState *st = pr.st;
-    if (!st->lz_on || st->lz_k < 0) return;  // no estimate, or the recurrence stopped early
-    const int n = pr.n;
-    const float *v = pr.lzv + n;
-    float *w = pr.lzv + 2 * static_cast<size_t>(n);
+// This block's share of w = H v: rows blockIdx.x * kWarps + warp, stepping
+// by the grid's warps, one warp per row.  H is read from its FP32 copy in the
+// problem's FP32 master (written by k_bounds_rows; rows 16-byte aligned, ld a
+// multiple of 4) as 16-byte quadruples, four per lane in flight.  v comes
+// from shared memory when `vs` holds it, else from L2 (ld.cg: another block
+// wrote it since this launch began, so L1 may hold a stale copy).  The
+// block's partial of w . v goes to its partial slot.
+template <bool kStaged>
+__device__ void lz_matvec(const MmaProb &pr, const float *vs, double *red) {
     constexpr int kWarps = kLzThreads / 32;
+    const int n = pr.n;
+    const float *v = kStaged ? vs : pr.lzv + n;
+    float *w = pr.lzv + 2 * static_cast<size_t>(n);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    auto vat = [&](int i) { return kStaged ? v[i] : __ldcg(v + i); };
     double part = 0.0;
     for (int row = blockIdx.x * kWarps + wid; row < n; row += gridDim.x * kWarps) {
         const float *h = pr.Y + static_cast<size_t>(row) * pr.ldy;
@@ -172,7 +205,7 @@ __global__ void __launch_bounds__(kLzThreads) k_lanczos_matvec(const MmaProb *pr
         float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
         int k = lane;
         auto dot4 = [&](const float4 a, int q, float acc) {
-            return fmaf(a.x, v[4 * q], fmaf(a.y, v[4 * q + 1], fmaf(a.z, v[4 * q + 2], fmaf(a.w, v[4 * q + 3], acc))));
+            return fmaf(a.x, vat(4 * q), fmaf(a.y, vat(4 * q + 1), fmaf(a.z, vat(4 * q + 2), fmaf(a.w, vat(4 * q + 3), acc))));
         };
         for (; k + 96 < m; k += 128) {
             const float4 a0 = h4[k], a1 = h4[k + 32], a2 = h4[k + 64], a3 = h4[k + 96];
@@ -182,14 +215,13 @@ __global__ void __launch_bounds__(kLzThreads) k_lanczos_matvec(const MmaProb *pr
             s3 = dot4(a3, k + 96, s3);
         }
         for (; k < m; k += 32) s0 = dot4(h4[k], k, s0);
-        for (int jj = 4 * m + lane; jj < n; jj += 32) s1 = fmaf(h[jj], v[jj], s1);
+        for (int jj = 4 * m + lane; jj < n; jj += 32) s1 = fmaf(h[jj], vat(jj), s1);
         const double s = warp_sum(static_cast<double>((s0 + s1) + (s2 + s3)));
         if (lane == 0) {
             w[row] = static_cast<float>(s);
-            part += s * static_cast<double>(v[row]);
+            part += s * static_cast<double>(vat(row));
         }
     }
-    __shared__ double red[kWarps];
     if (lane == 0) red[wid] = part;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -197,26 +229,25 @@ __global__ void __launch_bounds__(kLzThreads) k_lanczos_matvec(const MmaProb *pr
         for (int q = 0; q < kWarps; ++q) a += red[q];
         pr.part[static_cast<size_t>(blockIdx.x) * kPartStride] = a;
     }
+    __syncthreads();
 }
 
-// alpha_j = w . v; w' = w - alpha_j v - beta_j v_prev; beta_{j+1} = ||w'||;
-// v_prev <- v, v <- w' / beta_{j+1} (one block of 1024 threads per problem,
-// blockIdx.x)
-__global__ void k_lanczos_update(const MmaProb *probs, int k0, int j) {
-    const MmaProb &pr = probs[k0 + blockIdx.x];
+// alpha_j = w . v (the blocks' partials, in block order); w' = w - alpha_j v
+// - beta_j v_prev; beta_{j+1} = ||w'||; v_prev <- v, v <- w' / beta_{j+1}
+// (the whole block; everything another block wrote is read through L2)
+__device__ void lz_update(const MmaProb &pr, int j, double *sh) {
     SolveState *st = pr.st;
-    if (!st->lz_on || st->lz_k < 0) return;
     const int n = pr.n;
     float *vp = pr.lzv, *v = pr.lzv + n, *w = pr.lzv + 2 * static_cast<size_t>(n);
-    __shared__ double sh[1024];
     double a = 0.0;
-    for (int b = threadIdx.x; b < kLzBlocks; b += blockDim.x) a += pr.part[static_cast<size_t>(b) * kPartStride];
+    for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += blockDim.x)
+        a += __ldcg(pr.part + static_cast<size_t>(b) * kPartStride);
     const double alpha = block_sum_1024(a, sh);
     const double beta = st->lz_b[j];
     const float af = static_cast<float>(alpha), bf = static_cast<float>(beta);
     float ssf = 0.0f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float x = fmaf(-af, v[i], fmaf(-bf, vp[i], w[i]));
+        const float x = fmaf(-af, v[i], fmaf(-bf, vp[i], __ldcg(w + i)));
         w[i] = x;
         ssf = fmaf(x, x, ssf);
     }
@@ -234,12 +265,9 @@ __global__ void k_lanczos_update(const MmaProb *probs, int k0, int j) {
     }
 }
 
-// bounds from the tridiagonal, then the X0 preparation (one thread per
-// problem, blockIdx.x)
-__global__ void k_bounds_finish(const MmaProb *probs, int k0, double narrow) {
-    const MmaProb &pr = probs[k0 + blockIdx.x];
+// bounds from the tridiagonal, then the X0 preparation (warp 0 of the block)
+__device__ void lz_finish(const MmaProb &pr, double narrow) {
     SolveState *st = pr.st;
-    if (!st->lz_on) return;
     const int lane = threadIdx.x & 31;
     const int k = st->lz_k < 0 ? -st->lz_k : st->lz_k;
     const double glo = st->gersh_lo, ghi = st->gersh_hi;
@@ -267,6 +295,7 @@ __global__ void k_bounds_finish(const MmaProb *probs, int k0, double narrow) {
             hi = ghi;
         }
     }
+    __syncwarp();
     if (lane != 0) return;
     if (narrow < 1.0) {
         const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo) * narrow;
@@ -278,6 +307,49 @@ __global__ void k_bounds_finish(const MmaProb *probs, int k0, double narrow) {
     st->lz_hi = hi;
     st->chk_left = kCheckSteps;
     setup_from_bounds(pr, st, lo, hi);
+}
+
+}  // namespace
+
+// The whole estimate in one cooperative launch (see fe_kernels.cuh).  Block b
+// starts, updates and finishes the problems b, b + grid, ...; every block
+// takes part in every product.  Each product and each update ends at a grid
+// barrier; a problem whose recurrence stopped (lz_k < 0, written by its
+// updating block before the barrier) is skipped from then on.
+__global__ void __launch_bounds__(kLzThreads, 2)
+    k_lanczos_run(const MmaProb *probs, int k0, int m, int vcap, double narrow, DevCtl *ctl, unsigned *bar) {
+    extern __shared__ float vs[];  // v of the problem in hand, when n <= vcap
+    __shared__ double sh[kLzThreads];
+    __shared__ int flag;
+    const unsigned nb = gridDim.x;
+    unsigned nbar = 0;
+    for (int q = blockIdx.x; q < m; q += nb) lz_start(probs[k0 + q], sh);
+    if (!grid_barrier(bar, nbar++, nb, ctl, &flag)) return;
+    for (int j = 0; j < kLanczosSteps; ++j) {
+        for (int q = 0; q < m; ++q) {
+            const MmaProb &pr = probs[k0 + q];
+            const SolveState *st = pr.st;
+            if (!st->lz_on || *reinterpret_cast<const volatile int *>(&st->lz_k) < 0) continue;
+            const int n = pr.n;
+            if (n <= vcap) {
+                for (int i = threadIdx.x; i < n; i += blockDim.x) vs[i] = __ldcg(pr.lzv + n + i);
+                __syncthreads();
+                lz_matvec<true>(pr, vs, sh);
+            } else {
+                lz_matvec<false>(pr, vs, sh);
+            }
+        }
+        if (!grid_barrier(bar, nbar++, nb, ctl, &flag)) return;
+        for (int q = blockIdx.x; q < m; q += nb) {
+            const MmaProb &pr = probs[k0 + q];
+            if (pr.st->lz_on && pr.st->lz_k >= 0) lz_update(pr, j, sh);
+            __syncthreads();
+        }
+        if (!grid_barrier(bar, nbar++, nb, ctl, &flag)) return;
+    }
+    if (threadIdx.x < 32)
+        for (int q = blockIdx.x; q < m; q += nb)
+            if (probs[k0 + q].st->lz_on) lz_finish(probs[k0 + q], narrow);
 }
 
 // Certified bounds from the check steps, then the X0 preparation (one thread

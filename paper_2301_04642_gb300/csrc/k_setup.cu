@@ -8,6 +8,7 @@
 //     tr(Hp D) = sum_ij Hp_ij D_ij (Sec. III-C) and tr D.
 // Every reduction is a fixed-order tree, so results are bitwise reproducible.
 #include <cfloat>
+#include <type_traits>
 
 #include "fe_dev.cuh"
 #include "fe_kernels.cuh"
@@ -111,7 +112,7 @@ __global__ void k_bounds_reduce(const MmaProb *probs, int prob, const RowInfo *r
 
 // Y0 = X0 - c0 I with X0 = (eps_max I - Hp) / w; FP32 master + FP16 slices of s0 Y0.
 // For the all-FP64 schedule X0 itself goes to Xd[0] in FP64.
-__global__ void k_init_x0(const MmaProb *probs, int prob) {
+__global__ void __launch_bounds__(256, 4) k_init_x0(const MmaProb *probs, int prob) {
     const MmaProb &pr = probs[prob];
     SolveState *st = pr.st;
     const int n = pr.n;
@@ -130,109 +131,129 @@ __global__ void k_init_x0(const MmaProb *probs, int prob) {
     // summed in FP32 over its columns of one row (at most n / blockDim terms),
     // then in FP64 across rows
     const float inv_wf = static_cast<float>(inv_w), hb0f = static_cast<float>(hb0);
+    // everything the loop needs, read once: the stores below could alias the
+    // problem table as far as the compiler knows, which would reload these
+    // after every store
+    const MatSlot &msl = pr.mats[fermi ? kMatZ : kMatY0];
+    float *const mbase = msl.master;
+    __half *const s0base = msl.sl[0];
+    __half *const s1base = msl.sl[1];
+    const float sc = fermi ? sz : s0;
+    const double *const hbase = pr.H;
+    const long long ldh = pr.ldh, ldy = pr.ldy, lds = pr.lds, ldx = pr.ldx;
+    double *const xbase = pr.Xd[0];
+    double *const dgz = pr.dg[kMatZ];
+    float *const dgzf = pr.dgf[kMatZ];
+    const double emax = st->emax;
     double tr = 0.0, sq = 0.0;
-    // block b takes rows b, b + grid, ...; thread t the column pairs (2t, 2t + 1),
-    // (2t + 2 blockDim, ...), ...: 16-byte loads of Hp where its row is aligned,
-    // 8-byte FP32 and 4-byte FP16 stores (ldy and lds are even).  Four column
-    // pairs per thread are loaded before any is used (enough bytes in flight
-    // to approach the HBM rate with 2 blocks of 256 per SM).
-    const int cstride = 2 * blockDim.x;
-    for (int i = blockIdx.x; i < n; i += gridDim.x) {
-        float sqr = 0.0f;
-        double sqd = 0.0;
-        const double *hrow = pr.H + static_cast<long long>(i) * pr.ldh;
-        const bool h16 = (reinterpret_cast<uintptr_t>(hrow) & 15u) == 0;
-        auto body = [&](int j, double h0, double h1) {
-            const bool two = j + 1 < n;
-            if (fp64) {
-                double *xr = pr.Xd[0] + static_cast<long long>(i) * pr.ldx;
-                const double x0 = ((i == j) ? st->emax - h0 : -h0) * inv_w;
-                xr[j] = x0;
-                if (i == j) tr += x0;
-                sqd += x0 * x0;
+    // one warp per row (warp w of the grid takes rows w, w + warps, ...); lane
+    // l the column pairs (2l, 2l + 1), (2l + 64, ...), ...: 16-byte loads of Hp
+    // where its row is aligned, 8-byte FP32 and 4-byte FP16 stores (ldy and
+    // lds are even).  Four column pairs per lane are loaded before any is used;
+    // with every row of n <= 4864 in flight at once (kInitBlocks blocks of 8
+    // warps), the bytes outstanding approach the HBM rate.
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    // one instantiation of the row loop per form (0: zero temperature, 1:
+    // finite temperature, 2: the FP64 schedule), so each keeps only its own
+    // registers live
+    auto rows = [&](auto form) {
+        constexpr int kForm = decltype(form)::value;
+        for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nwarps) {
+            float sqr = 0.0f;
+            double sqd = 0.0;
+            const double *hrow = hbase + static_cast<long long>(i) * ldh;
+            const bool h16 = (reinterpret_cast<uintptr_t>(hrow) & 15u) == 0;
+            float *const mrow = mbase + static_cast<long long>(i) * ldy;
+            __half *const s0row = s0base + static_cast<long long>(i) * lds;
+            __half *const s1row = s1base + static_cast<long long>(i) * lds;
+            auto body = [&](int j, double h0, double h1) {
+                const bool two = j + 1 < n;
+                if constexpr (kForm == 2) {
+                    double *xr = xbase + static_cast<long long>(i) * ldx;
+                    const double x0 = ((i == j) ? emax - h0 : -h0) * inv_w;
+                    xr[j] = x0;
+                    if (i == j) tr += x0;
+                    sqd += x0 * x0;
+                    if (two) {
+                        const double x1 = ((i == j + 1) ? emax - h1 : -h1) * inv_w;
+                        xr[j + 1] = x1;
+                        if (i == j + 1) tr += x1;
+                        sqd += x1 * x1;
+                    }
+                    return;
+                }
+                float y0, y1;
+                if constexpr (kForm == 1) {
+                    // x = (beta0 / 2)(H - mu0 I) in the diagonal form: the diagonal
+                    // in FP64 (d_Z), the small part zero on it
+                    y0 = (i == j) ? 0.0f : hb0f * f64_to_f32_rn(h0);
+                    y1 = (i == j + 1) ? 0.0f : hb0f * f64_to_f32_rn(h1);
+                    if (i == j || i == j + 1) {
+                        const double dv = hb0 * (((i == j) ? h0 : h1) - mu0);
+                        dgz[i] = dv;
+                        dgzf[i] = static_cast<float>(dv);
+                        tr += dv;
+                        sqd += dv * dv;
+                    }
+                } else {
+                    // FP64 arithmetic on the diagonal only
+                    y0 = -inv_wf * f64_to_f32_rn(h0);
+                    y1 = -inv_wf * f64_to_f32_rn(h1);
+                    if (i == j) y0 = static_cast<float>(-h0 * inv_w + dshift);
+                    if (i == j + 1) y1 = static_cast<float>(-h1 * inv_w + dshift);
+                }
+                if (!two) y1 = 0.0f;
+                const float ys0 = y0 * sc, ys1 = y1 * sc;
+                const __half a0 = __float2half_rn(ys0), a1 = __float2half_rn(ys1);
+                const __half b0 = __float2half_rn(ys0 - __half2float(a0)), b1 = __float2half_rn(ys1 - __half2float(a1));
                 if (two) {
-                    const double x1 = ((i == j + 1) ? st->emax - h1 : -h1) * inv_w;
-                    xr[j + 1] = x1;
-                    if (i == j + 1) tr += x1;
-                    sqd += x1 * x1;
+                    *reinterpret_cast<float2 *>(mrow + j) = make_float2(y0, y1);
+                    *reinterpret_cast<__half2 *>(s0row + j) = __halves2half2(a0, a1);
+                    *reinterpret_cast<__half2 *>(s1row + j) = __halves2half2(b0, b1);
+                } else {
+                    mrow[j] = y0;
+                    s0row[j] = a0;
+                    s1row[j] = b0;
                 }
-                return;
-            }
-            float y0, y1;
-            float sc;
-            const MatSlot *ms;
-            if (fermi) {
-                // x = (beta0 / 2)(H - mu0 I) in the diagonal form: the diagonal
-                // in FP64 (d_Z), the small part zero on it
-                y0 = (i == j) ? 0.0f : hb0f * f64_to_f32_rn(h0);
-                y1 = (i == j + 1) ? 0.0f : hb0f * f64_to_f32_rn(h1);
-                if (i == j || i == j + 1) {
-                    const double dv = hb0 * (((i == j) ? h0 : h1) - mu0);
-                    pr.dg[kMatZ][i] = dv;
-                    pr.dgf[kMatZ][i] = static_cast<float>(dv);
-                    tr += dv;
-                    sqd += dv * dv;
-                }
-                ms = &pr.mats[kMatZ];
-                sc = sz;
-            } else {
-                // FP64 arithmetic on the diagonal only
-                y0 = -inv_wf * f64_to_f32_rn(h0);
-                y1 = -inv_wf * f64_to_f32_rn(h1);
-                if (i == j) y0 = static_cast<float>(-h0 * inv_w + dshift);
-                if (i == j + 1) y1 = static_cast<float>(-h1 * inv_w + dshift);
-                ms = &pr.mats[kMatY0];
-                sc = s0;
-            }
-            if (!two) y1 = 0.0f;
-            float *mrow = ms->master + static_cast<long long>(i) * pr.ldy;
-            const size_t so = static_cast<size_t>(i) * pr.lds + j;
-            const float ys0 = y0 * sc, ys1 = y1 * sc;
-            const __half a0 = __float2half_rn(ys0), a1 = __float2half_rn(ys1);
-            const __half b0 = __float2half_rn(ys0 - __half2float(a0)), b1 = __float2half_rn(ys1 - __half2float(a1));
-            if (two) {
-                *reinterpret_cast<float2 *>(mrow + j) = make_float2(y0, y1);
-                *reinterpret_cast<__half2 *>(ms->sl[0] + so) = __halves2half2(a0, a1);
-                *reinterpret_cast<__half2 *>(ms->sl[1] + so) = __halves2half2(b0, b1);
-            } else {
-                mrow[j] = y0;
-                ms->sl[0][so] = a0;
-                ms->sl[1][so] = b0;
-            }
-            if (i == j) tr += y0;
-            if (i == j + 1) tr += y1;
-            sqr = fmaf(y0, y0, fmaf(y1, y1, sqr));
-        };
-        for (int jb = 2 * threadIdx.x; jb < n; jb += 4 * cstride) {
-            double hx[4], hy[4];
+                if (i == j) tr += y0;
+                if (i == j + 1) tr += y1;
+                sqr = fmaf(y0, y0, fmaf(y1, y1, sqr));
+            };
+            for (int jb = 2 * lane; jb < n; jb += 4 * 64) {
+                double hx[4], hy[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = jb + q * cstride;
-                hx[q] = 0.0;
-                hy[q] = 0.0;
-                if (j < n) {
-                    if (j + 1 < n && h16) {
-                        const double2 hv = *reinterpret_cast<const double2 *>(hrow + j);
-                        hx[q] = hv.x;
-                        hy[q] = hv.y;
-                    } else {
-                        hx[q] = hrow[j];
-                        if (j + 1 < n) hy[q] = hrow[j + 1];
+                for (int q = 0; q < 4; ++q) {
+                    const int j = jb + q * 64;
+                    hx[q] = 0.0;
+                    hy[q] = 0.0;
+                    if (j < n) {
+                        if (j + 1 < n && h16) {
+                            const double2 hv = *reinterpret_cast<const double2 *>(hrow + j);
+                            hx[q] = hv.x;
+                            hy[q] = hv.y;
+                        } else {
+                            hx[q] = hrow[j];
+                            if (j + 1 < n) hy[q] = hrow[j + 1];
+                        }
                     }
                 }
-            }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = jb + q * cstride;
-                if (j < n) body(j, hx[q], hy[q]);
+                for (int q = 0; q < 4; ++q) {
+                    const int j = jb + q * 64;
+                    if (j < n) body(j, hx[q], hy[q]);
+                }
             }
+            sq += static_cast<double>(sqr) + sqd;
         }
-        sq += static_cast<double>(sqr) + sqd;
-    }
+    };
+    if (fp64) rows(std::integral_constant<int, 2>{});
+    else if (fermi) rows(std::integral_constant<int, 1>{});
+    else rows(std::integral_constant<int, 0>{});
     __shared__ double red[2][32];
     tr = warp_sum(tr);
     sq = warp_sum(sq);
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
     if (lane == 0) { red[0][wid] = tr; red[1][wid] = sq; }
     __syncthreads();
     if (threadIdx.x == 0) {

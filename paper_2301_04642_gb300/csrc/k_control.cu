@@ -703,6 +703,8 @@ __device__ void control_fermi_start(SolveState *st, int sub) {
 // about 2^-10 kappa(M) <= 4e-3 (kappa <= 2 here) besides the square of their
 // input; the remaining pairs are split-FP16 and bring the bound under 3e-8.
 constexpr double kNsTarget = 3e-8, kNsSingleAbove = 0.05, kNsSingleFloor = 4e-3;
+// largest Newton logit shift folded into a doubling without a shift-only step
+constexpr double kFoldMax = 0.4;
 constexpr int kNsMaxSteps = 12;
 
 __device__ double ns_residual0(double mmin, double mmax) {
@@ -838,8 +840,12 @@ __device__ void control_fermi(SolveState *st, double tr0, double sq0, double tr1
         b = 0.0;
     } else {
         // large errors (entering phase B, or after a big drift) are removed by
-        // shift-only steps; small ones ride along with the next doubling
-        shift_only = fabs(dN) > 0.05 * sqrt(fmax(ne, 1.0)) && st->ft_shifts < 6;
+        // shift-only steps; small ones ride along with the next doubling.
+        // "Small" is in the logit: a Newton step |b| <= kFoldMax is accurate
+        // to a few per cent (the trace is smooth in b on that scale), and the
+        // next stage measures and corrects what it missed, so nothing is
+        // gained by verifying it first with a shift-only step.
+        shift_only = fabs(b) > kFoldMax && st->ft_shifts < 6;
     }
     if (stages_done && (fabs(dN) <= 1e-3 || st->ft_shifts >= 6)) {
         // ---- final product: D0 = (I - z)/2 and Q = (I - z^2)/4 in FP64

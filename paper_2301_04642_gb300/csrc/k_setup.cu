@@ -183,27 +183,13 @@ __global__ void __launch_bounds__(256, 4) k_init_x0(const MmaProb *probs, int pr
                     }
                     return;
                 }
-                float y0, y1;
-                if constexpr (kForm == 1) {
-                    // x = (beta0 / 2)(H - mu0 I) in the diagonal form: the diagonal
-                    // in FP64 (d_Z), the small part zero on it
-                    y0 = (i == j) ? 0.0f : hb0f * f64_to_f32_rn(h0);
-                    y1 = (i == j + 1) ? 0.0f : hb0f * f64_to_f32_rn(h1);
-                    if (i == j || i == j + 1) {
-                        const double dv = hb0 * (((i == j) ? h0 : h1) - mu0);
-                        dgz[i] = dv;
-                        dgzf[i] = static_cast<float>(dv);
-                        tr += dv;
-                        sqd += dv * dv;
-                    }
-                } else {
-                    // FP64 arithmetic on the diagonal only
-                    y0 = -inv_wf * f64_to_f32_rn(h0);
-                    y1 = -inv_wf * f64_to_f32_rn(h1);
-                    if (i == j) y0 = static_cast<float>(-h0 * inv_w + dshift);
-                    if (i == j + 1) y1 = static_cast<float>(-h1 * inv_w + dshift);
-                }
-                if (!two) y1 = 0.0f;
+                // FP32 only here (GB300 runs FP64 at 1/64 of the FP32 rate, and an
+                // FP64 expression guarded by i == j is still evaluated for every
+                // element); the diagonal entry is written as 0 and set after the
+                // row's loop by the lane that owns it
+                const float f = (kForm == 1) ? hb0f : -inv_wf;
+                const float y0 = (i == j) ? 0.0f : f * f64_to_f32_rn(h0);
+                const float y1 = (i == j + 1 || !two) ? 0.0f : f * f64_to_f32_rn(h1);
                 const float ys0 = y0 * sc, ys1 = y1 * sc;
                 const __half a0 = __float2half_rn(ys0), a1 = __float2half_rn(ys1);
                 const __half b0 = __float2half_rn(ys0 - __half2float(a0)), b1 = __float2half_rn(ys1 - __half2float(a1));
@@ -216,8 +202,6 @@ __global__ void __launch_bounds__(256, 4) k_init_x0(const MmaProb *probs, int pr
                     s0row[j] = a0;
                     s1row[j] = b0;
                 }
-                if (i == j) tr += y0;
-                if (i == j + 1) tr += y1;
                 sqr = fmaf(y0, y0, fmaf(y1, y1, sqr));
             };
             for (int jb = 2 * lane; jb < n; jb += 4 * 64) {
@@ -242,6 +226,27 @@ __global__ void __launch_bounds__(256, 4) k_init_x0(const MmaProb *probs, int pr
                 for (int q = 0; q < 4; ++q) {
                     const int j = jb + q * 64;
                     if (j < n) body(j, hx[q], hy[q]);
+                }
+            }
+            if (kForm != 2 && lane == ((i & 63) >> 1)) {
+                // the diagonal entry, in FP64: finite temperature keeps it in d_Z
+                // (the small part stays 0 there), zero temperature in Y0
+                const double hd = hrow[i];
+                if (kForm == 1) {
+                    const double dv = hb0 * (hd - mu0);
+                    dgz[i] = dv;
+                    dgzf[i] = static_cast<float>(dv);
+                    tr += dv;
+                    sqd += dv * dv;
+                } else {
+                    const float yd = static_cast<float>(-hd * inv_w + dshift);
+                    const float ys = yd * sc;
+                    const __half a = __float2half_rn(ys);
+                    mrow[i] = yd;
+                    s0row[i] = a;
+                    s1row[i] = __float2half_rn(ys - __half2float(a));
+                    tr += static_cast<double>(yd);
+                    sqd += static_cast<double>(yd) * yd;
                 }
             }
             sq += static_cast<double>(sqr) + sqd;

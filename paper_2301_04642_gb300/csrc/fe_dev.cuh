@@ -252,6 +252,20 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
     return __uint_as_float(sign | r);
 }
 
+// Exact FP32 -> FP64 conversion by integer operations on the encodings: the
+// conversion instruction runs on the FP64 pipe, which GB300 executes at 1/64
+// of the FP32 rate.  Zero, subnormal, infinite and NaN inputs take the
+// conversion instruction.
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return static_cast<double>(x);
+    const unsigned long long r = (static_cast<unsigned long long>(b & 0x80000000u) << 32) |
+                                 (static_cast<unsigned long long>(e + 896u) << 52) |
+                                 (static_cast<unsigned long long>(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double(static_cast<long long>(r));
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

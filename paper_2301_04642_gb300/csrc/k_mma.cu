@@ -1021,18 +1021,23 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                                 const bool on_diag = (j == i);
                                 double d = 0.0;
                                 if (okf(u)) {
-                                    if (fl & kOutDiag) {
-                                        d = on_diag ? diagv(os, u) : static_cast<double>(offv(os, u));
+                                    // the FP32 terms summed in FP32 and converted exactly by
+                                    // integer operations: GB300's FP64 pipe (1/64 of the FP32
+                                    // rate) keeps only the FP64 diagonal, the FP64 addend and
+                                    // the squared norm
+                                    if ((fl & kOutDiag) && on_diag) {
+                                        d = diagv(os, u);
+                                    } else if (fl & kOutDiag) {
+                                        d = f32_to_f64(offv(os, u));
                                     } else {
-                                        d = static_cast<double>(os.a) * (acc[c8 * 8 + u] * inv) +
-                                            static_cast<double>(os.b1) * e1f(u) +
-                                            static_cast<double>(os.b2) * e2f(u) + (on_diag ? os.c : 0.0);
+                                        d = f32_to_f64(fmaf(os.a, acc[c8 * 8 + u] * inv, fmaf(os.b1, e1f(u), os.b2 * e2f(u))));
+                                        if (on_diag) d += os.c;
                                     }
                                     if (Xa) d += Xa[static_cast<size_t>(j) * ldx + i];  // symmetric: read at (j, i)
                                     if (!on_diag) X[static_cast<size_t>(j) * ldx + i] = d;
                                     if (o == pout) {
                                         if (on_diag) tr += d;
-                                        sq += (on_diag ? 1.0 : 2.0) * d * d;
+                                        sq = fma(on_diag ? d : 2.0 * d, d, sq);
                                     }
                                     if (o == 1 && on_diag) tr1 += d;
                                 }

@@ -48,3 +48,19 @@ def test_reference_arm_default_workload_is_sampled():
 def test_reference_arm_unavailable_on_many_problem_workloads():
     d = _bench("--impl", "reference", "--workload", "ragged_batch64")
     assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_traffic_records_match_the_kernel_sources():
+    """Every DRAM-traffic record in profiles/traffic.json was taken on the
+    kernel source as it stands (its sha256 matches), so the bench line's
+    roofline carries the measured traffic, not null; a kernel edit without a
+    new capture fails here instead of silently dropping the figure."""
+    sys.path.insert(0, ROOT)
+    import bench
+    tab = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    src = {"k_sym_mma": "k_mma.cu", "k_digit_mma": "k_digit.cu", "k_fp64_step": "k_fp64.cu"}
+    assert tab
+    for key in tab:
+        kernel, workload = key.split("@")
+        got = bench.traffic_record(kernel, src[kernel], workload)
+        assert got is not None and got > 0, key
